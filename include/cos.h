@@ -1,0 +1,165 @@
+/*
+ * cos.h -- C ABI of the GB300 combinatorial-summation (CoS) graph evaluator.
+ *
+ * The method (Sec. II.B, Fig. 1): a leveled directed graph whose top node holds
+ * 1; every edge multiplies the value of its origin node by a propagator and
+ * adds the product to its destination node; every node is the sum over its
+ * in-edges; the last node holds the sum over all root-to-sink paths, one path
+ * per Feynman diagram.  The graph is built once and evaluated for many Monte
+ * Carlo samples of the vertex times (Sec. II.B last paragraph, Sec. IV).
+ *
+ * Conventions shared by every entry point
+ *   - Levels l = 0..L-1.  Level l owns the contiguous global node ids
+ *     [off_l, off_l + W_l), off_0 = 0.  W_0 = W_{L-1} = 1: node 0 is the root,
+ *     node N-1 the sink (N = sum of W_l).
+ *   - Edges are the flattened per-level lists of Fig. 3: int32 rows
+ *     (src, dst, kind, i, j), level-major (level_edge_count[l] rows for level l,
+ *     in increasing l).  Every edge into level l has src in level l-1 and dst in
+ *     level l.  Duplicate (src, dst) pairs are separate edges.
+ *   - Edge factor for sample s: G_kind(t_{s,i} - t_{s,j}) with the free-fermion
+ *     propagator G_k(tau) = -exp(-eps_k tau)/(1+exp(-beta eps_k)) for tau >= 0
+ *     and G_k(tau) = -G_k(tau+beta) for tau < 0 (tau = 0 takes the first branch;
+ *     the comparison is made on the double-precision times).
+ *   - Device memory: every buffer the library allocates belongs to the graph
+ *     handle and is freed by cos_destroy.  Output buffers passed in are owned by
+ *     the caller.  All device work runs on the CUDA device that was current when
+ *     the graph was created, on the stream passed in (NULL = legacy default
+ *     stream).  One graph handle must be used by one stream at a time.
+ *   - Every function returns COS_OK (0) or a negative cos_status.  On error,
+ *     cos_last_error() returns a thread-local message; nothing aborts the
+ *     process and no call leaves the CUDA context unusable.
+ */
+#ifndef COS_H_
+#define COS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cos_graph* cos_graph_t;
+
+enum cos_status {
+    COS_OK = 0,
+    COS_ERR_INVALID = -1,   /* bad argument or malformed graph; nothing was created or changed */
+    COS_ERR_OOM = -2,       /* a device or host allocation failed */
+    COS_ERR_CUDA = -3,      /* a CUDA runtime call failed (message in cos_last_error) */
+    COS_ERR_TIMEOUT = -4,   /* a grid barrier inside a kernel gave up waiting; results are invalid */
+    COS_ERR_OVERFLOW = -5,  /* count mode: the exact path count exceeds 2^63-1 (results wrap mod 2^64) */
+    COS_ERR_STATE = -6      /* call out of order, e.g. cos_evaluate before cos_set_samples */
+};
+
+enum cos_mode {
+    COS_MODE_FP64 = 0,        /* propagators, products and sums in IEEE double */
+    COS_MODE_FP32_MIXED = 1,  /* propagators (formed in double, rounded once) and per-level products
+                                 in float; sink node and cross-sample sums in double, compensated */
+    COS_MODE_COUNT_I64 = 2    /* unit edge weights, int64 sums modulo 2^64: the number of paths */
+};
+
+enum cos_t_flags {
+    COS_T_DEVICE_DS = 0,      /* t is a device pointer, layout [D][S] (sample index fastest) */
+    COS_T_HOST = 1,           /* t is a host pointer (page-locked memory gives an asynchronous copy) */
+    COS_T_SAMPLE_MAJOR = 2    /* layout [S][D] (time-variable index fastest) */
+};
+
+/*
+ * Graph ingest (Sec. II.C "Graph flattening", Fig. 3).  Validates the levels
+ * and edges, buckets them per level, stable-sorts each level by destination
+ * into CSR form (the in-edges of one node stay in input order), numbers the
+ * distinct (kind, i, j) triples as propagator slots, counts root-to-sink paths
+ * exactly on the host (128-bit, for the count-mode overflow flag), and copies
+ * the result to the current device.
+ *   num_levels         L >= 2
+ *   level_width[L]     host, W_l >= 1, W_0 = W_{L-1} = 1, N = sum W_l < 2^31
+ *   level_edge_count[L] host, [0] == 0, [l] >= 0, E = sum < 2^31
+ *   edges[E][5]        host, int32 rows (src, dst, kind, i, j) as above
+ *   num_kinds K >= 1, num_times D >= 1 (kind < K, i, j < D)
+ *   out                receives the handle; untouched on error
+ * The caller keeps ownership of its arrays; they are not referenced afterwards.
+ * Errors: COS_ERR_INVALID (any violation, message names it), COS_ERR_OOM, COS_ERR_CUDA.
+ */
+int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64_t* level_edge_count,
+                     const int32_t* edges, int32_t num_kinds, int32_t num_times, cos_graph_t* out);
+
+/*
+ * Attach a batch of Monte Carlo samples (Sec. II.C "Distributing the task on a
+ * grid of blocks": one evaluation per set of internal variables).
+ *   num_samples S >= 0
+ *   t        S x D doubles, layout and location given by t_flags (cos_t_flags);
+ *            values are the imaginary times, expected in [0, beta)
+ *   eps[K]   host doubles, the per-kind energies
+ *   beta     inverse temperature (> 0)
+ *   stream   cudaStream_t (as void*) on which the copy is enqueued
+ * Grows the graph's device workspace if needed (the only call besides
+ * cos_create_graph that allocates).  The copy is asynchronous: a host t must
+ * stay valid until the stream reaches this point.
+ * Errors: COS_ERR_INVALID, COS_ERR_OOM, COS_ERR_CUDA.
+ */
+int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t t_flags,
+                    const double* eps, double beta, void* stream);
+
+/*
+ * Evaluate the path sum of every attached sample (Fig. 1; Sec. II.C): one
+ * persistent cooperative kernel computes the propagator table, walks the levels
+ * in order with a grid-wide barrier between levels, writes the sink value per
+ * sample and reduces the samples.  Allocates nothing; may be captured in a CUDA
+ * graph when mean_out is NULL.
+ *   mode            cos_mode
+ *   per_sample_out  device pointer or NULL: double[S] (FP64, FP32_MIXED) or
+ *                   int64[S] (COUNT_I64), index = sample index
+ *   mean_out        host pointer or NULL.  If non-NULL the call waits for the
+ *                   stream and stores the mean over samples (Neumaier-compensated
+ *                   double; in count mode the mean of the counts), and reports
+ *                   kernel-side errors.  If NULL the call returns at once; use
+ *                   cos_get_result to wait and collect.
+ * Errors: COS_ERR_STATE (no samples attached), COS_ERR_INVALID (mode),
+ *         COS_ERR_CUDA, COS_ERR_TIMEOUT, COS_ERR_OVERFLOW (count mode, exact
+ *         count > 2^63-1; the wrapped results are still written).
+ */
+int cos_evaluate(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean_out, void* stream);
+
+/*
+ * Wait for the last cos_evaluate on this graph (stream = the one it ran on) and
+ * return its status; if mean_out is non-NULL store its mean there.
+ */
+int cos_get_result(cos_graph_t g, double* mean_out, void* stream);
+
+/*
+ * Graph facts, written to info[0..n) in this order (n <= 10):
+ *   0 L, 1 N, 2 E, 3 number of propagator slots P, 4 widest level W_max,
+ *   5 path count mod 2^64 (from ingest), 6 path-count overflow flag,
+ *   7 K, 8 D, 9 device ordinal
+ */
+int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
+
+/*
+ * Launch shape used by cos_evaluate.  Fields <= 0 mean "automatic".
+ *   samples_per_lane  1, 2 or 4 consecutive samples per thread (vector width)
+ *   tile_samples      samples per tile (rounded up to 32 * samples_per_lane)
+ *   rows_per_warp     destination rows one warp takes per work item
+ *   blocks_per_sm     persistent CTAs per SM (capped by occupancy)
+ *   timeout_ms        grid-barrier wait limit
+ */
+typedef struct cos_tuning {
+    int32_t samples_per_lane;
+    int32_t tile_samples;
+    int32_t rows_per_warp;
+    int32_t blocks_per_sm;
+    int32_t timeout_ms;
+} cos_tuning;
+
+int cos_set_tuning(cos_graph_t g, const cos_tuning* tuning);
+int cos_get_tuning(cos_graph_t g, int32_t mode, cos_tuning* tuning);
+
+/* Free every device and host resource of the handle (NULL is accepted). */
+int cos_destroy(cos_graph_t g);
+
+/* Thread-local message describing the last non-OK return on this thread. */
+const char* cos_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COS_H_ */

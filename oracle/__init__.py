@@ -1,0 +1,193 @@
+"""CPU oracle for CoS graph evaluation -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this package.  The GPU library never imports, links or runs it, and this
+package never imports the GPU library.
+
+Contents
+  * ``cos_oracle.c`` (built here with gcc): the level-wise dynamic program of
+    Sec. II.B / Fig. 1 in IEEE double, per-sample propagators, unit-weight path
+    counts with 128-bit overflow detection, Neumaier summation.
+  * ``brute_force_paths`` / ``brute_force_sum``: pure-Python enumeration of all
+    root-to-sink paths (one path = one diagram, Sec. II.B) for tiny graphs.
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests
+(closed forms, brute force, library matrix products, propagator identities).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cos_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libcos_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile cos_oracle.c into oracle/_build/libcos_oracle.so (gcc, OpenMP, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            lib.cos_oracle_propagator.restype = ctypes.c_double
+            lib.cos_oracle_propagator.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            lib.cos_oracle_propagator_array.restype = None
+            lib.cos_oracle_propagator_array.argtypes = [ctypes.c_double, ctypes.c_double, _f64p, _f64p,
+                                                        ctypes.c_int64]
+            lib.cos_oracle_pathsum.restype = ctypes.c_int
+            lib.cos_oracle_pathsum.argtypes = [ctypes.c_int32, _i64p, _i64p, _i32p, _f64p, _f64p]
+            lib.cos_oracle_eval.restype = ctypes.c_int
+            lib.cos_oracle_eval.argtypes = [ctypes.c_int32, _i64p, _i64p, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                            _f64p, ctypes.c_double, ctypes.c_int64, _f64p, _f64p, _f64p,
+                                            ctypes.c_int32]
+            lib.cos_oracle_count.restype = ctypes.c_int
+            lib.cos_oracle_count.argtypes = [ctypes.c_int32, _i64p, _i64p, _i32p, _i64p, _i32p]
+            lib.cos_oracle_neumaier_sum.restype = ctypes.c_double
+            lib.cos_oracle_neumaier_sum.argtypes = [_f64p, ctypes.c_int64]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _graph_arrays(graph):
+    w = np.ascontiguousarray(graph.widths, dtype=np.int64)
+    c = np.ascontiguousarray(graph.edge_counts, dtype=np.int64)
+    e = np.ascontiguousarray(graph.edges, dtype=np.int32)
+    return w, c, e
+
+
+def propagator(eps: float, beta: float, tau) -> np.ndarray:
+    """G(tau) for one kind, elementwise over tau (free-fermion propagator, tau = t_i - t_j)."""
+    lib = _load()
+    tau = np.ascontiguousarray(np.atleast_1d(np.asarray(tau, dtype=np.float64)))
+    out = np.empty_like(tau)
+    lib.cos_oracle_propagator_array(float(eps), float(beta), _p(tau, _f64p), _p(out, _f64p), tau.size)
+    return out
+
+
+def edge_weights(graph, eps: np.ndarray, beta: float, t_sample: np.ndarray) -> np.ndarray:
+    """Per-edge factors w_e = G_{k_e}(t_{i_e} - t_{j_e}) for one sample (t_sample[D])."""
+    e = graph.edges
+    tau = t_sample[e[:, 3]] - t_sample[e[:, 4]]
+    out = np.empty(e.shape[0])
+    for k in np.unique(e[:, 2]):
+        m = e[:, 2] == k
+        out[m] = propagator(eps[k], beta, tau[m])
+    return out
+
+
+def pathsum(graph, w: np.ndarray) -> np.ndarray:
+    """All node values of the level-wise DP with sample-independent edge weights w[E]."""
+    lib = _load()
+    wd, c, e = _graph_arrays(graph)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.empty(int(wd.sum()))
+    rc = lib.cos_oracle_pathsum(len(wd), _p(wd, _i64p), _p(c, _i64p), _p(e, _i32p), _p(w, _f64p), _p(out, _f64p))
+    if rc:
+        raise ValueError("invalid graph")
+    return out
+
+
+def evaluate(graph, eps: np.ndarray, beta: float, t: np.ndarray, with_abs: bool = True,
+             nthreads: int = 0) -> Tuple[np.ndarray, Optional[np.ndarray]]:
+    """Per-sample sink values R[s] (and A[s] = sum of |path| values) in double precision."""
+    lib = _load()
+    wd, c, e = _graph_arrays(graph)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    S, D = t.shape
+    if D != graph.num_times:
+        raise ValueError("t must be [S, D]")
+    R = np.empty(S)
+    A = np.empty(S) if with_abs else None
+    rc = lib.cos_oracle_eval(len(wd), _p(wd, _i64p), _p(c, _i64p), _p(e, _i32p), graph.num_kinds, D,
+                             _p(eps, _f64p), float(beta), S, _p(t, _f64p), _p(R, _f64p),
+                             _p(A, _f64p) if A is not None else None, int(nthreads))
+    if rc:
+        raise ValueError(f"oracle evaluation failed ({rc})")
+    return R, A
+
+
+def count_paths(graph) -> Tuple[int, bool]:
+    """(path count modulo 2^64 as a signed int64, overflow flag for counts above 2^63-1)."""
+    lib = _load()
+    wd, c, e = _graph_arrays(graph)
+    cnt = ctypes.c_int64(0)
+    ovf = ctypes.c_int32(0)
+    rc = lib.cos_oracle_count(len(wd), _p(wd, _i64p), _p(c, _i64p), _p(e, _i32p), ctypes.byref(cnt),
+                              ctypes.byref(ovf))
+    if rc:
+        raise ValueError("invalid graph")
+    return int(cnt.value), bool(ovf.value)
+
+
+def neumaier_sum(x: np.ndarray) -> float:
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib.cos_oracle_neumaier_sum(_p(x, _f64p), x.size))
+
+
+def neumaier_mean(x: np.ndarray) -> float:
+    return neumaier_sum(x) / max(1, np.asarray(x).size)
+
+
+def brute_force_paths(graph, limit: int = 200_000) -> List[List[int]]:
+    """Every root-to-sink path as a list of edge indices (depth-first; tiny graphs only)."""
+    e = graph.edges
+    N = graph.num_nodes
+    out_edges: List[List[int]] = [[] for _ in range(N)]
+    for q in range(e.shape[0]):
+        out_edges[int(e[q, 0])].append(q)
+    paths: List[List[int]] = []
+    stack: List[Tuple[int, List[int]]] = [(0, [])]
+    while stack:
+        node, path = stack.pop()
+        if node == N - 1:
+            paths.append(path)
+            if len(paths) > limit:
+                raise ValueError("too many paths for brute force")
+            continue
+        for q in out_edges[node]:
+            stack.append((int(e[q, 1]), path + [q]))
+    return paths
+
+
+def brute_force_sum(paths: Sequence[Sequence[int]], w: np.ndarray) -> Tuple[float, float]:
+    """(sum over paths of the product of w along the path, the same with |w|)."""
+    r = 0.0
+    a = 0.0
+    for path in paths:
+        prod = 1.0
+        for q in path:
+            prod *= float(w[q])
+        r += prod
+        a += abs(prod)
+    return r, a

@@ -1,0 +1,69 @@
+"""Structure of the seeded synthetic workloads (no method arithmetic here)."""
+import numpy as np
+import pytest
+
+from workloads import (FaninSpec, batched, geometric_widths, make_graph, medium, serving_pool, tiny,
+                       widths_for_target)
+
+
+def _check_graph(g, fmax):
+    off = g.offsets()
+    e = g.edges
+    assert g.widths[0] == 1 and g.widths[-1] == 1
+    assert g.edge_counts[0] == 0 and int(g.edge_counts.sum()) == e.shape[0]
+    lo = 0
+    for l in range(1, g.num_levels):
+        hi = lo + int(g.edge_counts[l])
+        src, dst = e[lo:hi, 0], e[lo:hi, 1]
+        assert np.all((src >= off[l - 1]) & (src < off[l]))
+        assert np.all((dst >= off[l]) & (dst < off[l + 1]))
+        assert np.all(np.diff(src) >= 0)                       # flattened per level in src order
+        fan = np.bincount(dst - off[l], minlength=int(g.widths[l]))
+        assert fan.min() >= 1 and fan.max() <= min(fmax, int(g.widths[l - 1]))
+        pairs = set(zip(src.tolist(), dst.tolist()))
+        assert len(pairs) == hi - lo                           # parents drawn without replacement
+        lo = hi
+    assert np.all((e[:, 2] >= 0) & (e[:, 2] < g.num_kinds))
+    assert np.all((e[:, 3] >= 0) & (e[:, 3] < g.num_times) & (e[:, 4] >= 0) & (e[:, 4] < g.num_times))
+
+
+def test_tiny_shape_and_determinism():
+    a, b = tiny(), tiny()
+    assert a.graph.widths.tolist() == [1, 4, 8, 8, 4, 1] and a.graph.num_nodes == 26
+    np.testing.assert_array_equal(a.graph.edges, b.graph.edges)
+    np.testing.assert_array_equal(a.samples.t, b.samples.t)
+    assert a.samples.t.shape == (1024, 6) and a.samples.eps.shape == (4,)
+    assert np.all((a.samples.t >= 0) & (a.samples.t < 10.0))
+    assert np.all(np.abs(a.samples.eps) <= 2.0)
+    _check_graph(a.graph, 3)
+
+
+def test_medium_shape():
+    m = medium(num_samples=8)
+    assert m.graph.widths.tolist() == [1, 32, 1024, 4096, 4096, 4096, 4096, 1024, 32, 1]
+    assert m.graph.num_nodes == 18498 and m.graph.num_kinds == 16 and m.graph.num_times == 10
+    _check_graph(m.graph, 4)
+
+
+def test_geometric_profiles():
+    assert geometric_widths(14, 64, 1 << 18) == [1, 64, 4096] + [262144] * 8 + [4096, 64, 1]
+    for L, N in [(6, 1000), (6, 10 ** 6), (18, 5000), (10, 123456)]:
+        w = widths_for_target(L, N)
+        assert len(w) == L and w[0] == 1 and w[-1] == 1 and sum(w) >= N
+        assert sum(w) <= N * 1.25 + 64
+
+
+def test_geometric_fanin_mean():
+    rng = np.random.default_rng(0)
+    f = FaninSpec("geometric", 6, 0.31).draw(rng, 200000)
+    assert f.min() == 1 and f.max() == 6
+    assert abs(f.mean() - 2.5) < 0.05
+
+
+def test_batched_and_pool_are_valid():
+    for wl in batched(num_graphs=4, max_nodes=2e4, max_samples=8192):
+        _check_graph(wl.graph, 4)
+        assert wl.graph.num_times == wl.graph.num_levels
+    for g, eps in serving_pool(pool_size=3, max_nodes=2e4):
+        _check_graph(g, 6)
+        assert eps.shape == (32,)
