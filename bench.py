@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 CoS evaluator (edge.sample updates/s).
+
+One step = one pass of the hot path over one batch of synthetic samples:
+attach the samples (device-resident times, transposed on the GPU) and evaluate
+the path sums of every sample (propagator table, level walk, sink values,
+compensated mean) through the C ABI.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload medium|large|tiny]
+                  [--impl ours|reference]
+
+Under torchrun each rank evaluates its own batch of samples of the same graph
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import large, medium, tiny  # noqa: E402
+
+WORKLOADS = {
+    # name: (factory, mode name, description)
+    "medium": (medium, "fp64", "medium leveled DAG: L=10, widths 1..4096..1, N=18498, E=46188, fan-in U{1..4}, "
+                               "K=16 kinds, D=10 times, 65536 samples per GPU, beta=10, plain FP64"),
+    "large": (large, "mixed", "large leveled DAG: L=14, widths 1..262144..1, N=2105474, E=5263492, geometric "
+                              "fan-in 1..6, K=32, D=14, 2^20 samples per GPU, FP32 bulk / FP64 sink"),
+    "tiny": (tiny, "fp64", "tiny leveled DAG: L=6, widths [1,4,8,8,4,1], N=26, K=4, D=6, 1024 samples, FP64"),
+}
+MODES = {"fp64": 0, "mixed": 1, "count": 2}
+DTYPE = {"fp64": "f64", "mixed": "f32 (sink and sample sums f64)", "count": "int64"}
+L2_FLUSH_BYTES = 512 << 20
+FALLBACK_HBM_GBS = 6800.0
+# FP64 FMA peak: 152 SMs x 2 DFMA/clk/SM x 2070 MHz (the nominal 1.25 TFLOP/s FP64 of GB300).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="medium")
+    ap.add_argument("--mode", choices=sorted(MODES), default=None)
+    ap.add_argument("--samples", type=int, default=None, help="samples per GPU (default: the workload's)")
+    ap.add_argument("--tuning", type=str, default="", help="JSON dict passed to cos_set_tuning")
+    ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Rank 0 uses the workload's own seed; rank r > 0 draws its own samples."""
+    return base_seed if rank == 0 else base_seed * 1000003 + rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+    QUERY = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and parts[1] != self.uuid:
+                    continue
+                try:
+                    rows.append((float(parts[2]), float(parts[3]), parts[6:10]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        seen = sorted({name for _, _, flags in rows for name, fl in zip(self.REASONS, flags) if fl == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": seen, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ measured peaks and profiles
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if it covers this kernel build."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get(kernel_tag)
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_rate(graph, samples, seconds: float, nthreads: int = 0):
+    """Edge.sample updates/s of the CPU oracle on a bounded prefix of the samples."""
+    import oracle
+    oracle.build()
+    n = 16
+    t0 = time.perf_counter()
+    oracle.evaluate(graph, samples.eps, samples.beta, samples.t[:n], with_abs=False, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    n2 = int(min(samples.num_samples, max(n, n * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.evaluate(graph, samples.eps, samples.beta, samples.t[:n2], with_abs=False, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return graph.num_edges * n2 / dt, n2, dt
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2501_00675_gb300 as cg
+    from paper_2501_00675_gb300 import _build
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    factory, default_mode, desc = WORKLOADS[args.workload]
+    mode_name = args.mode or default_mode
+    mode = MODES[mode_name]
+    kw = {} if args.samples is None else {"num_samples": args.samples}
+    base = factory(**kw)
+    wl = factory(seed=rank_seed({"medium": 1, "large": 2, "tiny": 0}[args.workload], rank), **kw) if rank else base
+    # the graph is the workload's (replicated on every rank); samples are per rank
+    g, s = base.graph, wl.samples
+    S, E, N, D, K = s.num_samples, g.num_edges, g.num_nodes, g.num_times, g.num_kinds
+
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    cg.load_library()
+    gr = cg.Graph.from_workload_graph(g)
+    if args.tuning:
+        gr.set_tuning(**json.loads(args.tuning))
+    stream = torch.cuda.current_stream(dev)
+    t_dev = torch.from_numpy(s.t).to(dev)                                   # [S][D], resident in HBM
+    out_dtype = torch.int64 if mode == 2 else torch.float64
+    out = torch.empty(S, dtype=out_dtype, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        gr.set_samples(t_dev, s.eps, s.beta, cg.COS_T_SAMPLE_MAJOR, stream=stream)
+        gr.evaluate(mode, out=out, want_mean=False, stream=stream, allow_overflow=True)
+
+    for _ in range(args.warmup):
+        step()
+    gr.get_result(stream)
+    torch.cuda.synchronize()
+    tuning = gr.get_tuning(mode)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid).start()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()                                                       # untimed L2 flush
+        ev[k][0].record(stream)
+        gr.set_samples(t_dev, s.eps, s.beta, cg.COS_T_SAMPLE_MAJOR, stream=stream)
+        ev[k][1].record(stream)
+        gr.evaluate(mode, out=out, want_mean=False, stream=stream, allow_overflow=True)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    mean = gr.get_result(stream) if mode != 2 else float("nan")
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    walk_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    total_s = sum(step_ms) / 1e3
+    total_s = max_over_ranks(total_s, world, dev)
+    units = float(E) * S * args.steps * world
+    value = units / total_s
+
+    # roofline of the walker kernel (one launch per evaluate)
+    w_bytes = 4 if mode == 1 else 8
+    alg_bytes = S * (2.0 * N * w_bytes + D * 8 + 8)
+    walk_s = statistics.mean(walk_ms) / 1e3
+    peak, peak_kind = hbm_peak()
+    hbm = {"bound": "hbm", "achieved": alg_bytes / walk_s / 1e9, "peak": peak, "unit": "GB/s",
+           "frac": alg_bytes / walk_s / 1e9 / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+           if peak_kind == "measured" else "fallback 6.8 TB/s",
+           "traffic": profiled_traffic(f"walk_{mode_name}_{args.workload}"),
+           "algorithmic_bytes_per_launch": alg_bytes}
+    if mode == 0:
+        tflops = 2.0 * E * S / walk_s / 1e12
+        alu = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": tflops / FP64_PEAK_TFLOPS, "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2070 MHz",
+               "traffic": hbm["traffic"], "algorithmic_flops_per_launch": 2.0 * E * S}
+        roofline, other = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+    else:
+        roofline, other = hbm, None
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        t_host = torch.from_numpy(s.t).pin_memory()
+        r_host = torch.empty(S, dtype=out_dtype).pin_memory()
+        for _ in range(2):
+            gr.set_samples(t_host, s.eps, s.beta, cg.COS_T_HOST | cg.COS_T_SAMPLE_MAJOR, stream=stream)
+            gr.evaluate(mode, out=out, want_mean=False, stream=stream, allow_overflow=True)
+            r_host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        e_ms = []
+        barrier(world)
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gr.set_samples(t_host, s.eps, s.beta, cg.COS_T_HOST | cg.COS_T_SAMPLE_MAJOR, stream=stream)
+            gr.evaluate(mode, out=out, want_mean=False, stream=stream, allow_overflow=True)
+            r_host.copy_(out, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e_ms.append(a.elapsed_time(b))
+        barrier(world)
+        e_total = max_over_ranks(sum(e_ms) / 1e3, world, dev)
+        e2e = {"value": units / e_total, "unit": "edge·sample updates/s",
+               "h2d_bytes_per_step": int(S * D * 8 + K * 8), "d2h_bytes_per_step": int(S * 8)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, n, dt = oracle_rate(g, s, args.cpu_baseline_seconds)
+        cpu = {"value": rate, "unit": "edge·sample updates/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": f"first {n} of {S} samples of the same workload ({dt:.1f} s, OpenMP over samples)"}
+    gr.close()
+    if rank != 0:
+        return None
+    line = {
+        "metric": "edge·sample updates/s", "value": value, "unit": "edge·sample updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[mode_name],
+        "data": "synthetic (seeded random leveled DAG and uniform sample times)",
+        "config": {"workload": desc, "mode": mode_name, "samples_per_gpu": S, "graph": {"L": g.num_levels, "N": N, "E": E,
+                   "K": K, "D": D}, "parallelism": f"sample-sharded x{world}, graph replicated, no collective",
+                   "l2": "flushed between timed steps (512 MB write); working set larger than L2",
+                   "tuning": tuning},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+        "clocks": clk, "walk_ms_per_launch": statistics.mean(walk_ms), "mean_R": mean,
+    }
+    if other is not None:
+        line["roofline_secondary"] = other
+    return line
+
+
+# ------------------------------------------------------------------ reference arm (the CPU oracle)
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    factory, default_mode, desc = WORKLOADS[args.workload]
+    mode_name = args.mode or default_mode
+    kw = {} if args.samples is None else {"num_samples": args.samples}
+    wl = factory(**kw)
+    g, s = wl.graph, wl.samples
+    import oracle
+    oracle.build()
+    # size each step so that warmup + steps take about two minutes in total
+    n = 8
+    t0 = time.perf_counter()
+    oracle.evaluate(g, s.eps, s.beta, s.t[:n], with_abs=False)
+    per = (time.perf_counter() - t0) / n
+    n_step = int(max(8, min(s.num_samples, 120.0 / max(per, 1e-9) / max(1, args.steps + args.warmup))))
+    for k in range(args.warmup):
+        oracle.evaluate(g, s.eps, s.beta, s.t[:n_step], with_abs=False)
+    times = []
+    for k in range(args.steps):
+        lo = (k * n_step) % max(1, s.num_samples - n_step + 1)
+        t0 = time.perf_counter()
+        oracle.evaluate(g, s.eps, s.beta, s.t[lo:lo + n_step], with_abs=False)
+        times.append(time.perf_counter() - t0)
+    value = g.num_edges * n_step * args.steps / sum(times)
+    cores = len(os.sched_getaffinity(0))
+    return {
+        "impl": "reference", "metric": "edge·sample updates/s", "value": value, "unit": "edge·sample updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded random leveled DAG and uniform sample times)",
+        "config": {"workload": desc, "mode": mode_name, "samples_per_step": n_step,
+                   "note": "the reference arm is the CPU oracle (plain level-wise DP in double, OpenMP over samples)"},
+        "cpu_baseline": {"value": value, "unit": "edge·sample updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n_step} samples per step of the {args.workload} workload"},
+        "e2e": {"value": value, "unit": "edge·sample updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if args.impl == "reference":
+            # only rank 0 runs the oracle; the other ranks exit at once without work
+            if rank != 0:
+                return 0
+        else:
+            dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1 and args.impl != "reference":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+"""ctypes binding of libcosgpu.so: the C entry points under their C names, plus a
+small handle class.  Argument marshalling only -- every step of the evaluation
+runs in the CUDA library.  PyTorch supplies device memory and streams.
+
+There is no fallback: if the library is missing or no GPU is present, calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+COS_OK = 0
+COS_ERR_INVALID = -1
+COS_ERR_OOM = -2
+COS_ERR_CUDA = -3
+COS_ERR_TIMEOUT = -4
+COS_ERR_OVERFLOW = -5
+COS_ERR_STATE = -6
+
+COS_MODE_FP64 = 0
+COS_MODE_FP32_MIXED = 1
+COS_MODE_COUNT_I64 = 2
+
+COS_T_DEVICE_DS = 0
+COS_T_HOST = 1
+COS_T_SAMPLE_MAJOR = 2
+
+EXPORTED = ["cos_create_graph", "cos_set_samples", "cos_evaluate", "cos_get_result", "cos_graph_info",
+            "cos_set_tuning", "cos_get_tuning", "cos_destroy", "cos_last_error"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CosError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"[{code}] {message}")
+        self.code = code
+
+
+class CosTuning(ctypes.Structure):
+    _fields_ = [("samples_per_lane", ctypes.c_int32), ("tile_samples", ctypes.c_int32),
+                ("rows_per_warp", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("timeout_ms", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = False):
+    """Load libcosgpu.so (raises if it is missing and build_if_missing is False)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing: build it with paper_2501_00675_gb300._build.build()")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.cos_create_graph.argtypes = [i32, vp, vp, vp, i32, i32, ctypes.POINTER(vp)]
+        lib.cos_set_samples.argtypes = [vp, i64, vp, i32, vp, f64, vp]
+        lib.cos_evaluate.argtypes = [vp, i32, vp, vp, vp]
+        lib.cos_get_result.argtypes = [vp, vp, vp]
+        lib.cos_graph_info.argtypes = [vp, vp, i32]
+        lib.cos_set_tuning.argtypes = [vp, ctypes.POINTER(CosTuning)]
+        lib.cos_get_tuning.argtypes = [vp, i32, ctypes.POINTER(CosTuning)]
+        lib.cos_destroy.argtypes = [vp]
+        lib.cos_last_error.restype = ctypes.c_char_p
+        lib.cos_last_error.argtypes = []
+        for name in EXPORTED[:-1]:
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, allow=()) -> int:
+    if rc != COS_OK and rc not in allow:
+        msg = load_library().cos_last_error()
+        raise CosError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Graph:
+    """Owning handle of one device-resident CoS graph (cos_create_graph / cos_destroy)."""
+
+    def __init__(self, widths: Sequence[int], edge_counts: Sequence[int], edges: np.ndarray, num_kinds: int,
+                 num_times: int):
+        lib = load_library()
+        self._w = np.ascontiguousarray(widths, dtype=np.int64)
+        self._c = np.ascontiguousarray(edge_counts, dtype=np.int64)
+        e = np.ascontiguousarray(edges, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(lib.cos_create_graph(len(self._w), _ptr(self._w), _ptr(self._c), _ptr(e) if e.size else None,
+                                    int(num_kinds), int(num_times), ctypes.byref(h)))
+        self._h = h
+        self.num_samples = 0
+
+    @classmethod
+    def from_workload_graph(cls, g) -> "Graph":
+        return cls(g.widths, g.edge_counts, g.edges, g.num_kinds, g.num_times)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def info(self) -> dict:
+        arr = np.zeros(10, dtype=np.int64)
+        _check(load_library().cos_graph_info(self._h, _ptr(arr), 10))
+        keys = ["L", "N", "E", "P", "W_max", "count", "count_overflow", "K", "D", "device"]
+        return {k: int(v) for k, v in zip(keys, arr)}
+
+    def set_samples(self, t, eps, beta: float, t_flags: int, num_samples: Optional[int] = None, stream=None):
+        """t: torch tensor (device or host) or numpy array (host); layout per t_flags."""
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        if num_samples is None:
+            num_samples = int(t.shape[0] if (t_flags & COS_T_SAMPLE_MAJOR) else t.shape[1])
+        self._eps = eps
+        _check(load_library().cos_set_samples(self._h, int(num_samples), _ptr(t), int(t_flags), _ptr(eps),
+                                              float(beta), _stream_handle(stream)))
+        self.num_samples = int(num_samples)
+
+    def evaluate(self, mode: int, out=None, want_mean: bool = True, stream=None, allow_overflow: bool = False):
+        """Run cos_evaluate; returns the mean (float) if want_mean else None."""
+        mean = ctypes.c_double(0.0)
+        rc = load_library().cos_evaluate(self._h, int(mode), _ptr(out), ctypes.addressof(mean) if want_mean else None,
+                                         _stream_handle(stream))
+        _check(rc, allow=(COS_ERR_OVERFLOW,) if allow_overflow else ())
+        return mean.value if want_mean else None
+
+    def get_result(self, stream=None) -> float:
+        mean = ctypes.c_double(0.0)
+        _check(load_library().cos_get_result(self._h, ctypes.addressof(mean), _stream_handle(stream)))
+        return mean.value
+
+    def set_tuning(self, samples_per_lane=0, tile_samples=0, rows_per_warp=0, blocks_per_sm=0, timeout_ms=0):
+        t = CosTuning(samples_per_lane, tile_samples, rows_per_warp, blocks_per_sm, timeout_ms)
+        _check(load_library().cos_set_tuning(self._h, ctypes.byref(t)))
+
+    def get_tuning(self, mode: int) -> dict:
+        t = CosTuning()
+        _check(load_library().cos_get_tuning(self._h, int(mode), ctypes.byref(t)))
+        return t.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().cos_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,539 @@
+// Host side of the C ABI: graph ingest (validation, per-level dst-sorted CSR,
+// propagator slots, exact path count), sample upload, workspace management,
+// evaluate dispatch and error reporting.  See include/cos.h for the contract.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cos_internal.cuh"
+
+using namespace cosgpu;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(COS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(COS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define COS_CUDA(call, what)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct cos_graph {
+    int device = 0;
+    int32_t L = 0, K = 0, D = 0;
+    int64_t N = 0, E = 0, P = 0, Wmax = 0;
+    std::vector<int64_t> widths, off, ecount;
+    int64_t count_wrapped = 0;
+    bool count_overflow = false;
+    // device graph
+    LevelDesc* d_levels = nullptr;
+    int32_t* d_row_ptr = nullptr;
+    int2* d_edges = nullptr;
+    int32_t* d_slot_kij = nullptr;
+    Ctrl* d_ctrl = nullptr;
+    // samples
+    bool has_samples = false;
+    int64_t S = 0, t_ld = 0, t_cap = 0;
+    double beta = 0.0;
+    double* d_t = nullptr;
+    double* d_eps = nullptr;
+    double* d_stage = nullptr;      // [S][D] staging for host sample-major input
+    int64_t stage_cap = 0;
+    // workspace
+    void* d_arena = nullptr;
+    size_t arena_bytes = 0;
+    double* d_partials = nullptr;
+    int64_t partial_cap = 0;
+    void* d_R = nullptr;            // internal per-sample output when the caller passes none
+    int64_t R_cap = 0;
+    cos_tuning tuning{0, 0, 0, 0, 0};
+    int last_status_pending = 0;    // 1 while an evaluate has not been collected
+    int last_mode = 0;
+};
+
+namespace {
+
+// Bytes of workspace per sample of a tile in a given mode.
+size_t per_sample_bytes(const cos_graph* g, int mode) {
+    size_t val = (mode == COS_MODE_FP32_MIXED) ? 4 : 8;
+    size_t gt = (mode == COS_MODE_COUNT_I64) ? 0 : val;
+    size_t fac = (mode == COS_MODE_COUNT_I64) ? 0 : 2 * sizeof(double) * (size_t)g->K * (size_t)g->D;
+    return 2 * val * (size_t)g->Wmax + gt * (size_t)g->P + fac;
+}
+
+size_t default_budget_bytes() {
+    const char* env = getenv("COS_WORKSPACE_MB");
+    if (env && atoll(env) > 0) return (size_t)atoll(env) << 20;
+    return (size_t)16 << 30;
+}
+
+int default_vec(int mode) { return mode == COS_MODE_FP32_MIXED ? 4 : 2; }
+
+// Carve the arena for one tile; returns false if it does not fit.
+bool carve(cos_graph* g, int mode, int64_t tile, WalkParams& p) {
+    size_t val = (mode == COS_MODE_FP32_MIXED) ? 4 : 8;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off += round_up((int64_t)bytes, 256);
+        return at;
+    };
+    size_t s0 = take(val * g->Wmax * tile);
+    size_t s1 = take(val * g->Wmax * tile);
+    size_t gt = 0, fm = 0, fp = 0, cf = 0;
+    if (mode != COS_MODE_COUNT_I64) {
+        gt = take(val * g->P * tile);
+        fm = take(sizeof(double) * g->K * g->D * tile);
+        fp = take(sizeof(double) * g->K * g->D * tile);
+        cf = take(sizeof(double) * 2 * g->K);
+    } else {
+        cf = take(sizeof(double) * 2 * g->K);
+    }
+    if (off > g->arena_bytes) return false;
+    char* base = (char*)g->d_arena;
+    p.slab[0] = base + s0;
+    p.slab[1] = base + s1;
+    p.gtab = (mode != COS_MODE_COUNT_I64) ? (void*)(base + gt) : nullptr;
+    p.fac_m = (mode != COS_MODE_COUNT_I64) ? (double*)(base + fm) : nullptr;
+    p.fac_p = (mode != COS_MODE_COUNT_I64) ? (double*)(base + fp) : nullptr;
+    p.coef = (double*)(base + cf);
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cos_last_error(void) { return g_last_error.c_str(); }
+
+int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64_t* level_edge_count,
+                     const int32_t* edges, int32_t num_kinds, int32_t num_times, cos_graph_t* out) {
+    if (!out) return fail(COS_ERR_INVALID, "out is NULL");
+    if (!level_width || !level_edge_count) return fail(COS_ERR_INVALID, "level arrays are NULL");
+    if (num_levels < 2) return fail(COS_ERR_INVALID, "num_levels must be >= 2 (got %d)", num_levels);
+    if (num_kinds < 1 || num_times < 1) return fail(COS_ERR_INVALID, "num_kinds and num_times must be >= 1");
+    if ((int64_t)num_kinds * num_times > (1LL << 24)) return fail(COS_ERR_INVALID, "num_kinds * num_times too large");
+    const int32_t L = num_levels;
+    std::vector<int64_t> off(L + 1, 0);
+    int64_t E = 0, Wmax = 0;
+    for (int32_t l = 0; l < L; ++l) {
+        if (level_width[l] < 1) return fail(COS_ERR_INVALID, "level %d has width %lld (must be >= 1)", l, (long long)level_width[l]);
+        if (level_edge_count[l] < 0) return fail(COS_ERR_INVALID, "level %d has a negative edge count", l);
+        off[l + 1] = off[l] + level_width[l];
+        E += level_edge_count[l];
+        Wmax = std::max(Wmax, level_width[l]);
+        if (off[l + 1] >= (1LL << 31) - 1 || E >= (1LL << 31) - 1)
+            return fail(COS_ERR_INVALID, "graph too large (N and E must be < 2^31)");
+    }
+    if (level_width[0] != 1 || level_width[L - 1] != 1)
+        return fail(COS_ERR_INVALID, "the first and last levels must have width 1 (root and sink)");
+    if (level_edge_count[0] != 0) return fail(COS_ERR_INVALID, "level 0 (root) cannot have in-edges");
+    if (E > 0 && !edges) return fail(COS_ERR_INVALID, "edges is NULL");
+    const int64_t N = off[L];
+
+    // Validate every edge against its level, and number the propagator slots.
+    const int64_t key_space = (int64_t)num_kinds * num_times * num_times;
+    const bool dense = key_space <= (1LL << 22);
+    std::vector<int32_t> dense_slot;
+    if (dense) dense_slot.assign((size_t)key_space, -1);
+    std::vector<int64_t> keys;
+    if (!dense) keys.reserve((size_t)E);
+    int64_t e0 = 0;
+    for (int32_t l = 1; l < L; ++l) {
+        for (int64_t q = e0; q < e0 + level_edge_count[l]; ++q) {
+            const int32_t* r = edges + 5 * q;
+            if (r[0] < off[l - 1] || r[0] >= off[l])
+                return fail(COS_ERR_INVALID, "edge %lld into level %d: src %d is not in level %d", (long long)q, l, r[0], l - 1);
+            if (r[1] < off[l] || r[1] >= off[l + 1])
+                return fail(COS_ERR_INVALID, "edge %lld into level %d: dst %d is not in level %d", (long long)q, l, r[1], l);
+            if (r[2] < 0 || r[2] >= num_kinds)
+                return fail(COS_ERR_INVALID, "edge %lld: kind %d out of range [0,%d)", (long long)q, r[2], num_kinds);
+            if (r[3] < 0 || r[3] >= num_times || r[4] < 0 || r[4] >= num_times)
+                return fail(COS_ERR_INVALID, "edge %lld: time index out of range [0,%d)", (long long)q, num_times);
+            int64_t key = ((int64_t)r[2] * num_times + r[3]) * num_times + r[4];
+            if (dense) dense_slot[(size_t)key] = 0;
+            else keys.push_back(key);
+        }
+        e0 += level_edge_count[l];
+    }
+    std::vector<int32_t> slot_kij;
+    int64_t P = 0;
+    if (dense) {
+        for (int64_t key = 0; key < key_space; ++key)
+            if (dense_slot[(size_t)key] == 0) dense_slot[(size_t)key] = (int32_t)P++;
+        slot_kij.resize((size_t)(3 * P));
+        for (int64_t key = 0; key < key_space; ++key) {
+            int32_t s = dense_slot[(size_t)key];
+            if (s < 0) continue;
+            slot_kij[3 * s + 0] = (int32_t)(key / ((int64_t)num_times * num_times));
+            slot_kij[3 * s + 1] = (int32_t)((key / num_times) % num_times);
+            slot_kij[3 * s + 2] = (int32_t)(key % num_times);
+        }
+    } else {
+        std::sort(keys.begin(), keys.end());
+        keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+        P = (int64_t)keys.size();
+        slot_kij.resize((size_t)(3 * P));
+        for (int64_t s = 0; s < P; ++s) {
+            int64_t key = keys[(size_t)s];
+            slot_kij[3 * s + 0] = (int32_t)(key / ((int64_t)num_times * num_times));
+            slot_kij[3 * s + 1] = (int32_t)((key / num_times) % num_times);
+            slot_kij[3 * s + 2] = (int32_t)(key % num_times);
+        }
+    }
+
+    // Per-level stable counting sort by destination: CSR rows in node-id order,
+    // in-edges of one node in input order.
+    std::vector<int32_t> row_ptr((size_t)N + 1, 0);
+    std::vector<int2> csr((size_t)E);
+    std::vector<int64_t> cnt;
+    e0 = 0;
+    for (int32_t l = 1; l < L; ++l) {
+        const int64_t W = level_width[l];
+        cnt.assign((size_t)W + 1, 0);
+        for (int64_t q = e0; q < e0 + level_edge_count[l]; ++q) cnt[(size_t)(edges[5 * q + 1] - off[l] + 1)]++;
+        for (int64_t r = 0; r < W; ++r) cnt[(size_t)r + 1] += cnt[(size_t)r];
+        for (int64_t r = 0; r < W; ++r) row_ptr[(size_t)(off[l] + r)] = (int32_t)(e0 + cnt[(size_t)r]);
+        for (int64_t q = e0; q < e0 + level_edge_count[l]; ++q) {
+            const int32_t* r = edges + 5 * q;
+            int64_t pos = e0 + cnt[(size_t)(r[1] - off[l])]++;
+            int64_t key = ((int64_t)r[2] * num_times + r[3]) * num_times + r[4];
+            int32_t slot = dense ? dense_slot[(size_t)key]
+                                 : (int32_t)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
+            csr[(size_t)pos] = make_int2((int32_t)(r[0] - off[l - 1]), slot);
+        }
+        e0 += level_edge_count[l];
+    }
+    row_ptr[(size_t)N] = (int32_t)E;   // (root row: row_ptr[0] = row_ptr[1] = 0)
+    row_ptr[0] = 0;
+
+    // Exact path count (unit weights), 128-bit with saturation, for the overflow flag.
+    std::vector<unsigned __int128> cexact((size_t)N, 0);
+    std::vector<uint64_t> cwrap((size_t)N, 0);
+    cexact[0] = 1;
+    cwrap[0] = 1;
+    const unsigned __int128 cap = ((unsigned __int128)1) << 120;
+    for (int32_t l = 1; l < L; ++l)
+        for (int64_t r = off[l]; r < off[l + 1]; ++r)
+            for (int32_t q = row_ptr[(size_t)r]; q < row_ptr[(size_t)r + 1]; ++q) {
+                int64_t src = off[l - 1] + csr[(size_t)q].x;
+                unsigned __int128 x = cexact[(size_t)r] + cexact[(size_t)src];
+                cexact[(size_t)r] = x > cap ? cap : x;
+                cwrap[(size_t)r] += cwrap[(size_t)src];
+            }
+
+    cos_graph* g = new (std::nothrow) cos_graph();
+    if (!g) return fail(COS_ERR_OOM, "host allocation failed");
+    g->L = L; g->K = num_kinds; g->D = num_times; g->N = N; g->E = E; g->P = P; g->Wmax = Wmax;
+    g->widths.assign(level_width, level_width + L);
+    g->ecount.assign(level_edge_count, level_edge_count + L);
+    g->off = off;
+    g->count_wrapped = (int64_t)cwrap[(size_t)N - 1];
+    g->count_overflow = cexact[(size_t)N - 1] > (unsigned __int128)INT64_MAX;
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        delete g;
+        return fail(COS_ERR_CUDA, "no CUDA device");
+    }
+    std::vector<LevelDesc> lv((size_t)L);
+    for (int32_t l = 0; l < L; ++l) {
+        lv[(size_t)l].row_begin = (int32_t)off[l];
+        lv[(size_t)l].width = (int32_t)level_width[l];
+        lv[(size_t)l].prev_width = l ? (int32_t)level_width[l - 1] : 0;
+        lv[(size_t)l].pad = 0;
+    }
+    auto cleanup_fail = [&](cudaError_t e, const char* what) {
+        int rc = cuda_fail(e, what);
+        cos_destroy(g);
+        return rc;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&g->d_levels, sizeof(LevelDesc) * L)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc levels");
+    if ((e = cudaMalloc(&g->d_row_ptr, sizeof(int32_t) * (N + 1))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc row_ptr");
+    if ((e = cudaMalloc(&g->d_edges, sizeof(int2) * std::max<int64_t>(E, 1))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc edges");
+    if ((e = cudaMalloc(&g->d_slot_kij, sizeof(int32_t) * std::max<int64_t>(3 * P, 3))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc slots");
+    if ((e = cudaMalloc(&g->d_ctrl, sizeof(Ctrl))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc ctrl");
+    if ((e = cudaMemcpy(g->d_levels, lv.data(), sizeof(LevelDesc) * L, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy levels");
+    if ((e = cudaMemcpy(g->d_row_ptr, row_ptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy row_ptr");
+    if (E && (e = cudaMemcpy(g->d_edges, csr.data(), sizeof(int2) * E, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy edges");
+    if (P && (e = cudaMemcpy(g->d_slot_kij, slot_kij.data(), sizeof(int32_t) * 3 * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy slots");
+    if ((e = cudaMemset(g->d_ctrl, 0, sizeof(Ctrl))) != cudaSuccess) return cleanup_fail(e, "memset ctrl");
+    *out = g;
+    return COS_OK;
+}
+
+int cos_destroy(cos_graph_t g) {
+    if (!g) return COS_OK;
+    {
+        DeviceGuard dg(g->device);
+        dfree(g->d_levels);
+        dfree(g->d_row_ptr);
+        dfree(g->d_edges);
+        dfree(g->d_slot_kij);
+        dfree(g->d_ctrl);
+        dfree(g->d_t);
+        dfree(g->d_eps);
+        dfree(g->d_stage);
+        if (g->d_arena) cudaFree(g->d_arena);
+        g->d_arena = nullptr;
+        dfree(g->d_partials);
+        if (g->d_R) cudaFree(g->d_R);
+        g->d_R = nullptr;
+    }
+    delete g;
+    return COS_OK;
+}
+
+int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n) {
+    if (!g || !info || n < 0) return fail(COS_ERR_INVALID, "bad arguments");
+    const int64_t v[10] = {g->L, g->N, g->E, g->P, g->Wmax, g->count_wrapped, g->count_overflow ? 1 : 0,
+                           g->K, g->D, g->device};
+    for (int32_t q = 0; q < n && q < 10; ++q) info[q] = v[q];
+    return COS_OK;
+}
+
+int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
+    if (!g || !t) return fail(COS_ERR_INVALID, "bad arguments");
+    if (t->samples_per_lane > 0 && t->samples_per_lane != 1 && t->samples_per_lane != 2 && t->samples_per_lane != 4)
+        return fail(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
+    if (t->rows_per_warp > 64) return fail(COS_ERR_INVALID, "rows_per_warp must be <= 64");
+    if (t->blocks_per_sm > 32) return fail(COS_ERR_INVALID, "blocks_per_sm must be <= 32");
+    g->tuning = *t;
+    return COS_OK;
+}
+
+static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* tile_out) {
+    cos_tuning t = g->tuning;
+    if (t.samples_per_lane <= 0) t.samples_per_lane = default_vec(mode);
+    if (t.rows_per_warp <= 0) t.rows_per_warp = 1;
+    if (t.timeout_ms <= 0) {
+        const char* env = getenv("COS_TIMEOUT_MS");
+        t.timeout_ms = (env && atoi(env) > 0) ? atoi(env) : 10000;
+    }
+    int dev_max = max_coresident_blocks(mode, t.samples_per_lane, g->device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (dev_max <= 0 || sms <= 0) return fail(COS_ERR_CUDA, "cannot query occupancy of the walker kernel");
+    int per_sm = dev_max / sms;
+    if (t.blocks_per_sm <= 0 || t.blocks_per_sm > per_sm) t.blocks_per_sm = per_sm;
+    const int64_t ch = 32LL * t.samples_per_lane;
+    int64_t need = std::max<int64_t>(round_up(std::max<int64_t>(g->S, 1), ch), ch);
+    int64_t tile;
+    if (t.tile_samples > 0) {
+        tile = round_up(t.tile_samples, ch);
+    } else {
+        size_t psb = per_sample_bytes(g, mode);
+        const size_t slack = (size_t)4 << 20;   // alignment padding and coefficients
+        int64_t fit = g->arena_bytes > slack ? (int64_t)((g->arena_bytes - slack) / (psb + 1)) : 0;
+        tile = std::max<int64_t>(ch, fit / ch * ch);
+        tile = std::min<int64_t>(tile, 65536);
+    }
+    tile = std::min(tile, need);
+    t.tile_samples = (int32_t)tile;
+    *out = t;
+    *tile_out = tile;
+    return COS_OK;
+}
+
+int cos_get_tuning(cos_graph_t g, int32_t mode, cos_tuning* tuning) {
+    if (!g || !tuning) return fail(COS_ERR_INVALID, "bad arguments");
+    if (mode < 0 || mode > 2) return fail(COS_ERR_INVALID, "bad mode %d", mode);
+    int64_t tile;
+    return resolve_tuning(g, mode, tuning, &tile);
+}
+
+int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t t_flags, const double* eps,
+                    double beta, void* stream) {
+    if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
+    if (num_samples < 0) return fail(COS_ERR_INVALID, "num_samples must be >= 0");
+    if (num_samples > 0 && !t) return fail(COS_ERR_INVALID, "t is NULL");
+    if (!eps) return fail(COS_ERR_INVALID, "eps is NULL");
+    if (t_flags & ~(COS_T_HOST | COS_T_SAMPLE_MAJOR)) return fail(COS_ERR_INVALID, "unknown t_flags bits");
+    if (!(beta > 0.0) || !std::isfinite(beta)) return fail(COS_ERR_INVALID, "beta must be positive and finite");
+    for (int32_t k = 0; k < g->K; ++k)
+        if (!std::isfinite(eps[k]) || std::fabs(eps[k]) * beta > 600.0)
+            return fail(COS_ERR_INVALID, "eps[%d] * beta must be finite with magnitude <= 600", k);
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(COS_ERR_CUDA, "cannot select device %d", g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t S = num_samples;
+    const int64_t t_ld = std::max<int64_t>(round_up(S, 128), 128);
+    const int32_t D = g->D;
+    if (t_ld * D > g->t_cap) {
+        dfree(g->d_t);
+        COS_CUDA(cudaMalloc(&g->d_t, sizeof(double) * t_ld * D), "cudaMalloc t");
+        g->t_cap = t_ld * D;
+    }
+    if (!g->d_eps) COS_CUDA(cudaMalloc(&g->d_eps, sizeof(double) * g->K), "cudaMalloc eps");
+    const int64_t nblk = std::max<int64_t>((S + kReduceBlock - 1) / kReduceBlock, 1);
+    if (nblk > g->partial_cap) {
+        dfree(g->d_partials);
+        COS_CUDA(cudaMalloc(&g->d_partials, sizeof(double) * nblk), "cudaMalloc partials");
+        g->partial_cap = nblk;
+    }
+    if (std::max<int64_t>(S, 1) > g->R_cap) {
+        if (g->d_R) cudaFree(g->d_R);
+        g->d_R = nullptr;
+        COS_CUDA(cudaMalloc(&g->d_R, sizeof(double) * std::max<int64_t>(S, 1)), "cudaMalloc R");
+        g->R_cap = std::max<int64_t>(S, 1);
+    }
+    // Workspace arena: enough for the FP64 mode over all samples, up to the budget.
+    {
+        size_t psb = std::max(per_sample_bytes(g, COS_MODE_FP64), per_sample_bytes(g, COS_MODE_FP32_MIXED));
+        size_t want = psb * (size_t)std::max<int64_t>(round_up(std::max<int64_t>(S, 1), 128), 128) + ((size_t)8 << 20);
+        size_t budget = default_budget_bytes();
+        size_t minimum = psb * 128 + ((size_t)8 << 20);
+        size_t bytes = std::max(std::min(want, budget), minimum);
+        if (g->tuning.tile_samples > 0)
+            bytes = std::max(bytes, psb * (size_t)round_up(g->tuning.tile_samples, 128) + ((size_t)8 << 20));
+        if (bytes > g->arena_bytes) {
+            if (g->d_arena) cudaFree(g->d_arena);
+            g->d_arena = nullptr;
+            g->arena_bytes = 0;
+            COS_CUDA(cudaMalloc(&g->d_arena, bytes), "cudaMalloc workspace");
+            g->arena_bytes = bytes;
+        }
+    }
+    COS_CUDA(cudaMemcpyAsync(g->d_eps, eps, sizeof(double) * g->K, cudaMemcpyHostToDevice, st), "copy eps");
+    COS_CUDA(cudaMemsetAsync(g->d_t, 0, sizeof(double) * t_ld * D, st), "clear t");
+    if (S > 0) {
+        const bool host = (t_flags & COS_T_HOST) != 0;
+        const bool smaj = (t_flags & COS_T_SAMPLE_MAJOR) != 0;
+        if (!smaj) {
+            COS_CUDA(cudaMemcpy2DAsync(g->d_t, sizeof(double) * t_ld, t, sizeof(double) * S, sizeof(double) * S, D,
+                                       host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st),
+                     "copy t");
+        } else {
+            const double* src = t;
+            if (host) {
+                if (S * D > g->stage_cap) {
+                    dfree(g->d_stage);
+                    COS_CUDA(cudaMalloc(&g->d_stage, sizeof(double) * S * D), "cudaMalloc staging");
+                    g->stage_cap = S * D;
+                }
+                COS_CUDA(cudaMemcpyAsync(g->d_stage, t, sizeof(double) * S * D, cudaMemcpyHostToDevice, st), "copy t");
+                src = g->d_stage;
+            }
+            int rc = launch_transpose(src, S, D, g->d_t, t_ld, st);
+            if (rc != COS_OK) return fail(rc, "transpose launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+    }
+    g->S = S;
+    g->t_ld = t_ld;
+    g->beta = beta;
+    g->has_samples = true;
+    return COS_OK;
+}
+
+static int collect(cos_graph_t g, double* mean_out, cudaStream_t st) {
+    Ctrl c;
+    COS_CUDA(cudaMemcpyAsync(&c, g->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "read result");
+    COS_CUDA(cudaStreamSynchronize(st), "synchronize");
+    g->last_status_pending = 0;
+    if (c.err == KERR_BARRIER_TIMEOUT) return fail(COS_ERR_TIMEOUT, "grid barrier timed out (phase %d)", c.err_detail);
+    if (c.err != 0) return fail(COS_ERR_CUDA, "kernel reported error %d", c.err);
+    if (mean_out) *mean_out = c.mean;
+    if (g->last_mode == COS_MODE_COUNT_I64 && g->count_overflow)
+        return fail(COS_ERR_OVERFLOW, "path count exceeds 2^63-1; results wrap modulo 2^64");
+    return COS_OK;
+}
+
+int cos_evaluate(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean_out, void* stream) {
+    if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
+    if (mode < 0 || mode > 2) return fail(COS_ERR_INVALID, "bad mode %d", mode);
+    if (!g->has_samples) return fail(COS_ERR_STATE, "cos_set_samples has not been called");
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(COS_ERR_CUDA, "cannot select device %d", g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cos_tuning tn;
+    int64_t tile;
+    int rc = resolve_tuning(g, mode, &tn, &tile);
+    if (rc != COS_OK) return rc;
+    WalkParams p;
+    memset(&p, 0, sizeof(p));
+    if (!carve(g, mode, tile, p)) return fail(COS_ERR_STATE, "workspace too small for a tile of %lld samples", (long long)tile);
+    p.levels = g->d_levels;
+    p.row_ptr = g->d_row_ptr;
+    p.edges = g->d_edges;
+    p.slot_kij = g->d_slot_kij;
+    p.L = g->L;
+    p.P = (int32_t)g->P;
+    p.K = g->K;
+    p.D = g->D;
+    p.t = g->d_t;
+    p.eps = g->d_eps;
+    p.beta = g->beta;
+    p.S = g->S;
+    p.t_ld = g->t_ld;
+    p.R = per_sample_out ? per_sample_out : g->d_R;
+    p.partials = g->d_partials;
+    p.ctrl = g->d_ctrl;
+    p.tile = tile;
+    p.rows_per_warp = tn.rows_per_warp;
+    p.timeout_ns = (long long)tn.timeout_ms * 1000000LL;
+    if (const char* env = getenv("COS_TEST_SKIP_BARRIER_PHASE")) p.skip_barrier_phase = atoi(env);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    const int grid = sms * tn.blocks_per_sm;
+    COS_CUDA(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), st), "reset control block");
+    char msg[256] = {0};
+    rc = launch_walk(mode, tn.samples_per_lane, p, grid, st, msg, sizeof(msg));
+    if (rc != COS_OK) return fail(rc, "walker launch failed: %s", msg);
+    g->last_mode = mode;
+    g->last_status_pending = 1;
+    if (mean_out) return collect(g, mean_out, st);
+    return COS_OK;
+}
+
+int cos_get_result(cos_graph_t g, double* mean_out, void* stream) {
+    if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
+    DeviceGuard dg(g->device);
+    return collect(g, mean_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

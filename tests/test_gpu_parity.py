@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (per sample s, relative to the oracle's sum of |path| values A(s)):
+  FP64 mode       |R_gpu - R_oracle| <= 1e-12 * A
+  FP32 mixed mode |R_gpu - R_oracle| <= 1e-5  * A
+  count mode      bit-exact int64
+The mean over samples is held to the same bound relative to mean(A).
+"""
+import math
+import os
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from workloads import (FaninSpec, chain_graph, complete_layered_graph, figure_graph, large, make_graph,  # noqa: E402
+                       medium, tiny)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_00675_gb300 as cg
+    from paper_2501_00675_gb300 import _build
+    _build.build()
+    cg.load_library()
+    return cg
+
+
+def run_gpu(cg, g, eps, beta, t, mode, tuning=None, layout="device_sd"):
+    """Evaluate through the C ABI; returns (per-sample results as numpy, mean)."""
+    gr = cg.Graph.from_workload_graph(g)
+    if tuning:
+        gr.set_tuning(**tuning)
+    S = t.shape[0]
+    if layout == "device_sd":
+        tt = torch.from_numpy(np.ascontiguousarray(t)).cuda()
+        flags = cg.COS_T_SAMPLE_MAJOR
+    elif layout == "device_ds":
+        tt = torch.from_numpy(np.ascontiguousarray(t.T)).cuda()
+        flags = cg.COS_T_DEVICE_DS
+    elif layout == "host_sd":
+        tt = torch.from_numpy(np.ascontiguousarray(t)).pin_memory()
+        flags = cg.COS_T_HOST | cg.COS_T_SAMPLE_MAJOR
+    elif layout == "host_ds":
+        tt = np.ascontiguousarray(t.T)
+        flags = cg.COS_T_HOST
+    else:
+        raise ValueError(layout)
+    gr.set_samples(tt, eps, beta, flags, num_samples=S)
+    dt = torch.int64 if mode == cg.COS_MODE_COUNT_I64 else torch.float64
+    out = torch.full((max(S, 1),), -7, dtype=dt, device="cuda")
+    mean = gr.evaluate(mode, out=out[:S] if S else None, allow_overflow=True)
+    torch.cuda.synchronize()
+    res = out[:S].cpu().numpy()
+    gr.close()
+    return res, mean
+
+
+def check_fp(R_gpu, mean_gpu, R, A, mode, idx=None):
+    tol = TOL[mode]
+    if idx is not None:
+        R_gpu = R_gpu[idx]
+    err = np.abs(R_gpu - R)
+    bad = err > tol * A
+    assert not bad.any(), f"max err/A = {np.max(err / np.where(A > 0, A, 1)):.3e} at {np.nonzero(bad)[0][:5]}"
+    if idx is None and R.size:
+        assert abs(mean_gpu - oracle.neumaier_mean(R)) <= tol * float(np.mean(A)) + 1e-300
+
+
+# ------------------------------------------------------------------ tiny (full)
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tiny_parity(cg, mode):
+    w = tiny()
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode)
+    check_fp(Rg, mg, R, A, mode)
+
+
+def test_tiny_count_bit_exact(cg):
+    w = tiny()
+    cnt, ovf = oracle.count_paths(w.graph)
+    Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 2)
+    assert not ovf and np.all(Rg == cnt) and mg == float(cnt)
+
+
+def test_figure_graph_count(cg):
+    g = figure_graph()
+    t = np.random.default_rng(0).uniform(0, 10, (70, 1))
+    Rg, _ = run_gpu(cg, g, np.array([0.3]), 10.0, t, 2)
+    assert np.all(Rg == 6)
+
+
+# ------------------------------------------------------------------ medium
+
+def test_medium_multi_tile_ragged_fp64(cg):
+    w = medium(num_samples=5000)
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    for tuning in ({"tile_samples": 1024}, {"tile_samples": 640, "samples_per_lane": 1}):
+        Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 0, tuning)
+        check_fp(Rg, mg, R, A, 0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_medium_full_size_sampled(cg, mode):
+    w = medium()
+    S = w.samples.num_samples
+    idx = np.unique(np.r_[0, 1, 31, 32, 4095, 4096, np.random.default_rng(5).integers(0, S, 120), S - 2, S - 1])
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[idx])
+    Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode)
+    check_fp(Rg, mg, R, A, mode, idx=idx)
+    # the mean against the full-sample mean is checked by the multi-tile test; here check it is finite
+    assert math.isfinite(mg)
+
+
+def test_medium_count_bit_exact(cg):
+    w = medium(num_samples=777)
+    cnt, ovf = oracle.count_paths(w.graph)
+    Rg, _ = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 2)
+    assert not ovf and np.all(Rg == cnt)
+
+
+# ------------------------------------------------------------------ large (sampled)
+
+def test_large_mixed_sampled(cg):
+    w = large()
+    S = w.samples.num_samples
+    idx = np.unique(np.r_[0, 127, 128, np.random.default_rng(6).integers(0, S, 40), S - 1])
+    t0 = time.time()
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[idx])
+    print(f"oracle {len(idx)} samples: {time.time() - t0:.1f}s")
+    Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 1)
+    check_fp(Rg, mg, R, A, 1, idx=idx)
+    cnt, ovf = oracle.count_paths(w.graph)
+    assert np.all(np.abs(R) <= A) and np.all(A <= cnt)
+
+
+# ------------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("S", [1, 2, 31, 33, 129, 4097])
+def test_ragged_sample_counts(cg, S):
+    w = tiny(num_samples=S)
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    for mode in (0, 1):
+        Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode)
+        check_fp(Rg, mg, R, A, mode)
+
+
+def test_zero_samples(cg):
+    w = tiny(num_samples=0)
+    Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 0)
+    assert Rg.size == 0 and mg == 0.0
+
+
+def test_two_level_graph_and_chain(cg):
+    g = chain_graph([0], [0], [1], 1, 2)          # L = 2: root -> sink
+    t = np.random.default_rng(1).uniform(0, 10, (50, 2))
+    eps = np.array([0.7])
+    R, A = oracle.evaluate(g, eps, 10.0, t)
+    for mode in (0, 1):
+        Rg, mg = run_gpu(cg, g, eps, 10.0, t, mode)
+        check_fp(Rg, mg, R, A, mode)
+    g = chain_graph([0, 1, 1, 0, 1, 0, 1, 1, 0], [0, 1, 2, 2, 0, 1, 2, 0, 1], [1, 2, 0, 2, 1, 1, 0, 0, 2], 2, 3)
+    t = np.random.default_rng(2).uniform(0, 10, (300, 3))
+    eps = np.array([1.3, -1.7])
+    R, A = oracle.evaluate(g, eps, 10.0, t)
+    for mode in (0, 1):
+        Rg, mg = run_gpu(cg, g, eps, 10.0, t, mode)
+        check_fp(Rg, mg, R, A, mode)
+
+
+def test_wide_fanin_duplicates_dead_and_orphan_nodes(cg):
+    rng = np.random.default_rng(3)
+    # complete levels give fan-in 40 (> one warp of in-edges); then add duplicates, an orphan node
+    g = complete_layered_graph([1, 5, 40, 40, 7, 1], num_kinds=3, num_times=4, rng=rng)
+    e = g.edges.tolist()
+    off = g.offsets()
+    counts = g.edge_counts.copy()
+    lvl = np.repeat(np.arange(g.num_levels), counts)
+    extra = [row for row, l in zip(e, lvl) if l == 3][:10]       # duplicate (src, dst) pairs into level 3
+    e3_end = int(counts[:4].sum())
+    e = e[:e3_end] + extra + e[e3_end:]
+    counts[3] += len(extra)
+    # orphan: drop every in-edge of the first node of level 4
+    orphan = off[4]
+    keep = [row for row in e if row[1] != orphan]
+    counts[4] -= len(e) - len(keep)
+    e = np.array(keep, dtype=np.int32)
+    from workloads import Graph
+    g2 = Graph(g.widths, counts, e, 3, 4)
+    t = rng.uniform(0, 10, (200, 4))
+    t[:, 2] = t[:, 3]                                               # tau == 0 for (2,3) and (3,2) pairs
+    eps = rng.uniform(-2, 2, 3)
+    R, A = oracle.evaluate(g2, eps, 10.0, t)
+    for mode in (0, 1):
+        Rg, mg = run_gpu(cg, g2, eps, 10.0, t, mode)
+        check_fp(Rg, mg, R, A, mode)
+    cnt, _ = oracle.count_paths(g2)
+    Rg, _ = run_gpu(cg, g2, eps, 10.0, t, 2)
+    assert np.all(Rg == cnt)
+
+
+def test_count_overflow_reports_and_wraps(cg):
+    g = complete_layered_graph([1] + [256] * 8 + [1])
+    cnt, ovf = oracle.count_paths(g)
+    assert ovf
+    gr = cg.Graph.from_workload_graph(g)
+    assert gr.info()["count_overflow"] == 1 and gr.info()["count"] == cnt
+    t = torch.zeros((64, 1), dtype=torch.float64, device="cuda")
+    gr.set_samples(t, np.array([0.0]), 10.0, cg.COS_T_SAMPLE_MAJOR)
+    out = torch.empty(64, dtype=torch.int64, device="cuda")
+    with pytest.raises(cg.CosError) as ei:
+        gr.evaluate(cg.COS_MODE_COUNT_I64, out=out)
+    assert ei.value.code == cg.COS_ERR_OVERFLOW
+    assert np.all(out.cpu().numpy() == cnt)
+    gr.close()
+
+
+# ------------------------------------------------------------------ invariances
+
+def test_results_independent_of_launch_shape(cg):
+    w = medium(num_samples=3000)
+    ref = None
+    for tuning in ({}, {"samples_per_lane": 1}, {"samples_per_lane": 4, "tile_samples": 512},
+                   {"samples_per_lane": 2, "rows_per_warp": 4, "blocks_per_sm": 1}):
+        for mode in (0, 1):
+            Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode, tuning)
+            if ref is None:
+                ref = {}
+            if mode in ref:
+                np.testing.assert_array_equal(Rg, ref[mode][0])      # bitwise: same per-row order
+                assert mg == ref[mode][1]
+            else:
+                ref[mode] = (Rg, mg)
+
+
+@pytest.mark.parametrize("layout", ["device_ds", "host_sd", "host_ds"])
+def test_sample_input_layouts(cg, layout):
+    w = tiny(num_samples=300)
+    a, ma = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 0, layout="device_sd")
+    b, mb = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 0, layout=layout)
+    np.testing.assert_array_equal(a, b)
+    assert ma == mb
+
+
+def test_repeat_and_reuse_handle(cg):
+    w = tiny(num_samples=500)
+    gr = cg.Graph.from_workload_graph(w.graph)
+    t = torch.from_numpy(w.samples.t).cuda()
+    gr.set_samples(t, w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+    outs = []
+    for _ in range(3):
+        o = torch.empty(500, dtype=torch.float64, device="cuda")
+        gr.evaluate(0, out=o)
+        outs.append(o.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    # new samples on the same handle
+    t2 = torch.from_numpy(w.samples.t[::-1].copy()).cuda()
+    gr.set_samples(t2, w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+    o = torch.empty(500, dtype=torch.float64, device="cuda")
+    gr.evaluate(0, out=o)
+    np.testing.assert_array_equal(o.cpu().numpy(), outs[0][::-1])
+    gr.close()
+
+
+def test_evaluate_before_samples_is_state_error(cg):
+    gr = cg.Graph.from_workload_graph(tiny().graph)
+    with pytest.raises(cg.CosError) as ei:
+        gr.evaluate(0)
+    assert ei.value.code == cg.COS_ERR_STATE
+    gr.close()
+
+
+def test_barrier_timeout_is_reported_and_context_survives(cg, monkeypatch):
+    # One CTA leaves before the first level barrier; the others' bounded waits run
+    # out and the launch ends with COS_ERR_TIMEOUT.  No GPU fault is involved.
+    w = tiny(num_samples=256)
+    gr = cg.Graph.from_workload_graph(w.graph)
+    gr.set_tuning(timeout_ms=200)
+    t = torch.from_numpy(w.samples.t).cuda()
+    gr.set_samples(t, w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+    monkeypatch.setenv("COS_TEST_SKIP_BARRIER_PHASE", "3")
+    t0 = time.time()
+    with pytest.raises(cg.CosError) as ei:
+        gr.evaluate(0)
+    assert ei.value.code == cg.COS_ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    monkeypatch.delenv("COS_TEST_SKIP_BARRIER_PHASE")
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    o = torch.empty(256, dtype=torch.float64, device="cuda")
+    m = gr.evaluate(0, out=o)
+    check_fp(o.cpu().numpy(), m, R, A, 0)
+    gr.close()
