@@ -152,6 +152,56 @@ typedef struct cos_tuning {
 int cos_set_tuning(cos_graph_t g, const cos_tuning* tuning);
 int cos_get_tuning(cos_graph_t g, int32_t mode, cos_tuning* tuning);
 
+/*
+ * cos_evaluate_static -- evaluate an existing graph without allocating device memory.
+ *
+ * The paper has no counterpart; this entry point exists for callers that cannot
+ * call cudaMalloc when they evaluate: code running while its stream is being
+ * captured into a CUDA graph, latency-bound serving loops that cannot afford an
+ * allocation or the device-wide synchronisation cudaFree may imply, and host
+ * applications whose own memory manager owns the device budget.  Such callers
+ * create the graph once at set-up time (cos_create_graph allocates) and then
+ * call this function with their own device buffers for the times and results.
+ *
+ * Scratch memory.  All working memory of the evaluation (node-value slabs of one
+ * tile of samples, propagator table, exponential factors, partial sums, the grid
+ * barrier counter and the result) lives in one file-scope __device__ array of
+ * COS_STATIC_SCRATCH_BYTES (64 MiB) inside the library; every GPU that loads the
+ * library holds it until the process exits.  The function calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The control block is cleared on every
+ * call; the rest keeps the last call's contents and is overwritten before use.
+ * Every call on a device shares the one array, so calls whose execution overlaps
+ * on the GPU (different streams, or host threads) race and give wrong results:
+ * serialise them.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, which may load the module); make that first call before
+ * any stream capture begins.
+ *
+ * Limits.  The tile of samples is sized to fit the array; a graph whose working
+ * set for 32 samples exceeds it (roughly 2 * W_max * w + P * w + 16 * K * D bytes
+ * per sample, w = 8 in FP64 and count modes, 4 in FP32 mixed mode) is rejected
+ * with COS_ERR_INVALID, as is a sample count whose partial sums do not fit.
+ *
+ *   g               graph from cos_create_graph; its device must be current
+ *   mode            cos_mode
+ *   num_samples     S >= 0
+ *   t               device, layout [D][t_ld] (sample index fastest); t_ld >= S
+ *                   rounded up to a multiple of 128; the padding columns are
+ *                   read (must be finite) but do not affect any result
+ *   eps             device, [K] doubles
+ *   beta            inverse temperature (> 0)
+ *   per_sample_out  device, double[S] (FP64, FP32_MIXED) or int64[S] (COUNT_I64);
+ *                   required when S > 0
+ *   mean_out        host pointer or NULL; as in cos_evaluate (non-NULL waits for
+ *                   the stream and reports kernel-side errors)
+ *   stream          cudaStream_t as void*
+ * Results equal those of cos_evaluate on the same samples (the per-sample sums
+ * do not depend on the tile size).  Errors: as cos_evaluate, plus
+ * COS_ERR_INVALID for the size limits above.
+ */
+#define COS_STATIC_SCRATCH_BYTES (64LL * 1024 * 1024)
+int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samples, const double* t, int64_t t_ld,
+                        const double* eps, double beta, void* per_sample_out, double* mean_out, void* stream);
+
 /* Free every device and host resource of the handle (NULL is accepted). */
 int cos_destroy(cos_graph_t g);
 

@@ -33,7 +33,7 @@ COS_T_HOST = 1
 COS_T_SAMPLE_MAJOR = 2
 
 EXPORTED = ["cos_create_graph", "cos_set_samples", "cos_evaluate", "cos_get_result", "cos_graph_info",
-            "cos_set_tuning", "cos_get_tuning", "cos_destroy", "cos_last_error"]
+            "cos_set_tuning", "cos_get_tuning", "cos_evaluate_static", "cos_destroy", "cos_last_error"]
 
 _lock = threading.Lock()
 _lib = None
@@ -78,6 +78,7 @@ def load_library(build_if_missing: bool = False):
         lib.cos_graph_info.argtypes = [vp, vp, i32]
         lib.cos_set_tuning.argtypes = [vp, ctypes.POINTER(CosTuning)]
         lib.cos_get_tuning.argtypes = [vp, i32, ctypes.POINTER(CosTuning)]
+        lib.cos_evaluate_static.argtypes = [vp, i32, i64, vp, i64, vp, f64, vp, vp, vp]
         lib.cos_destroy.argtypes = [vp]
         lib.cos_last_error.restype = ctypes.c_char_p
         lib.cos_last_error.argtypes = []

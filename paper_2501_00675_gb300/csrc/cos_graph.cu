@@ -537,3 +537,33 @@ int cos_get_result(cos_graph_t g, double* mean_out, void* stream) {
 }
 
 }  // extern "C"
+
+namespace cosgpu {
+
+int graph_view(cos_graph_t g, GraphView* out) {
+    if (!g || !out) return fail(COS_ERR_INVALID, "graph is NULL");
+    out->levels = g->d_levels;
+    out->row_ptr = g->d_row_ptr;
+    out->edges = g->d_edges;
+    out->slot_kij = g->d_slot_kij;
+    out->L = g->L;
+    out->P = (int32_t)g->P;
+    out->K = g->K;
+    out->D = g->D;
+    out->Wmax = g->Wmax;
+    out->device = g->device;
+    out->count_overflow = g->count_overflow ? 1 : 0;
+    return COS_OK;
+}
+
+int set_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+}  // namespace cosgpu

@@ -67,6 +67,22 @@ constexpr int kThreads = 256;           // 8 warps per CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kReduceBlock = 4096;      // samples per compensated partial sum
 
+// Device-resident view of a graph handle (read-only), for entry points that
+// evaluate an existing graph with scratch memory of their own.
+struct GraphView {
+    const LevelDesc* levels;
+    const int32_t* row_ptr;
+    const int2* edges;
+    const int32_t* slot_kij;
+    int32_t L, P, K, D;
+    int64_t Wmax;
+    int device;
+    int count_overflow;
+};
+int graph_view(cos_graph_t g, GraphView* out);
+// Records a message for cos_last_error() and returns code.
+int set_error(int code, const char* fmt, ...);
+
 // Host launcher implemented in cos_walk.cu.  Returns COS_OK or COS_ERR_CUDA and
 // fills msg on failure.
 int launch_walk(int mode, int vec, const WalkParams& p, int grid, cudaStream_t stream, char* msg, size_t msglen);
