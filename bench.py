@@ -55,7 +55,13 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="medium")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving"], default="medium")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--pool-size", type=int, default=128, help="serving: resident graphs")
+    ap.add_argument("--max-nodes", type=float, default=2e6, help="serving: largest graph")
+    ap.add_argument("--max-queue", type=int, default=256, help="serving: bounded wait queue (excess is shed)")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: device memory budget")
     ap.add_argument("--mode", choices=sorted(MODES), default=None)
     ap.add_argument("--samples", type=int, default=None, help="samples per GPU (default: the workload's)")
     ap.add_argument("--tuning", type=str, default="", help="JSON dict passed to cos_set_tuning")
@@ -330,6 +336,57 @@ def run_ours(args, rank, world, local):
     return line
 
 
+# ------------------------------------------------------------------ serving
+
+def run_serving(args, rank, world, local):
+    """Poisson request stream against the resident pool: continuous batching in the
+    FP32/FP64-mixed mode next to one-request-at-a-time plain FP64."""
+    import torch
+    import paper_2501_00675_gb300 as cg
+    from paper_2501_00675_gb300.serve import RequestSpec, Server, latency_summary, poisson_run
+    from workloads import serving_pool
+
+    torch.cuda.set_device(local)
+    cg.load_library(build_if_missing=True)
+    t0 = time.perf_counter()
+    pool = [(cg.Graph.from_workload_graph(g), eps) for g, eps in serving_pool(seed=4, pool_size=args.pool_size,
+                                                                               max_nodes=args.max_nodes)]
+    build_s = time.perf_counter() - t0
+    rng = np.random.default_rng(1234 + rank)
+    n_spec = int(args.rate * args.duration * 1.2) + 16
+    gids = rng.integers(0, len(pool), n_spec)
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(1e6), n_spec)).astype(np.int64)
+    specs = [RequestSpec(int(g), int(sz), 10_000 + q) for q, (g, sz) in enumerate(zip(gids, sizes))]
+    budget = int(args.budget_gb * (1 << 30))
+    out = {}
+    for name, kw in (("batched_mixed", dict(mode=cg.COS_MODE_FP32_MIXED, max_batch=64, streams=2)),
+                     ("plain_fp64", dict(mode=cg.COS_MODE_FP64, single=True))):
+        srv = Server(pool, budget_bytes=budget, max_queue=args.max_queue, **kw)
+        reqs, wall = poisson_run(srv, specs, rate_per_s=args.rate, duration_s=args.duration, seed=rank)
+        summ = latency_summary(reqs)
+        summ.update({"offered": len(reqs), "shed": int(sum(r.status == "shed" for r in reqs)),
+                     "failed": int(sum(r.status == "failed" for r in reqs)), "wall_s": wall,
+                     "edge_sample_updates_per_s": srv.units_done / wall,
+                     "peak_admitted_gb": srv.ctrl.peak / (1 << 30)})
+        out[name] = summ
+        srv.close()
+    for g, _ in pool:
+        g.close()
+    if rank != 0:
+        return None
+    b = out["batched_mixed"]
+    return {
+        "metric": "served edge·sample updates/s", "value": b["edge_sample_updates_per_s"],
+        "unit": "edge·sample updates/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (sink and sample sums f64)", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson {args.rate:g} req/s for {args.duration:g} s; pool of "
+                               f"{args.pool_size} leveled DAGs, N logU[1e3,{args.max_nodes:g}], geometric fan-in "
+                               f"1..6, K=32, D=L; samples per request logU[1e3,1e6]; budget {args.budget_gb:g} GB; "
+                               f"queue bound {args.max_queue}", "pool_build_s": build_s},
+        "serving": out,
+    }
+
+
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
 
 def run_reference(args, rank, world):
@@ -385,7 +442,12 @@ def main(argv=None):
         else:
             dist.init_process_group(backend=backend)
     if args.impl == "reference":
-        line = run_reference(args, rank, world)
+        if args.workload == "serving":
+            line = {"impl": "reference", "unavailable": "the serving workload has no CPU reference arm"} if rank == 0 else None
+        else:
+            line = run_reference(args, rank, world)
+    elif args.workload == "serving":
+        line = run_serving(args, rank, world, local)
     else:
         line = run_ours(args, rank, world, local)
     if line is not None:

@@ -60,7 +60,10 @@ enum cos_mode {
 enum cos_t_flags {
     COS_T_DEVICE_DS = 0,      /* t is a device pointer, layout [D][S] (sample index fastest) */
     COS_T_HOST = 1,           /* t is a host pointer (page-locked memory gives an asynchronous copy) */
-    COS_T_SAMPLE_MAJOR = 2    /* layout [S][D] (time-variable index fastest) */
+    COS_T_SAMPLE_MAJOR = 2,   /* layout [S][D] (time-variable index fastest) */
+    COS_T_BORROW = 4          /* device [D][t_ld] buffer, t_ld = S rounded up to 128, used in place
+                                 without a copy: it must stay valid and unchanged until the last
+                                 evaluation of these samples has finished; padding must be finite */
 };
 
 /*
@@ -83,6 +86,16 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
                      const int32_t* edges, int32_t num_kinds, int32_t num_times, cos_graph_t* out);
 
 /*
+ * A second handle on the structure of `src` (levels, CSR, propagator slots stay
+ * on the device once, shared): the new handle has its own samples, workspace and
+ * results, so several sample sets of one resident graph can be evaluated
+ * concurrently (e.g. one per in-flight request).  The structure is freed with the
+ * last handle that uses it; handles may be destroyed in any order.
+ * Errors: COS_ERR_INVALID, COS_ERR_OOM, COS_ERR_CUDA.
+ */
+int cos_graph_share(cos_graph_t src, cos_graph_t* out);
+
+/*
  * Attach a batch of Monte Carlo samples (Sec. II.C "Distributing the task on a
  * grid of blocks": one evaluation per set of internal variables).
  *   num_samples S >= 0
@@ -92,7 +105,8 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
  *   beta     inverse temperature (> 0)
  *   stream   cudaStream_t (as void*) on which the copy is enqueued
  * Grows the graph's device workspace if needed (the only call besides
- * cos_create_graph that allocates).  The copy is asynchronous: a host t must
+ * cos_create_graph that allocates); a tile_samples tuning fixes the workspace
+ * to that many samples (set it before the first cos_set_samples).  The copy is asynchronous: a host t must
  * stay valid until the stream reaches this point.
  * Errors: COS_ERR_INVALID, COS_ERR_OOM, COS_ERR_CUDA.
  */
@@ -101,9 +115,9 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
 
 /*
  * Evaluate the path sum of every attached sample (Fig. 1; Sec. II.C): one
- * persistent cooperative kernel computes the propagator table, walks the levels
- * in order with a grid-wide barrier between levels, writes the sink value per
- * sample and reduces the samples.  Allocates nothing; may be captured in a CUDA
+ * persistent cooperative kernel computes, tile of samples by tile, the propagator
+ * table, walks the levels in order with a grid-wide barrier between levels,
+ * writes the sink value per sample, and finally reduces the samples.  Allocates nothing; may be captured in a CUDA
  * graph when mean_out is NULL.
  *   mode            cos_mode
  *   per_sample_out  device pointer or NULL: double[S] (FP64, FP32_MIXED) or
@@ -137,9 +151,12 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  * Launch shape used by cos_evaluate.  Fields <= 0 mean "automatic".
  *   samples_per_lane  1, 2 or 4 consecutive samples per thread (vector width)
  *   tile_samples      samples per tile (rounded up to 32 * samples_per_lane)
- *   rows_per_warp     destination rows one warp takes per work item
+ *   rows_per_warp     consecutive destination rows one warp takes per work item (<= 31)
  *   blocks_per_sm     persistent CTAs per SM (capped by occupancy)
  *   timeout_ms        grid-barrier wait limit
+ *   layout            1 = wide (a warp owns one row; chunks of 32*samples_per_lane
+ *                     samples), 2 = grouped (a warp owns samples_per_lane rows, each
+ *                     served by 32/samples_per_lane lanes; chunks of 32 samples)
  */
 typedef struct cos_tuning {
     int32_t samples_per_lane;
@@ -147,10 +164,73 @@ typedef struct cos_tuning {
     int32_t rows_per_warp;
     int32_t blocks_per_sm;
     int32_t timeout_ms;
+    int32_t layout;
 } cos_tuning;
 
 int cos_set_tuning(cos_graph_t g, const cos_tuning* tuning);
+/* Tuning cos_evaluate will use for `mode` with the current samples (automatic fields resolved). */
 int cos_get_tuning(cos_graph_t g, int32_t mode, cos_tuning* tuning);
+
+/*
+ * Batched evaluation of many graphs of uneven size and sample count in ONE
+ * persistent launch (Sec. III "Acceleration" notes that small graphs leave most
+ * of a thread block idle and suggests packing several small levels per block;
+ * Sec. II.C "Windowing" suggests evaluating levels asynchronously).  Every graph's
+ * work is cut into CTA-sized items (propagator factors and table per tile of
+ * samples, each level per tile, the sample reduction); the per-graph phase chains
+ * are interleaved into one task list that a persistent grid drains through a
+ * ticket counter, each item waiting only for the previous phase of its own graph.
+ * The launch (counter reset + kernel) is captured into a CUDA graph on first use
+ * and replayed by every later cos_batch_launch.
+ *
+ *   cos_batch_create  n distinct graph handles (each with samples attached, all on
+ *                     one device), one mode for the batch, per_sample_outs[n]
+ *                     device pointers (entries may be NULL; NULL array = none).
+ *                     The handles must outlive the batch; re-attaching samples to
+ *                     one of them requires a new batch (the plan captures the
+ *                     workspace layout).
+ *   cos_batch_reset   replace the members (same rules as create) keeping the device
+ *                     buffers; the previous launch must have been collected.
+ *   cos_batch_set_tuning  batch-wide overrides (fields > 0): samples_per_lane (one
+ *                     value for the launch), rows_per_warp, tile_samples,
+ *                     blocks_per_sm, timeout_ms; other fields come from each graph.
+ *   cos_batch_autotune  times every (samples_per_lane, rows_per_warp) candidate on
+ *                     the batch itself, keeps the fastest and returns it in *best.
+ *   cos_batch_launch  enqueue one evaluation of all graphs on `stream`.  The first
+ *                     launch of a plan uploads it (stream-ordered) and runs the
+ *                     kernel directly; the second captures counter reset + kernel
+ *                     into a CUDA graph, which every later launch replays.
+ *   cos_batch_results wait for `stream`; means[n] (host, may be NULL) receives each
+ *                     graph's mean; errors as cos_evaluate (COS_ERR_TIMEOUT if a
+ *                     dependency wait gave up).
+ *   cos_evaluate_batch  create + launch + results + destroy in one call.
+ * Per-sample results are identical to cos_evaluate's for the same tuning.
+ */
+typedef struct cos_batch* cos_batch_t;
+int cos_batch_create(int32_t n, const cos_graph_t* graphs, int32_t mode, void* const* per_sample_outs,
+                     cos_batch_t* out);
+int cos_batch_reset(cos_batch_t b, int32_t n, const cos_graph_t* graphs, void* const* per_sample_outs);
+int cos_batch_set_tuning(cos_batch_t b, const cos_tuning* tuning);
+int cos_batch_get_tuning(cos_batch_t b, cos_tuning* tuning);
+int cos_batch_autotune(cos_batch_t b, void* stream, cos_tuning* best);
+int cos_batch_launch(cos_batch_t b, void* stream);
+int cos_batch_results(cos_batch_t b, double* means, void* stream);
+int cos_batch_destroy(cos_batch_t b);
+int cos_evaluate_batch(int32_t n, const cos_graph_t* graphs, int32_t mode, void* const* per_sample_outs,
+                       double* means, void* stream);
+
+/*
+ * Phase trace (profiling aid; the paper reports only FLOPS).  cos_set_trace(g, n)
+ * with n > 0 allocates room for n records and makes every later cos_evaluate on
+ * g record, at each grid barrier, the %globaltimer value (ns) when CTA 0 passed
+ * it and the phase id (0 = kernel start, 1 = coefficients, 2 = propagator table
+ * of a tile (exponentials and products), 3+l = level l, 1000 = sample partial
+ * sums).  n = 0 frees it.  cos_get_trace waits for the device, copies up to
+ * `capacity` (time, phase) pairs of the last evaluate into out[2*capacity] and
+ * stores how many were written in *count.
+ */
+int cos_set_trace(cos_graph_t g, int32_t capacity);
+int cos_get_trace(cos_graph_t g, int64_t* out, int32_t capacity, int32_t* count);
 
 /*
  * cos_evaluate_static -- evaluate an existing graph without allocating device memory.
@@ -177,7 +257,7 @@ int cos_get_tuning(cos_graph_t g, int32_t mode, cos_tuning* tuning);
  * any stream capture begins.
  *
  * Limits.  The tile of samples is sized to fit the array; a graph whose working
- * set for 32 samples exceeds it (roughly 2 * W_max * w + P * w + 16 * K * D bytes
+ * set for 32 samples exceeds it (roughly 2 * W_max * w + P * w bytes
  * per sample, w = 8 in FP64 and count modes, 4 in FP32 mixed mode) is rejected
  * with COS_ERR_INVALID, as is a sample count whose partial sums do not fit.
  *
@@ -201,6 +281,14 @@ int cos_get_tuning(cos_graph_t g, int32_t mode, cos_tuning* tuning);
 #define COS_STATIC_SCRATCH_BYTES (64LL * 1024 * 1024)
 int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samples, const double* t, int64_t t_ld,
                         const double* eps, double beta, void* per_sample_out, double* mean_out, void* stream);
+
+/*
+ * Self test of the evaluator's double-precision exponentials: em[q] = e^{-x[q]},
+ * ep[q] = e^{+x[q]} for device arrays of n doubles, |x| <= 708, computed exactly as
+ * the propagator phase computes them (table-driven method, P. T. P. Tang, ACM TOMS
+ * 15 (1989)).  g supplies the device and the 2^{j/64} table.  Asynchronous on stream.
+ */
+int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, double* ep, void* stream);
 
 /* Free every device and host resource of the handle (NULL is accepted). */
 int cos_destroy(cos_graph_t g);

@@ -31,9 +31,13 @@ COS_MODE_COUNT_I64 = 2
 COS_T_DEVICE_DS = 0
 COS_T_HOST = 1
 COS_T_SAMPLE_MAJOR = 2
+COS_T_BORROW = 4
 
 EXPORTED = ["cos_create_graph", "cos_set_samples", "cos_evaluate", "cos_get_result", "cos_graph_info",
-            "cos_set_tuning", "cos_get_tuning", "cos_evaluate_static", "cos_destroy", "cos_last_error"]
+            "cos_set_tuning", "cos_get_tuning", "cos_set_trace", "cos_get_trace", "cos_evaluate_static",
+            "cos_graph_share", "cos_batch_create", "cos_batch_reset", "cos_batch_set_tuning", "cos_batch_get_tuning", "cos_batch_autotune",
+            "cos_batch_launch", "cos_batch_results", "cos_batch_destroy", "cos_evaluate_batch",
+            "cos_selftest_exp", "cos_destroy", "cos_last_error"]
 
 _lock = threading.Lock()
 _lib = None
@@ -48,7 +52,7 @@ class CosError(RuntimeError):
 class CosTuning(ctypes.Structure):
     _fields_ = [("samples_per_lane", ctypes.c_int32), ("tile_samples", ctypes.c_int32),
                 ("rows_per_warp", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("timeout_ms", ctypes.c_int32)]
+                ("timeout_ms", ctypes.c_int32), ("layout", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -78,7 +82,20 @@ def load_library(build_if_missing: bool = False):
         lib.cos_graph_info.argtypes = [vp, vp, i32]
         lib.cos_set_tuning.argtypes = [vp, ctypes.POINTER(CosTuning)]
         lib.cos_get_tuning.argtypes = [vp, i32, ctypes.POINTER(CosTuning)]
+        lib.cos_set_trace.argtypes = [vp, i32]
+        lib.cos_get_trace.argtypes = [vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
         lib.cos_evaluate_static.argtypes = [vp, i32, i64, vp, i64, vp, f64, vp, vp, vp]
+        lib.cos_graph_share.argtypes = [vp, ctypes.POINTER(vp)]
+        lib.cos_batch_create.argtypes = [i32, vp, i32, vp, ctypes.POINTER(vp)]
+        lib.cos_batch_reset.argtypes = [vp, i32, vp, vp]
+        lib.cos_batch_set_tuning.argtypes = [vp, ctypes.POINTER(CosTuning)]
+        lib.cos_batch_get_tuning.argtypes = [vp, ctypes.POINTER(CosTuning)]
+        lib.cos_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(CosTuning)]
+        lib.cos_batch_launch.argtypes = [vp, vp]
+        lib.cos_batch_results.argtypes = [vp, vp, vp]
+        lib.cos_batch_destroy.argtypes = [vp]
+        lib.cos_evaluate_batch.argtypes = [i32, vp, i32, vp, vp, vp]
+        lib.cos_selftest_exp.argtypes = [vp, i64, vp, vp, vp, vp]
         lib.cos_destroy.argtypes = [vp]
         lib.cos_last_error.restype = ctypes.c_char_p
         lib.cos_last_error.argtypes = []
@@ -131,6 +148,16 @@ class Graph:
     def from_workload_graph(cls, g) -> "Graph":
         return cls(g.widths, g.edge_counts, g.edges, g.num_kinds, g.num_times)
 
+    def share(self) -> "Graph":
+        """cos_graph_share: a second handle on this graph's device structure."""
+        h = ctypes.c_void_p()
+        _check(load_library().cos_graph_share(self._h, ctypes.byref(h)))
+        obj = Graph.__new__(Graph)
+        obj._h = h
+        obj._w, obj._c = self._w, self._c
+        obj.num_samples = 0
+        return obj
+
     @property
     def handle(self) -> int:
         return self._h.value
@@ -164,14 +191,33 @@ class Graph:
         _check(load_library().cos_get_result(self._h, ctypes.addressof(mean), _stream_handle(stream)))
         return mean.value
 
-    def set_tuning(self, samples_per_lane=0, tile_samples=0, rows_per_warp=0, blocks_per_sm=0, timeout_ms=0):
-        t = CosTuning(samples_per_lane, tile_samples, rows_per_warp, blocks_per_sm, timeout_ms)
+    def set_tuning(self, samples_per_lane=0, tile_samples=0, rows_per_warp=0, blocks_per_sm=0, timeout_ms=0,
+                   layout=0):
+        t = CosTuning(samples_per_lane, tile_samples, rows_per_warp, blocks_per_sm, timeout_ms, layout)
         _check(load_library().cos_set_tuning(self._h, ctypes.byref(t)))
 
     def get_tuning(self, mode: int) -> dict:
         t = CosTuning()
         _check(load_library().cos_get_tuning(self._h, int(mode), ctypes.byref(t)))
         return t.as_dict()
+
+    def set_trace(self, capacity: int):
+        _check(load_library().cos_set_trace(self._h, int(capacity)))
+        self._trace_cap = int(capacity)
+
+    def get_trace(self):
+        """[(phase id, ms since kernel start)] of the last evaluate (needs set_trace first)."""
+        cap = getattr(self, "_trace_cap", 0)
+        if cap <= 0:
+            return []
+        buf = np.zeros(2 * cap, dtype=np.int64)
+        n = ctypes.c_int32(0)
+        _check(load_library().cos_get_trace(self._h, _ptr(buf), cap, ctypes.byref(n)))
+        rec = buf[:2 * n.value].reshape(-1, 2)
+        if not len(rec):
+            return []
+        t0 = rec[0, 0]
+        return [(int(ph), (int(t) - int(t0)) / 1e6) for t, ph in rec]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -189,3 +235,71 @@ class Graph:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Owning handle of one batched launch plan (cos_batch_create / cos_batch_destroy)."""
+
+    def __init__(self, graphs: Sequence[Graph], mode: int, outs=None):
+        lib = load_library()
+        n = len(graphs)
+        self._graphs = list(graphs)                       # keep the handles alive
+        hs = (ctypes.c_void_p * max(n, 1))(*[g.handle for g in graphs])
+        self._outs = list(outs) if outs is not None else None
+        optr = None
+        if outs is not None:
+            arr = (ctypes.c_void_p * max(n, 1))(*[_ptr(o) for o in outs])
+            self._optr = arr
+            optr = arr
+        h = ctypes.c_void_p()
+        _check(lib.cos_batch_create(n, hs, int(mode), optr, ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    def reset(self, graphs: Sequence[Graph], outs=None):
+        """cos_batch_reset: new members, same device buffers (previous launch must be collected)."""
+        n = len(graphs)
+        self._graphs = list(graphs)
+        hs = (ctypes.c_void_p * max(n, 1))(*[g.handle for g in graphs])
+        optr = None
+        if outs is not None:
+            optr = (ctypes.c_void_p * max(n, 1))(*[_ptr(o) for o in outs])
+        self._optr = optr
+        self._outs = list(outs) if outs is not None else None
+        _check(load_library().cos_batch_reset(self._h, n, hs, optr))
+        self.n = n
+
+    def set_tuning(self, samples_per_lane=0, tile_samples=0, rows_per_warp=0, blocks_per_sm=0, timeout_ms=0,
+                   layout=0):
+        t = CosTuning(samples_per_lane, tile_samples, rows_per_warp, blocks_per_sm, timeout_ms, layout)
+        _check(load_library().cos_batch_set_tuning(self._h, ctypes.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = CosTuning()
+        _check(load_library().cos_batch_get_tuning(self._h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def autotune(self, stream=None) -> dict:
+        t = CosTuning()
+        _check(load_library().cos_batch_autotune(self._h, _stream_handle(stream), ctypes.byref(t)))
+        return t.as_dict()
+
+    def launch(self, stream=None):
+        _check(load_library().cos_batch_launch(self._h, _stream_handle(stream)))
+
+    def results(self, stream=None, allow_overflow: bool = False) -> np.ndarray:
+        means = np.zeros(max(self.n, 1))
+        _check(load_library().cos_batch_results(self._h, _ptr(means), _stream_handle(stream)),
+               allow=(COS_ERR_OVERFLOW,) if allow_overflow else ())
+        return means[:self.n]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().cos_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,601 @@
+// Batched evaluation of many graphs of uneven size and sample count in one
+// persistent launch.  The paper evaluates one graph per thread block and notes
+// that small graphs leave most of a block idle (Sec. III "Acceleration"); here
+// every graph's work is cut into the same CTA-sized items as the single-graph
+// kernel and all graphs share one persistent grid.
+//
+// Plan: each graph contributes a chain of phase tasks -- coefficients, then per
+// tile of samples (exponential factors, propagator table, levels 1..L-1), then
+// partial sums and the final mean.  The chains are interleaved round-robin into
+// one task list; CTAs draw tickets from a global counter, a ticket names one item
+// of one task, and an item waits (bounded) until the previous task of its own
+// chain has completed all its items.  Tickets are handed out in list order and a
+// task only ever waits on an earlier task, so the lowest pending item can always
+// run: no co-residency is required.  The launch (counter reset + kernel) is
+// captured once into a CUDA graph and replayed.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "cos_items.cuh"
+
+namespace cosgpu {
+namespace {
+
+enum TaskKind : int32_t { TK_COEF = 0, TK_PROP = 1, TK_LEVEL = 3, TK_PARTIALS = 4, TK_FINAL = 5 };
+
+struct Task {
+    int32_t graph;   // index into the parameter array
+    int32_t kind;
+    int32_t level;
+    int32_t dep;     // task that must be complete first (-1: none)
+    int64_t tix;     // tile index
+    int64_t first;   // first ticket of this task
+    int32_t items;
+    int32_t pad;
+};
+
+struct BatchCtrl {
+    unsigned long long ticket;
+    int err;
+    int err_task;
+};
+
+struct BatchArgs {
+    const Task* tasks;
+    int32_t ntasks;
+    int32_t pad;
+    int64_t total;
+    const WalkParams* params;
+    unsigned* done;
+    BatchCtrl* ctrl;
+    long long timeout_ns;
+};
+
+template <int MODE, int V>
+constexpr int batch_min_blocks() {
+    return (MODE == COS_MODE_FP64 && V > 2) ? 2 : 3;
+}
+
+template <int MODE, int V, int LAYOUT>
+__global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V>()) batch_kernel(const BatchArgs a) {
+    constexpr int CHV = chunk_samples<V, LAYOUT>();
+    extern __shared__ __align__(16) double smem[];
+    __shared__ long long s_ticket;
+    __shared__ int s_ok;
+    int cursor = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = (long long)atomicAdd(&a.ctrl->ticket, 1ull);
+        __syncthreads();
+        const long long t = s_ticket;
+        if (t >= a.total) break;
+        while (cursor + 1 < a.ntasks && a.tasks[cursor + 1].first <= t) ++cursor;
+        const Task tk = a.tasks[cursor];
+        const int item = (int)(t - tk.first);
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (tk.dep >= 0) {
+                const unsigned need = (unsigned)a.tasks[tk.dep].items;
+                const unsigned long long t0 = global_timer_ns();
+                for (unsigned long long spin = 0;; ++spin) {
+                    if (ld_acquire_gpu_u32(a.done + tk.dep) >= need) break;
+                    if (*(volatile int*)&a.ctrl->err != 0) { ok = 0; break; }
+                    if ((spin & 31) == 31 &&
+                        ((long long)(global_timer_ns() - t0) > a.timeout_ns || spin > (1ull << 32))) {
+                        if (atomicCAS(&a.ctrl->err, 0, KERR_BARRIER_TIMEOUT) == 0) a.ctrl->err_task = cursor;
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const WalkParams& p = a.params[tk.graph];
+        switch (tk.kind) {
+            case TK_COEF: item_coef(p); break;
+            case TK_PROP: item_props<MODE, CHV>(p, tile_ctx<CHV>(p, tk.tix), item, smem); break;
+            case TK_LEVEL: item_level<MODE, V, LAYOUT>(p, tk.level, tile_ctx<CHV>(p, tk.tix), item); break;
+            case TK_PARTIALS: item_partials<MODE>(p, item); break;
+            default: item_final(p); break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.done + cursor, 1u);
+        }
+    }
+}
+
+template <int MODE, int V, int LAYOUT>
+const void* bk() {
+    return reinterpret_cast<const void*>(&batch_kernel<MODE, V, LAYOUT>);
+}
+
+template <int LAYOUT>
+const void* select_batch_layout(int mode, int vec) {
+    switch (mode * 8 + vec) {
+        case COS_MODE_FP64 * 8 + 1: return bk<COS_MODE_FP64, 1, LAYOUT>();
+        case COS_MODE_FP64 * 8 + 2: return bk<COS_MODE_FP64, 2, LAYOUT>();
+        case COS_MODE_FP64 * 8 + 4: return bk<COS_MODE_FP64, 4, LAYOUT>();
+        case COS_MODE_FP32_MIXED * 8 + 1: return bk<COS_MODE_FP32_MIXED, 1, LAYOUT>();
+        case COS_MODE_FP32_MIXED * 8 + 2: return bk<COS_MODE_FP32_MIXED, 2, LAYOUT>();
+        case COS_MODE_FP32_MIXED * 8 + 4: return bk<COS_MODE_FP32_MIXED, 4, LAYOUT>();
+        case COS_MODE_COUNT_I64 * 8 + 1: return bk<COS_MODE_COUNT_I64, 1, LAYOUT>();
+        case COS_MODE_COUNT_I64 * 8 + 2: return bk<COS_MODE_COUNT_I64, 2, LAYOUT>();
+        case COS_MODE_COUNT_I64 * 8 + 4: return bk<COS_MODE_COUNT_I64, 4, LAYOUT>();
+        default: return nullptr;
+    }
+}
+
+const void* select_batch_kernel(int mode, int vec, int layout) {
+    if (layout == 2) return select_batch_layout<LAYOUT_GROUPED>(mode, vec);
+    if (layout == 1) return select_batch_layout<LAYOUT_WIDE>(mode, vec);
+    return nullptr;
+}
+
+int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+}  // namespace cosgpu
+
+using namespace cosgpu;
+
+struct cos_batch {
+    int device = 0;
+    int32_t n = 0;
+    int32_t mode = 0;
+    std::vector<cos_graph_t> graphs;
+    std::vector<void*> outs;
+    cos_tuning tuning{0, 0, 0, 0, 0, 0};     // batch-level overrides (samples_per_lane, rows_per_warp, ...)
+    cos_tuning resolved{0, 0, 0, 0, 0, 0};
+    // host plan and its pinned staging copies
+    std::vector<Task> tasks;
+    std::vector<WalkParams> params;
+    std::vector<int> counts_overflow;
+    Task* h_tasks = nullptr;
+    WalkParams* h_params = nullptr;
+    double* h_means = nullptr;
+    BatchCtrl* h_ctrl = nullptr;
+    // device buffers (grow only)
+    Task* d_tasks = nullptr;
+    WalkParams* d_params = nullptr;
+    unsigned* d_done = nullptr;
+    double* d_means = nullptr;
+    BatchCtrl* d_ctrl = nullptr;
+    size_t cap_tasks = 0, cap_graphs = 0;
+    int32_t ntasks = 0;
+    int64_t total = 0;
+    int grid = 0;
+    int smem = 0;
+    bool planned = false;        // host plan matches members and tuning
+    bool uploaded = false;       // device copy of the plan is current
+    int launches_since_plan = 0;
+    // captured launch (counter reset + kernel), built on the second launch of a plan
+    cudaGraph_t cgraph = nullptr;
+    cudaGraphExec_t cexec = nullptr;
+};
+
+namespace {
+
+void drop_capture(cos_batch* b) {
+    if (b->cexec) cudaGraphExecDestroy(b->cexec);
+    if (b->cgraph) cudaGraphDestroy(b->cgraph);
+    b->cexec = nullptr;
+    b->cgraph = nullptr;
+}
+
+void free_buffers(cos_batch* b) {
+    drop_capture(b);
+    cudaFree(b->d_tasks);
+    cudaFree(b->d_params);
+    cudaFree(b->d_done);
+    cudaFree(b->d_means);
+    cudaFree(b->d_ctrl);
+    cudaFreeHost(b->h_tasks);
+    cudaFreeHost(b->h_params);
+    cudaFreeHost(b->h_means);
+    cudaFreeHost(b->h_ctrl);
+    b->d_tasks = nullptr;
+    b->d_params = nullptr;
+    b->d_done = nullptr;
+    b->d_means = nullptr;
+    b->d_ctrl = nullptr;
+    b->h_tasks = nullptr;
+    b->h_params = nullptr;
+    b->h_means = nullptr;
+    b->h_ctrl = nullptr;
+    b->cap_tasks = b->cap_graphs = 0;
+}
+
+int ensure_capacity(cos_batch* b, size_t ntasks, size_t ngraphs) {
+    cudaError_t e = cudaSuccess;
+    if (!b->d_ctrl) {
+        if ((e = cudaMalloc(&b->d_ctrl, sizeof(BatchCtrl))) != cudaSuccess ||
+            (e = cudaMallocHost(&b->h_ctrl, sizeof(BatchCtrl))) != cudaSuccess)
+            return set_error(COS_ERR_OOM, "batch control: %s", cudaGetErrorString(e));
+    }
+    if (ntasks > b->cap_tasks) {
+        cudaFree(b->d_tasks);
+        cudaFree(b->d_done);
+        cudaFreeHost(b->h_tasks);
+        b->d_tasks = nullptr;
+        b->d_done = nullptr;
+        b->h_tasks = nullptr;
+        const size_t cap = std::max<size_t>(ntasks, 2 * b->cap_tasks);
+        if ((e = cudaMalloc(&b->d_tasks, sizeof(Task) * cap)) != cudaSuccess ||
+            (e = cudaMalloc(&b->d_done, sizeof(unsigned) * cap)) != cudaSuccess ||
+            (e = cudaMallocHost(&b->h_tasks, sizeof(Task) * cap)) != cudaSuccess)
+            return set_error(COS_ERR_OOM, "batch task list: %s", cudaGetErrorString(e));
+        b->cap_tasks = cap;
+    }
+    if (ngraphs > b->cap_graphs) {
+        cudaFree(b->d_params);
+        cudaFree(b->d_means);
+        cudaFreeHost(b->h_params);
+        cudaFreeHost(b->h_means);
+        b->d_params = nullptr;
+        b->d_means = nullptr;
+        b->h_params = nullptr;
+        b->h_means = nullptr;
+        const size_t cap = std::max<size_t>(ngraphs, 2 * b->cap_graphs);
+        if ((e = cudaMalloc(&b->d_params, sizeof(WalkParams) * cap)) != cudaSuccess ||
+            (e = cudaMalloc(&b->d_means, sizeof(double) * cap)) != cudaSuccess ||
+            (e = cudaMallocHost(&b->h_params, sizeof(WalkParams) * cap)) != cudaSuccess ||
+            (e = cudaMallocHost(&b->h_means, sizeof(double) * cap)) != cudaSuccess)
+            return set_error(COS_ERR_OOM, "batch parameters: %s", cudaGetErrorString(e));
+        b->cap_graphs = cap;
+    }
+    return COS_OK;
+}
+
+// Build the interleaved task list and the per-graph parameters on the host.
+int plan(cos_batch* b) {
+    const int mode = b->mode;
+    // one vector width and layout for the whole launch (kernel template parameters)
+    cos_tuning force = b->tuning;
+    if (force.samples_per_lane <= 0) force.samples_per_lane = (mode == COS_MODE_FP32_MIXED) ? 4 : 2;
+    if (force.layout <= 0) force.layout = 1;
+    const int chv = force.layout == 2 ? 32 : 32 * force.samples_per_lane;
+    cos_tuning first = force;
+    b->params.assign((size_t)b->n, WalkParams{});
+    b->counts_overflow.assign((size_t)b->n, 0);
+    std::vector<std::vector<Task>> chains((size_t)b->n);
+    for (int32_t g = 0; g < b->n; ++g) {
+        cos_tuning tn;
+        int rc = prepare_walk(b->graphs[(size_t)g], mode, &force, b->outs[(size_t)g], &b->params[(size_t)g], &tn);
+        if (rc != COS_OK) return rc;
+        if (g == 0) first = tn;
+        GraphView gv;
+        graph_view(b->graphs[(size_t)g], &gv);
+        b->counts_overflow[(size_t)g] = gv.count_overflow;
+        WalkParams& p = b->params[(size_t)g];
+        std::vector<Task>& ch = chains[(size_t)g];
+        auto push = [&](int32_t kind, int32_t level, int64_t tix, int64_t items) {
+            Task t;
+            memset(&t, 0, sizeof(t));
+            t.graph = g;
+            t.kind = kind;
+            t.level = level;
+            t.tix = tix;
+            t.items = (int32_t)items;
+            t.dep = -1;
+            ch.push_back(t);
+        };
+        if (mode != COS_MODE_COUNT_I64) push(TK_COEF, 0, 0, 1);
+        const int64_t ntiles = (p.S + p.tile - 1) / p.tile;
+        for (int64_t tix = 0; tix < ntiles; ++tix) {
+            const int64_t base = tix * p.tile;
+            const int64_t nsamp = std::min(p.tile, p.S - base);
+            const int nch = div_up(nsamp, chv);
+            push(TK_PROP, 0, tix, mode == COS_MODE_COUNT_I64 ? nch : (int64_t)nch * p.K);
+            for (int l = 1; l < p.L; ++l) {
+                const int rows_per_item = kWarps * p.rows_per_warp;
+                push(TK_LEVEL, l, tix, (int64_t)nch * div_up(gv.widths_host[l], rows_per_item));
+            }
+        }
+        push(TK_PARTIALS, 0, 0, div_up(div_up(p.S, kReduceBlock), kWarps));
+        push(TK_FINAL, 0, 0, 1);
+    }
+    // Round-robin interleave; each task depends on its predecessor in its chain.
+    b->tasks.clear();
+    std::vector<int32_t> last((size_t)b->n, -1);
+    size_t longest = 0;
+    for (auto& ch : chains) longest = std::max(longest, ch.size());
+    for (size_t r = 0; r < longest; ++r)
+        for (int32_t g = 0; g < b->n; ++g) {
+            if (r >= chains[(size_t)g].size()) continue;
+            Task t = chains[(size_t)g][r];
+            t.dep = last[(size_t)g];
+            last[(size_t)g] = (int32_t)b->tasks.size();
+            b->tasks.push_back(t);
+        }
+    int64_t first_ticket = 0;
+    for (auto& t : b->tasks) {
+        t.first = first_ticket;
+        first_ticket += t.items;
+    }
+    b->ntasks = (int32_t)b->tasks.size();
+    b->total = first_ticket;
+    b->resolved = first;
+    b->resolved.samples_per_lane = force.samples_per_lane;
+    b->resolved.layout = force.layout;
+    const void* k = select_batch_kernel(mode, b->resolved.samples_per_lane, b->resolved.layout);
+    if (!k) return set_error(COS_ERR_INVALID, "no batch kernel for samples_per_lane %d", b->resolved.samples_per_lane);
+    int dmax = 1;
+    for (const WalkParams& p : b->params) dmax = std::max(dmax, p.D);
+    const int smem = walk_smem_bytes(mode, dmax);
+    if (prepare_kernel_attrs(k, smem) != COS_OK) return set_error(COS_ERR_CUDA, "cannot set dynamic shared memory");
+    b->smem = smem;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess || per_sm <= 0)
+        return set_error(COS_ERR_CUDA, "occupancy query failed");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    int bps = per_sm;
+    if (b->tuning.blocks_per_sm > 0) bps = std::min(bps, b->tuning.blocks_per_sm);
+    b->resolved.blocks_per_sm = bps;
+    b->grid = sms * bps;
+    int rc = ensure_capacity(b, std::max<size_t>(b->tasks.size(), 1), std::max<int32_t>(b->n, 1));
+    if (rc != COS_OK) return rc;
+    for (int32_t g = 0; g < b->n; ++g) b->params[(size_t)g].mean_out = b->d_means + g;
+    drop_capture(b);
+    b->planned = true;
+    b->uploaded = false;
+    b->launches_since_plan = 0;
+    return COS_OK;
+}
+
+// Counter reset + kernel: the part of a launch that is captured and replayed.
+int enqueue_run(cos_batch* b, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned) * std::max<int32_t>(b->ntasks, 1), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_ctrl, 0, sizeof(BatchCtrl), st)) != cudaSuccess)
+        return set_error(COS_ERR_CUDA, "reset batch counters: %s", cudaGetErrorString(e));
+    BatchArgs a;
+    a.tasks = b->d_tasks;
+    a.ntasks = b->ntasks;
+    a.pad = 0;
+    a.total = b->total;
+    a.params = b->d_params;
+    a.done = b->d_done;
+    a.ctrl = b->d_ctrl;
+    a.timeout_ns = (long long)(b->resolved.timeout_ms > 0 ? b->resolved.timeout_ms : 10000) * 1000000LL;
+    void* args[] = {&a};
+    const void* k = select_batch_kernel(b->mode, b->resolved.samples_per_lane, b->resolved.layout);
+    const size_t smem = (size_t)b->smem;
+    if (b->total > 0 && (e = cudaLaunchKernel(k, dim3(b->grid), dim3(kThreads), args, smem, st)) != cudaSuccess)
+        return set_error(COS_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+    return COS_OK;
+}
+
+// Stream-ordered upload of the plan from pinned staging buffers.
+int upload(cos_batch* b, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (!b->tasks.empty()) {
+        memcpy(b->h_tasks, b->tasks.data(), sizeof(Task) * b->tasks.size());
+        e = cudaMemcpyAsync(b->d_tasks, b->h_tasks, sizeof(Task) * b->tasks.size(), cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess && b->n) {
+        memcpy(b->h_params, b->params.data(), sizeof(WalkParams) * b->n);
+        e = cudaMemcpyAsync(b->d_params, b->h_params, sizeof(WalkParams) * b->n, cudaMemcpyHostToDevice, st);
+    }
+    if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "upload plan: %s", cudaGetErrorString(e));
+    b->uploaded = true;
+    return COS_OK;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) {
+        cudaGetDevice(&prev);
+        cudaSetDevice(dev);
+    }
+    ~DevGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int cos_batch_create(int32_t n, const cos_graph_t* graphs, int32_t mode, void* const* per_sample_outs,
+                     cos_batch_t* out) {
+    if (!out) return set_error(COS_ERR_INVALID, "out is NULL");
+    if (mode < 0 || mode > 2) return set_error(COS_ERR_INVALID, "bad mode %d", mode);
+    cos_batch* b = new (std::nothrow) cos_batch();
+    if (!b) return set_error(COS_ERR_OOM, "host allocation failed");
+    b->mode = mode;
+    int rc = cos_batch_reset(b, n, graphs, per_sample_outs);
+    if (rc != COS_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return COS_OK;
+}
+
+int cos_batch_reset(cos_batch_t b, int32_t n, const cos_graph_t* graphs, void* const* per_sample_outs) {
+    if (!b || n < 0 || (n > 0 && !graphs)) return set_error(COS_ERR_INVALID, "bad arguments");
+    int dev = -1;
+    for (int32_t g = 0; g < n; ++g) {
+        GraphView gv;
+        int rc = graph_view(graphs[g], &gv);
+        if (rc != COS_OK) return rc;
+        if (dev >= 0 && gv.device != dev) return set_error(COS_ERR_INVALID, "all graphs must be on one device");
+        dev = gv.device;
+        for (int32_t h = 0; h < g; ++h)
+            if (graphs[h] == graphs[g]) return set_error(COS_ERR_INVALID, "graph handle %d appears twice in the batch", g);
+    }
+    if (b->d_ctrl && dev >= 0 && dev != b->device) return set_error(COS_ERR_INVALID, "a batch stays on one device");
+    if (dev >= 0) b->device = dev;
+    else cudaGetDevice(&b->device);
+    b->n = n;
+    b->graphs.assign(graphs, graphs + n);
+    b->outs.assign((size_t)n, nullptr);
+    if (per_sample_outs)
+        for (int32_t g = 0; g < n; ++g) b->outs[(size_t)g] = per_sample_outs[g];
+    b->planned = false;
+    return COS_OK;
+}
+
+int cos_batch_set_tuning(cos_batch_t b, const cos_tuning* t) {
+    if (!b || !t) return set_error(COS_ERR_INVALID, "bad arguments");
+    if (t->samples_per_lane > 0 && t->samples_per_lane != 1 && t->samples_per_lane != 2 && t->samples_per_lane != 4)
+        return set_error(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
+    if (t->rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
+    if (t->layout < 0 || t->layout > 2) return set_error(COS_ERR_INVALID, "layout must be 0, 1 or 2");
+    b->tuning = *t;
+    b->planned = false;
+    return COS_OK;
+}
+
+int cos_batch_get_tuning(cos_batch_t b, cos_tuning* t) {
+    if (!b || !t) return set_error(COS_ERR_INVALID, "bad arguments");
+    *t = b->resolved;
+    return COS_OK;
+}
+
+int cos_batch_launch(cos_batch_t b, void* stream) {
+    if (!b) return set_error(COS_ERR_INVALID, "batch is NULL");
+    DevGuard dg(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = COS_OK;
+    if (!b->planned) rc = plan(b);
+    if (rc != COS_OK) return rc;
+    if (!b->uploaded) {
+        rc = upload(b, st);
+        if (rc != COS_OK) return rc;
+    }
+    b->launches_since_plan++;
+    if (b->launches_since_plan == 1) return enqueue_run(b, st);   // a plan launched once is not worth capturing
+    if (!b->cexec) {
+        // second launch of the same plan: capture counter reset + kernel once, replay afterwards
+        cudaStream_t cap;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "capture stream: %s", cudaGetErrorString(e));
+        if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return set_error(COS_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+        }
+        rc = enqueue_run(b, cap);
+        e = cudaStreamEndCapture(cap, &b->cgraph);
+        cudaStreamDestroy(cap);
+        if (rc != COS_OK) return rc;
+        if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+        if ((e = cudaGraphInstantiate(&b->cexec, b->cgraph, 0)) != cudaSuccess)
+            return set_error(COS_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaGraphLaunch(b->cexec, st);
+    if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    return COS_OK;
+}
+
+int cos_batch_results(cos_batch_t b, double* means, void* stream) {
+    if (!b) return set_error(COS_ERR_INVALID, "batch is NULL");
+    if (!b->planned || !b->uploaded) return set_error(COS_ERR_STATE, "batch has not been launched");
+    DevGuard dg(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && b->n)
+        e = cudaMemcpyAsync(b->h_means, b->d_means, sizeof(double) * b->n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "batch results: %s", cudaGetErrorString(e));
+    if (b->h_ctrl->err == KERR_BARRIER_TIMEOUT)
+        return set_error(COS_ERR_TIMEOUT, "dependency wait timed out (task %d)", b->h_ctrl->err_task);
+    if (b->h_ctrl->err != 0) return set_error(COS_ERR_CUDA, "batch kernel error %d", b->h_ctrl->err);
+    if (means)
+        for (int32_t g = 0; g < b->n; ++g) means[g] = b->h_means[g];
+    if (b->mode == COS_MODE_COUNT_I64)
+        for (int32_t g = 0; g < b->n; ++g)
+            if (b->counts_overflow[(size_t)g])
+                return set_error(COS_ERR_OVERFLOW, "graph %d: path count exceeds 2^63-1", g);
+    return COS_OK;
+}
+
+int cos_batch_autotune(cos_batch_t b, void* stream, cos_tuning* best_out) {
+    if (!b) return set_error(COS_ERR_INVALID, "batch is NULL");
+    DevGuard dg(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const cos_tuning base = b->tuning;
+    const int vecs[] = {1, 2, 4};
+    const int rpws[] = {4, 8, 16, 28};
+    float best_ms = 1e30f;
+    cos_tuning best = base;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = COS_OK;
+    const int layouts[] = {1, 2};
+    for (int lay : layouts)
+    for (int v : vecs) {
+        if (b->mode == COS_MODE_FP64 && v == 4) continue;   // register-heavy; never faster in FP64
+        if (lay == 2 && v == 1) continue;                   // identical to the wide layout
+        for (int r : rpws) {
+            cos_tuning t = base;
+            t.samples_per_lane = v;
+            t.rows_per_warp = r;
+            t.layout = lay;
+            b->tuning = t;
+            rc = plan(b);
+            if (rc == COS_OK) rc = upload(b, st);
+            if (rc != COS_OK) break;
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, st);
+                rc = enqueue_run(b, st);
+                cudaEventRecord(e1, st);
+                if (rc != COS_OK) break;
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_best = std::min(ms_best, ms);
+            }
+            if (rc != COS_OK) break;
+            cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            if (b->h_ctrl->err != 0) {
+                rc = set_error(COS_ERR_TIMEOUT, "autotune candidate failed (error %d)", b->h_ctrl->err);
+                break;
+            }
+            if (ms_best < best_ms) {
+                best_ms = ms_best;
+                best = t;
+            }
+        }
+        if (rc != COS_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tuning = best;
+    if (rc == COS_OK) rc = plan(b);
+    if (rc == COS_OK && best_out) *best_out = b->resolved;
+    return rc;
+}
+
+int cos_batch_destroy(cos_batch_t b) {
+    if (!b) return COS_OK;
+    {
+        DevGuard dg(b->device);
+        free_buffers(b);
+    }
+    delete b;
+    return COS_OK;
+}
+
+int cos_evaluate_batch(int32_t n, const cos_graph_t* graphs, int32_t mode, void* const* per_sample_outs,
+                       double* means, void* stream) {
+    cos_batch_t b = nullptr;
+    int rc = cos_batch_create(n, graphs, mode, per_sample_outs, &b);
+    if (rc != COS_OK) return rc;
+    rc = cos_batch_launch(b, stream);
+    if (rc == COS_OK) rc = cos_batch_results(b, means, stream);
+    cos_batch_destroy(b);
+    return rc;
+}
+
+}  // extern "C"

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,27 @@ void dfree(T*& p) {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Device arrays of one graph structure, shared by every handle created from it with
+// cos_graph_share and freed with the last of them.
+struct SharedArrays {
+    int device = 0;
+    LevelDesc* levels = nullptr;
+    int32_t* row_ptr = nullptr;
+    int2* edges = nullptr;
+    int32_t* slot_kij = nullptr;
+    int32_t* kind_slot = nullptr;
+    double* exp_tab = nullptr;
+    ~SharedArrays() {
+        DeviceGuard dg(device);
+        dfree(levels);
+        dfree(row_ptr);
+        dfree(edges);
+        dfree(slot_kij);
+        dfree(kind_slot);
+        dfree(exp_tab);
+    }
+};
+
 }  // namespace
 
 struct cos_graph {
@@ -76,6 +98,9 @@ struct cos_graph {
     int32_t* d_row_ptr = nullptr;
     int2* d_edges = nullptr;
     int32_t* d_slot_kij = nullptr;
+    int32_t* d_kind_slot = nullptr;
+    double* d_exp_tab = nullptr;
+    std::shared_ptr<SharedArrays> arrays;   // owner of the four arrays above once creation succeeded
     Ctrl* d_ctrl = nullptr;
     // samples
     bool has_samples = false;
@@ -84,6 +109,7 @@ struct cos_graph {
     double* d_t = nullptr;
     double* d_eps = nullptr;
     double* d_stage = nullptr;      // [S][D] staging for host sample-major input
+    const double* t_borrowed = nullptr;   // caller's [D][t_ld] times (COS_T_BORROW)
     int64_t stage_cap = 0;
     // workspace
     void* d_arena = nullptr;
@@ -92,8 +118,10 @@ struct cos_graph {
     int64_t partial_cap = 0;
     void* d_R = nullptr;            // internal per-sample output when the caller passes none
     int64_t R_cap = 0;
-    cos_tuning tuning{0, 0, 0, 0, 0};
+    cos_tuning tuning{0, 0, 0, 0, 0, 0};
     int last_status_pending = 0;    // 1 while an evaluate has not been collected
+    unsigned long long* d_trace = nullptr;   // per-barrier timestamps of the last evaluate
+    int32_t trace_cap = 0;
     int last_mode = 0;
 };
 
@@ -103,8 +131,7 @@ namespace {
 size_t per_sample_bytes(const cos_graph* g, int mode) {
     size_t val = (mode == COS_MODE_FP32_MIXED) ? 4 : 8;
     size_t gt = (mode == COS_MODE_COUNT_I64) ? 0 : val;
-    size_t fac = (mode == COS_MODE_COUNT_I64) ? 0 : 2 * sizeof(double) * (size_t)g->K * (size_t)g->D;
-    return 2 * val * (size_t)g->Wmax + gt * (size_t)g->P + fac;
+    return 2 * val * (size_t)g->Wmax + gt * (size_t)g->P;
 }
 
 size_t default_budget_bytes() {
@@ -126,22 +153,14 @@ bool carve(cos_graph* g, int mode, int64_t tile, WalkParams& p) {
     };
     size_t s0 = take(val * g->Wmax * tile);
     size_t s1 = take(val * g->Wmax * tile);
-    size_t gt = 0, fm = 0, fp = 0, cf = 0;
-    if (mode != COS_MODE_COUNT_I64) {
-        gt = take(val * g->P * tile);
-        fm = take(sizeof(double) * g->K * g->D * tile);
-        fp = take(sizeof(double) * g->K * g->D * tile);
-        cf = take(sizeof(double) * 2 * g->K);
-    } else {
-        cf = take(sizeof(double) * 2 * g->K);
-    }
+    size_t gt = 0;
+    if (mode != COS_MODE_COUNT_I64) gt = take(val * g->P * tile);
+    const size_t cf = take(sizeof(double) * 2 * g->K);
     if (off > g->arena_bytes) return false;
     char* base = (char*)g->d_arena;
     p.slab[0] = base + s0;
     p.slab[1] = base + s1;
     p.gtab = (mode != COS_MODE_COUNT_I64) ? (void*)(base + gt) : nullptr;
-    p.fac_m = (mode != COS_MODE_COUNT_I64) ? (double*)(base + fm) : nullptr;
-    p.fac_p = (mode != COS_MODE_COUNT_I64) ? (double*)(base + fp) : nullptr;
     p.coef = (double*)(base + cf);
     return true;
 }
@@ -298,11 +317,68 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
     if ((e = cudaMalloc(&g->d_edges, sizeof(int2) * std::max<int64_t>(E, 1))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc edges");
     if ((e = cudaMalloc(&g->d_slot_kij, sizeof(int32_t) * std::max<int64_t>(3 * P, 3))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc slots");
     if ((e = cudaMalloc(&g->d_ctrl, sizeof(Ctrl))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc ctrl");
+    {
+        // slots are numbered in (kind, i, j) order, so every kind owns one contiguous range
+        std::vector<int32_t> ks((size_t)num_kinds + 1, 0);
+        for (int64_t q = 0; q < P; ++q) ks[(size_t)slot_kij[3 * q] + 1]++;
+        for (int32_t k = 0; k < num_kinds; ++k) ks[(size_t)k + 1] += ks[(size_t)k];
+        // 2^{j/64} and 2^{-j/64}, j = 0..63, for the table-driven exponentials
+        std::vector<double> tab(128);
+        for (int j = 0; j < 64; ++j) {
+            tab[(size_t)j] = (double)std::exp2l((long double)j / 64.0L);
+            tab[(size_t)j + 64] = (double)std::exp2l(-(long double)j / 64.0L);
+        }
+        if ((e = cudaMalloc(&g->d_kind_slot, sizeof(int32_t) * (num_kinds + 1))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc kind slots");
+        if ((e = cudaMalloc(&g->d_exp_tab, sizeof(double) * 128)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc exp table");
+        if ((e = cudaMemcpy(g->d_kind_slot, ks.data(), sizeof(int32_t) * (num_kinds + 1), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy kind slots");
+        if ((e = cudaMemcpy(g->d_exp_tab, tab.data(), sizeof(double) * 128, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy exp table");
+    }
     if ((e = cudaMemcpy(g->d_levels, lv.data(), sizeof(LevelDesc) * L, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy levels");
     if ((e = cudaMemcpy(g->d_row_ptr, row_ptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy row_ptr");
     if (E && (e = cudaMemcpy(g->d_edges, csr.data(), sizeof(int2) * E, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy edges");
     if (P && (e = cudaMemcpy(g->d_slot_kij, slot_kij.data(), sizeof(int32_t) * 3 * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy slots");
     if ((e = cudaMemset(g->d_ctrl, 0, sizeof(Ctrl))) != cudaSuccess) return cleanup_fail(e, "memset ctrl");
+    auto arr = std::make_shared<SharedArrays>();
+    arr->device = g->device;
+    arr->levels = g->d_levels;
+    arr->row_ptr = g->d_row_ptr;
+    arr->edges = g->d_edges;
+    arr->slot_kij = g->d_slot_kij;
+    arr->kind_slot = g->d_kind_slot;
+    arr->exp_tab = g->d_exp_tab;
+    g->arrays = std::move(arr);
+    *out = g;
+    return COS_OK;
+}
+
+int cos_graph_share(cos_graph_t src, cos_graph_t* out) {
+    if (!src || !out) return fail(COS_ERR_INVALID, "bad arguments");
+    if (!src->arrays) return fail(COS_ERR_STATE, "source graph is incomplete");
+    cos_graph* g = new (std::nothrow) cos_graph();
+    if (!g) return fail(COS_ERR_OOM, "host allocation failed");
+    g->device = src->device;
+    g->L = src->L; g->K = src->K; g->D = src->D; g->N = src->N; g->E = src->E; g->P = src->P; g->Wmax = src->Wmax;
+    g->widths = src->widths;
+    g->off = src->off;
+    g->ecount = src->ecount;
+    g->count_wrapped = src->count_wrapped;
+    g->count_overflow = src->count_overflow;
+    g->d_levels = src->d_levels;
+    g->d_row_ptr = src->d_row_ptr;
+    g->d_edges = src->d_edges;
+    g->d_slot_kij = src->d_slot_kij;
+    g->d_kind_slot = src->d_kind_slot;
+    g->d_exp_tab = src->d_exp_tab;
+    g->arrays = src->arrays;
+    g->tuning = src->tuning;
+    DeviceGuard dg(g->device);
+    cudaError_t e = cudaMalloc(&g->d_ctrl, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaMemset(g->d_ctrl, 0, sizeof(Ctrl));
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "cudaMalloc ctrl");
+        cos_destroy(g);
+        return rc;
+    }
     *out = g;
     return COS_OK;
 }
@@ -311,10 +387,16 @@ int cos_destroy(cos_graph_t g) {
     if (!g) return COS_OK;
     {
         DeviceGuard dg(g->device);
-        dfree(g->d_levels);
-        dfree(g->d_row_ptr);
-        dfree(g->d_edges);
-        dfree(g->d_slot_kij);
+        if (g->arrays) {
+            g->arrays.reset();   // frees the structure arrays with the last handle sharing them
+        } else {
+            dfree(g->d_levels);
+            dfree(g->d_row_ptr);
+            dfree(g->d_edges);
+            dfree(g->d_slot_kij);
+            dfree(g->d_kind_slot);
+            dfree(g->d_exp_tab);
+        }
         dfree(g->d_ctrl);
         dfree(g->d_t);
         dfree(g->d_eps);
@@ -322,6 +404,7 @@ int cos_destroy(cos_graph_t g) {
         if (g->d_arena) cudaFree(g->d_arena);
         g->d_arena = nullptr;
         dfree(g->d_partials);
+        dfree(g->d_trace);
         if (g->d_R) cudaFree(g->d_R);
         g->d_R = nullptr;
     }
@@ -341,8 +424,9 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
     if (!g || !t) return fail(COS_ERR_INVALID, "bad arguments");
     if (t->samples_per_lane > 0 && t->samples_per_lane != 1 && t->samples_per_lane != 2 && t->samples_per_lane != 4)
         return fail(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
-    if (t->rows_per_warp > 64) return fail(COS_ERR_INVALID, "rows_per_warp must be <= 64");
+    if (t->rows_per_warp > 31) return fail(COS_ERR_INVALID, "rows_per_warp must be <= 31");
     if (t->blocks_per_sm > 32) return fail(COS_ERR_INVALID, "blocks_per_sm must be <= 32");
+    if (t->layout < 0 || t->layout > 2) return fail(COS_ERR_INVALID, "layout must be 0 (auto), 1 (wide) or 2 (grouped)");
     g->tuning = *t;
     return COS_OK;
 }
@@ -350,18 +434,19 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
 static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* tile_out) {
     cos_tuning t = g->tuning;
     if (t.samples_per_lane <= 0) t.samples_per_lane = default_vec(mode);
-    if (t.rows_per_warp <= 0) t.rows_per_warp = 1;
+    if (t.rows_per_warp <= 0) t.rows_per_warp = 16;
+    if (t.layout <= 0) t.layout = 1;
     if (t.timeout_ms <= 0) {
         const char* env = getenv("COS_TIMEOUT_MS");
         t.timeout_ms = (env && atoi(env) > 0) ? atoi(env) : 10000;
     }
-    int dev_max = max_coresident_blocks(mode, t.samples_per_lane, g->device);
+    int dev_max = max_coresident_blocks(mode, t.samples_per_lane, t.layout, g->D, g->device);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     if (dev_max <= 0 || sms <= 0) return fail(COS_ERR_CUDA, "cannot query occupancy of the walker kernel");
     int per_sm = dev_max / sms;
     if (t.blocks_per_sm <= 0 || t.blocks_per_sm > per_sm) t.blocks_per_sm = per_sm;
-    const int64_t ch = 32LL * t.samples_per_lane;
+    const int64_t ch = t.layout == 2 ? 32 : 32LL * t.samples_per_lane;   // samples per chunk
     int64_t need = std::max<int64_t>(round_up(std::max<int64_t>(g->S, 1), ch), ch);
     int64_t tile;
     if (t.tile_samples > 0) {
@@ -393,7 +478,9 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
     if (num_samples < 0) return fail(COS_ERR_INVALID, "num_samples must be >= 0");
     if (num_samples > 0 && !t) return fail(COS_ERR_INVALID, "t is NULL");
     if (!eps) return fail(COS_ERR_INVALID, "eps is NULL");
-    if (t_flags & ~(COS_T_HOST | COS_T_SAMPLE_MAJOR)) return fail(COS_ERR_INVALID, "unknown t_flags bits");
+    if (t_flags & ~(COS_T_HOST | COS_T_SAMPLE_MAJOR | COS_T_BORROW)) return fail(COS_ERR_INVALID, "unknown t_flags bits");
+    if ((t_flags & COS_T_BORROW) && (t_flags & (COS_T_HOST | COS_T_SAMPLE_MAJOR)))
+        return fail(COS_ERR_INVALID, "COS_T_BORROW needs a device [D][t_ld] buffer");
     if (!(beta > 0.0) || !std::isfinite(beta)) return fail(COS_ERR_INVALID, "beta must be positive and finite");
     for (int32_t k = 0; k < g->K; ++k)
         if (!std::isfinite(eps[k]) || std::fabs(eps[k]) * beta > 600.0)
@@ -404,7 +491,8 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
     const int64_t S = num_samples;
     const int64_t t_ld = std::max<int64_t>(round_up(S, 128), 128);
     const int32_t D = g->D;
-    if (t_ld * D > g->t_cap) {
+    const bool borrow = (t_flags & COS_T_BORROW) != 0;
+    if (!borrow && t_ld * D > g->t_cap) {
         dfree(g->d_t);
         COS_CUDA(cudaMalloc(&g->d_t, sizeof(double) * t_ld * D), "cudaMalloc t");
         g->t_cap = t_ld * D;
@@ -429,8 +517,8 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
         size_t budget = default_budget_bytes();
         size_t minimum = psb * 128 + ((size_t)8 << 20);
         size_t bytes = std::max(std::min(want, budget), minimum);
-        if (g->tuning.tile_samples > 0)
-            bytes = std::max(bytes, psb * (size_t)round_up(g->tuning.tile_samples, 128) + ((size_t)8 << 20));
+        if (g->tuning.tile_samples > 0)   // a fixed tile fixes the workspace
+            bytes = psb * (size_t)round_up(g->tuning.tile_samples, 128) + ((size_t)8 << 20);
         if (bytes > g->arena_bytes) {
             if (g->d_arena) cudaFree(g->d_arena);
             g->d_arena = nullptr;
@@ -440,8 +528,9 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
         }
     }
     COS_CUDA(cudaMemcpyAsync(g->d_eps, eps, sizeof(double) * g->K, cudaMemcpyHostToDevice, st), "copy eps");
-    COS_CUDA(cudaMemsetAsync(g->d_t, 0, sizeof(double) * t_ld * D, st), "clear t");
-    if (S > 0) {
+    g->t_borrowed = borrow ? t : nullptr;
+    if (!borrow) COS_CUDA(cudaMemsetAsync(g->d_t, 0, sizeof(double) * t_ld * D, st), "clear t");
+    if (S > 0 && !borrow) {
         const bool host = (t_flags & COS_T_HOST) != 0;
         const bool smaj = (t_flags & COS_T_SAMPLE_MAJOR) != 0;
         if (!smaj) {
@@ -485,49 +574,70 @@ static int collect(cos_graph_t g, double* mean_out, cudaStream_t st) {
 
 int cos_evaluate(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean_out, void* stream) {
     if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
-    if (mode < 0 || mode > 2) return fail(COS_ERR_INVALID, "bad mode %d", mode);
-    if (!g->has_samples) return fail(COS_ERR_STATE, "cos_set_samples has not been called");
     DeviceGuard dg(g->device);
     if (!dg.ok) return fail(COS_ERR_CUDA, "cannot select device %d", g->device);
     cudaStream_t st = (cudaStream_t)stream;
-    cos_tuning tn;
-    int64_t tile;
-    int rc = resolve_tuning(g, mode, &tn, &tile);
-    if (rc != COS_OK) return rc;
     WalkParams p;
-    memset(&p, 0, sizeof(p));
-    if (!carve(g, mode, tile, p)) return fail(COS_ERR_STATE, "workspace too small for a tile of %lld samples", (long long)tile);
-    p.levels = g->d_levels;
-    p.row_ptr = g->d_row_ptr;
-    p.edges = g->d_edges;
-    p.slot_kij = g->d_slot_kij;
-    p.L = g->L;
-    p.P = (int32_t)g->P;
-    p.K = g->K;
-    p.D = g->D;
-    p.t = g->d_t;
-    p.eps = g->d_eps;
-    p.beta = g->beta;
-    p.S = g->S;
-    p.t_ld = g->t_ld;
-    p.R = per_sample_out ? per_sample_out : g->d_R;
-    p.partials = g->d_partials;
-    p.ctrl = g->d_ctrl;
-    p.tile = tile;
-    p.rows_per_warp = tn.rows_per_warp;
-    p.timeout_ns = (long long)tn.timeout_ms * 1000000LL;
+    cos_tuning tn;
+    int rc = cosgpu::prepare_walk(g, mode, nullptr, per_sample_out, &p, &tn);
+    if (rc != COS_OK) return rc;
     if (const char* env = getenv("COS_TEST_SKIP_BARRIER_PHASE")) p.skip_barrier_phase = atoi(env);
+    if (g->d_trace) {
+        p.trace = g->d_trace;
+        p.trace_cap = g->trace_cap;
+        COS_CUDA(cudaMemsetAsync(g->d_trace, 0, sizeof(unsigned long long) * 2 * g->trace_cap, st), "reset trace");
+    }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     const int grid = sms * tn.blocks_per_sm;
     COS_CUDA(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), st), "reset control block");
     char msg[256] = {0};
-    rc = launch_walk(mode, tn.samples_per_lane, p, grid, st, msg, sizeof(msg));
+    rc = launch_walk(mode, tn.samples_per_lane, tn.layout, p, grid, st, msg, sizeof(msg));
     if (rc != COS_OK) return fail(rc, "walker launch failed: %s", msg);
     g->last_mode = mode;
     g->last_status_pending = 1;
     if (mean_out) return collect(g, mean_out, st);
     return COS_OK;
+}
+
+int cos_set_trace(cos_graph_t g, int32_t capacity) {
+    if (!g || capacity < 0 || capacity > (1 << 20)) return fail(COS_ERR_INVALID, "bad arguments");
+    DeviceGuard dg(g->device);
+    dfree(g->d_trace);
+    g->trace_cap = 0;
+    if (capacity > 0) {
+        COS_CUDA(cudaMalloc(&g->d_trace, sizeof(unsigned long long) * 2 * capacity), "cudaMalloc trace");
+        COS_CUDA(cudaMemset(g->d_trace, 0, sizeof(unsigned long long) * 2 * capacity), "clear trace");
+        g->trace_cap = capacity;
+    }
+    return COS_OK;
+}
+
+int cos_get_trace(cos_graph_t g, int64_t* out, int32_t capacity, int32_t* count) {
+    if (!g || !out || !count || capacity < 0) return fail(COS_ERR_INVALID, "bad arguments");
+    *count = 0;
+    if (!g->d_trace) return COS_OK;
+    DeviceGuard dg(g->device);
+    const int32_t n = std::min(capacity, g->trace_cap);
+    std::vector<unsigned long long> h((size_t)2 * n);
+    COS_CUDA(cudaMemcpy(h.data(), g->d_trace, sizeof(unsigned long long) * 2 * n, cudaMemcpyDeviceToHost), "read trace");
+    int32_t c = 0;
+    for (int32_t q = 0; q < n; ++q) {
+        if (q > 0 && h[2 * q] == 0) break;
+        out[2 * q] = (int64_t)h[2 * q];
+        out[2 * q + 1] = (int64_t)h[2 * q + 1];
+        c = q + 1;
+    }
+    *count = c;
+    return COS_OK;
+}
+
+int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, double* ep, void* stream) {
+    if (!g || n < 0 || (n > 0 && (!x || !em || !ep))) return fail(COS_ERR_INVALID, "bad arguments");
+    DeviceGuard dg(g->device);
+    if (n == 0) return COS_OK;
+    int rc = launch_exp_pair(x, n, g->d_exp_tab, em, ep, (cudaStream_t)stream);
+    return rc == COS_OK ? COS_OK : fail(rc, "exp self-test launch failed");
 }
 
 int cos_get_result(cos_graph_t g, double* mean_out, void* stream) {
@@ -546,6 +656,8 @@ int graph_view(cos_graph_t g, GraphView* out) {
     out->row_ptr = g->d_row_ptr;
     out->edges = g->d_edges;
     out->slot_kij = g->d_slot_kij;
+    out->kind_slot = g->d_kind_slot;
+    out->exp_tab = g->d_exp_tab;
     out->L = g->L;
     out->P = (int32_t)g->P;
     out->K = g->K;
@@ -553,6 +665,55 @@ int graph_view(cos_graph_t g, GraphView* out) {
     out->Wmax = g->Wmax;
     out->device = g->device;
     out->count_overflow = g->count_overflow ? 1 : 0;
+    out->widths_host = g->widths.data();
+    out->S = g->has_samples ? g->S : -1;
+    return COS_OK;
+}
+
+int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sample_out, WalkParams* out,
+                 cos_tuning* tn_out) {
+    if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
+    if (mode < 0 || mode > 2) return fail(COS_ERR_INVALID, "bad mode %d", mode);
+    if (!g->has_samples) return fail(COS_ERR_STATE, "cos_set_samples has not been called");
+    const cos_tuning saved = g->tuning;
+    if (force) {
+        if (force->samples_per_lane > 0) g->tuning.samples_per_lane = force->samples_per_lane;
+        if (force->rows_per_warp > 0) g->tuning.rows_per_warp = force->rows_per_warp;
+        if (force->tile_samples > 0) g->tuning.tile_samples = force->tile_samples;
+        if (force->blocks_per_sm > 0) g->tuning.blocks_per_sm = force->blocks_per_sm;
+        if (force->timeout_ms > 0) g->tuning.timeout_ms = force->timeout_ms;
+        if (force->layout > 0) g->tuning.layout = force->layout;
+    }
+    cos_tuning tn;
+    int64_t tile;
+    int rc = resolve_tuning(g, mode, &tn, &tile);
+    g->tuning = saved;
+    if (rc != COS_OK) return rc;
+    WalkParams& p = *out;
+    memset(&p, 0, sizeof(p));
+    if (!carve(g, mode, tile, p)) return fail(COS_ERR_STATE, "workspace too small for a tile of %lld samples", (long long)tile);
+    p.levels = g->d_levels;
+    p.row_ptr = g->d_row_ptr;
+    p.edges = g->d_edges;
+    p.slot_kij = g->d_slot_kij;
+    p.kind_slot = g->d_kind_slot;
+    p.exp_tab = g->d_exp_tab;
+    p.L = g->L;
+    p.P = (int32_t)g->P;
+    p.K = g->K;
+    p.D = g->D;
+    p.t = g->t_borrowed ? g->t_borrowed : g->d_t;
+    p.eps = g->d_eps;
+    p.beta = g->beta;
+    p.S = g->S;
+    p.t_ld = g->t_ld;
+    p.R = per_sample_out ? per_sample_out : g->d_R;
+    p.partials = g->d_partials;
+    p.ctrl = g->d_ctrl;
+    p.tile = tile;
+    p.rows_per_warp = tn.rows_per_warp;
+    p.timeout_ns = (long long)tn.timeout_ms * 1000000LL;
+    if (tn_out) *tn_out = tn;
     return COS_OK;
 }
 

@@ -51,9 +51,9 @@ struct WalkParams {
     // workspace, carved from one arena per tile
     void* slab[2];             // [nchunk][W][CH] node values, ping-pong between levels
     void* gtab;                // [nchunk][P][CH] propagator table of the tile
-    double* fac_m;             // [K][D][tile] exp(-eps_k t_i)
-    double* fac_p;             // [K][D][tile] exp(+eps_k t_i)
     double* coef;              // [2K]: -1/(1+e^{-beta eps_k}) (tau >= 0), 1/(1+e^{beta eps_k}) (tau < 0)
+    const int32_t* kind_slot;  // [K+1]: slots of kind k are [kind_slot[k], kind_slot[k+1])
+    const double* exp_tab;     // [128]: 2^{j/64}, then 2^{-j/64}, j = 0..63
     void* R;                   // [S] sink value per sample (double, or int64 in count mode)
     double* partials;          // [ceil(S/4096)] compensated partial sums
     Ctrl* ctrl;
@@ -61,6 +61,10 @@ struct WalkParams {
     int32_t rows_per_warp;
     int32_t skip_barrier_phase;  // test hook: CTA 0 leaves before this barrier (0 = off)
     long long timeout_ns;
+    unsigned long long* trace;   // optional: [2*trace_cap] (globaltimer ns, phase id) per barrier
+    int32_t trace_cap;
+    int32_t pad2;
+    double* mean_out;            // optional second destination of the mean (batched launches)
 };
 
 constexpr int kThreads = 256;           // 8 warps per CTA
@@ -78,16 +82,32 @@ struct GraphView {
     int64_t Wmax;
     int device;
     int count_overflow;
+    const int32_t* kind_slot;
+    const double* exp_tab;
+    const int64_t* widths_host;   // [L], host copy of the level widths
+    int64_t S;                    // attached samples (-1: none)
 };
 int graph_view(cos_graph_t g, GraphView* out);
+// Resolve the launch tuning of `mode` (fields of `force` > 0 override the graph's own
+// tuning) and fill the walker parameters for the graph's current samples.
+int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sample_out, WalkParams* out,
+                 cos_tuning* tn_out);
 // Records a message for cos_last_error() and returns code.
 int set_error(int code, const char* fmt, ...);
 
 // Host launcher implemented in cos_walk.cu.  Returns COS_OK or COS_ERR_CUDA and
 // fills msg on failure.
-int launch_walk(int mode, int vec, const WalkParams& p, int grid, cudaStream_t stream, char* msg, size_t msglen);
-// Co-resident persistent grid size for (mode, vec); 0 on failure.
-int max_coresident_blocks(int mode, int vec, int device);
+// layout: 1 = wide, 2 = grouped (cos_tuning.layout).
+int launch_walk(int mode, int vec, int layout, const WalkParams& p, int grid, cudaStream_t stream, char* msg,
+                size_t msglen);
+// Co-resident persistent grid size for (mode, vec, layout) with D time variables; 0 on failure.
+int max_coresident_blocks(int mode, int vec, int layout, int D, int device);
+// Dynamic shared memory of a launch (the propagator phase keeps 32 samples x D times
+// in shared memory), and the once-per-kernel opt-in to sizes above 48 KB.
+int walk_smem_bytes(int mode, int D);
+int prepare_kernel_attrs(const void* kernel, int smem_bytes);
+// e^{-x} and e^{+x} with the evaluator's table-driven exponentials (self test).
+int launch_exp_pair(const double* x, int64_t n, const double* tab, double* em, double* ep, cudaStream_t stream);
 // Transpose t from [S][D] (src_ld = D) into [D][t_ld].
 int launch_transpose(const double* src, int64_t S, int32_t D, double* dst, int64_t t_ld, cudaStream_t stream);
 

@@ -1,0 +1,556 @@
+// Device work items of the CoS evaluator, shared by the single-graph cooperative
+// kernel (cos_walk.cu, grid barriers between phases) and the batched work-queue
+// kernel (cos_batch.cu, per-graph dependency counters).  Every function below
+// executes one CTA-sized unit of one phase.
+//
+// Layout (node x sample, App. A "Cache and locality"): the samples of a tile are
+// split into chunks of CHV consecutive samples.  Node values of one level are
+// stored [chunk][row][CHV], the propagator table [chunk][slot][CHV], exponential
+// factors [K][D][tile].  Two level-walk layouts share this storage scheme:
+//   wide    (CHV = 32*V): a warp owns one row at a time, lane q holds samples
+//           [q*V, q*V+V) of the chunk; one warp instruction reads one contiguous run.
+//   grouped (CHV = 32):   a warp serves V rows at once, each row owned by a group
+//           of 32/V lanes holding V samples each; the parent slice of a chunk
+//           (W x 32 values) stays small enough for L2.
+// Either way a lane moves V values per access (16 B for float with V = 4).
+#pragma once
+
+#include <cstdint>
+
+#include "cos_internal.cuh"
+
+namespace cosgpu {
+
+enum Layout : int { LAYOUT_WIDE = 0, LAYOUT_GROUPED = 1 };
+
+template <int V, int LAYOUT>
+__host__ __device__ constexpr int chunk_samples() {
+    return LAYOUT == LAYOUT_WIDE ? 32 * V : 32;
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ---------------------------------------------------------------- vector access
+
+template <typename T, int V>
+struct alignas(sizeof(T) * V) VecT {
+    T v[V];
+};
+
+template <typename T, int V>
+__device__ __forceinline__ VecT<T, V> load_cg(const T* ptr) {  // L2 only: data written earlier by this kernel
+    VecT<T, V> r;
+    constexpr int bytes = sizeof(T) * V;
+    if constexpr (bytes == 32) {
+        const uint4* q = reinterpret_cast<const uint4*>(ptr);
+        uint4 a = __ldcg(q), b = __ldcg(q + 1);
+        memcpy(&r.v[0], &a, 16);
+        memcpy(reinterpret_cast<char*>(&r.v[0]) + 16, &b, 16);
+    } else if constexpr (bytes == 16) {
+        uint4 a = __ldcg(reinterpret_cast<const uint4*>(ptr));
+        memcpy(&r.v[0], &a, 16);
+    } else if constexpr (bytes == 8) {
+        uint2 a = __ldcg(reinterpret_cast<const uint2*>(ptr));
+        memcpy(&r.v[0], &a, 8);
+    } else {
+        unsigned a = __ldcg(reinterpret_cast<const unsigned*>(ptr));
+        memcpy(&r.v[0], &a, 4);
+    }
+    return r;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ VecT<T, V> load_ca(const T* ptr) {  // L1-cacheable coherent load
+    return *reinterpret_cast<const VecT<T, V>*>(ptr);
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void store_cg(T* ptr, const VecT<T, V>& x) {
+    constexpr int bytes = sizeof(T) * V;
+    if constexpr (bytes == 32) {
+        uint4 a, b;
+        memcpy(&a, &x.v[0], 16);
+        memcpy(&b, reinterpret_cast<const char*>(&x.v[0]) + 16, 16);
+        __stcg(reinterpret_cast<uint4*>(ptr), a);
+        __stcg(reinterpret_cast<uint4*>(ptr) + 1, b);
+    } else if constexpr (bytes == 16) {
+        uint4 a;
+        memcpy(&a, &x.v[0], 16);
+        __stcg(reinterpret_cast<uint4*>(ptr), a);
+    } else if constexpr (bytes == 8) {
+        uint2 a;
+        memcpy(&a, &x.v[0], 8);
+        __stcg(reinterpret_cast<uint2*>(ptr), a);
+    } else {
+        unsigned a;
+        memcpy(&a, &x.v[0], 4);
+        __stcg(reinterpret_cast<unsigned*>(ptr), a);
+    }
+}
+
+// ---------------------------------------------------------------- mode traits
+
+template <int MODE>
+struct Traits;
+template <>
+struct Traits<COS_MODE_FP64> {       // everything in double
+    using Val = double;
+    using Prop = double;
+    using SinkAcc = double;
+    static constexpr bool kCount = false;
+};
+template <>
+struct Traits<COS_MODE_FP32_MIXED> { // float propagators and products, double sink
+    using Val = float;
+    using Prop = float;
+    using SinkAcc = double;
+    static constexpr bool kCount = false;
+};
+template <>
+struct Traits<COS_MODE_COUNT_I64> {  // unit weights, sums modulo 2^64
+    using Val = unsigned long long;
+    using Prop = unsigned long long;
+    using SinkAcc = unsigned long long;
+    static constexpr bool kCount = true;
+};
+
+__device__ __forceinline__ double madd(double p, double g, double acc) { return fma(p, g, acc); }
+__device__ __forceinline__ float madd(float p, float g, float acc) { return fmaf(p, g, acc); }
+
+__device__ __forceinline__ void neumaier_add(double& sum, double& comp, double y) {
+    const double u = sum + y;
+    if (fabs(sum) >= fabs(y)) comp += (sum - u) + y;
+    else comp += (y - u) + sum;
+    sum = u;
+}
+
+// Samples of the tile that starts at sample `base` (tile_n = samples rounded up to the chunk).
+struct TileCtx {
+    int64_t base;
+    int64_t tile_n;
+    int nch;
+};
+
+template <int CHV>
+__device__ __forceinline__ TileCtx tile_ctx(const WalkParams& p, int64_t tix) {
+    TileCtx tc;
+    tc.base = tix * p.tile;
+    const int64_t n = min(p.tile, p.S - tc.base);
+    tc.tile_n = (n + CHV - 1) / CHV * CHV;
+    tc.nch = (int)(tc.tile_n / CHV);
+    return tc;
+}
+
+// ---------------------------------------------------------------- phase: coefficients (1 item)
+
+// The tau >= 0 and tau < 0 prefactors of every kind.
+__device__ __forceinline__ void item_coef(const WalkParams& p) {
+    for (int k = threadIdx.x; k < p.K; k += blockDim.x) {
+        const double be = p.beta * p.eps[k];
+        p.coef[k] = -1.0 / (1.0 + exp(-be));        // tau >= 0: -e^{-eps tau} / (1 + e^{-beta eps})
+        p.coef[p.K + k] = 1.0 / (1.0 + exp(be));    // tau <  0: +e^{-eps (tau+beta)} / (1 + e^{-beta eps})
+    }
+}
+
+// ---------------------------------------------------------------- exponentials
+
+// e^{-x} and e^{+x} in double precision for |x| <= 708, by the table-driven method of
+// P. T. P. Tang (ACM TOMS 15, 1989): x = (64 m + j) ln2/64 + r with |r| <= ln2/128,
+// e^{+-x} = 2^{+-m} 2^{+-j/64} e^{+-r}; e^{+-r} = 1 + E +- O with the even and odd parts
+// of the Taylor series through r^5 (truncation below 4e-17 relative).  The 64 values
+// 2^{j/64} (and 2^{-j/64}) are read from `tab` ([0..63] = 2^{j/64}, [64..127] = 2^{-j/64}).
+__device__ __forceinline__ void exp_pair(double x, const double* __restrict__ tab, double& em, double& ep) {
+    const double inv = 92.33248261689366;                  // 64 / ln 2 (only rounds n)
+    const double c_hi = 0.01083042469326756;               // ln2/64 to 32 significant bits: n*c_hi is exact
+    const double c_lo = 2.9815858269852933e-12;            // ln2/64 - c_hi
+    const double nd = rint(x * inv);
+    const int n = (int)nd;
+    double r = fma(-nd, c_hi, x);
+    r = fma(-nd, c_lo, r);
+    const double r2 = r * r;
+    const double even = r2 * fma(r2, fma(r2, 1.0 / 720.0, 1.0 / 24.0), 0.5);      // cosh(r) - 1
+    const double odd = r * fma(r2, fma(r2, 1.0 / 120.0, 1.0 / 6.0), 1.0);         // sinh(r)
+    const int j = n & 63;
+    const int m = n >> 6;                                                       // floor(n / 64)
+    // e^{+x} = 2^m 2^{j/64} (1 + even + odd);  e^{-x} = 2^{-m} 2^{-j/64} (1 + even - odd)
+    const double tp = __ldg(tab + j), tm = __ldg(tab + 64 + j);
+    const double vp = fma(tp, even + odd, tp);
+    const double vm = fma(tm, even - odd, tm);
+    ep = __hiloint2double(__double2hiint(vp) + (m << 20), __double2loint(vp));
+    em = __hiloint2double(__double2hiint(vm) - (m << 20), __double2loint(vm));
+}
+
+// ---------------------------------------------------------------- phase: propagators
+
+// Item = (chunk, kind k); count mode: item = chunk (root values only).
+template <int MODE>
+__device__ __forceinline__ int prop_items(const WalkParams& p, const TileCtx& tc) {
+    if constexpr (Traits<MODE>::kCount) return tc.nch;
+    return tc.nch * p.K;
+}
+
+// Shared memory of one propagator item: times and exponentials of 32 samples.
+__host__ __device__ constexpr int prop_smem_bytes(int D) { return 4 * 32 * 8 * D; }
+
+// For each 32-sample run of the chunk: load t_i, form e^{-eps_k t_i} (times the tau >= 0
+// and tau < 0 prefactors) and e^{+eps_k t_i} for every time i in shared memory, then
+// write every propagator slot q = (k, i, j) of this kind:
+//   G[c][q][s] = (t_i >= t_j ? coef+ : coef-) e^{-eps_k t_i} e^{+eps_k t_j}
+// formed in double, rounded once to the propagator type.  The kind-k slots are the
+// contiguous range [kind_slot[k], kind_slot[k+1]).  The first kind also writes the
+// chunk's root values (node 0 holds 1, Fig. 1 caption).
+template <int MODE, int CHV>
+__device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& tc, int item, double* sm) {
+    using Tr = Traits<MODE>;
+    using Prop = typename Tr::Prop;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nk = Tr::kCount ? 1 : p.K;
+    const int c = item / nk;
+    const int k = item - c * nk;
+    if (warp == 0 && k == 0)
+        for (int v = lane; v < CHV; v += 32)
+            static_cast<typename Tr::Val*>(p.slab[0])[(int64_t)c * CHV + v] = (typename Tr::Val)1;
+    if constexpr (!Tr::kCount) {
+        const int D = p.D;
+        double* st = sm;              // [D][32] times
+        double* sp = sm + 32 * D;     // [D][32] coef+ e^{-eps t}
+        double* sn = sm + 64 * D;     // [D][32] coef- e^{-eps t}
+        double* se = sm + 96 * D;     // [D][32] e^{+eps t}
+        const double eps = p.eps[k], cpos = p.coef[k], cneg = p.coef[p.K + k];
+        const int q0 = __ldg(p.kind_slot + k), q1 = __ldg(p.kind_slot + k + 1);
+        Prop* gt = static_cast<Prop*>(p.gtab) + (int64_t)c * p.P * CHV;
+        for (int sub = 0; sub < CHV / 32; ++sub) {
+            const int64_t s0 = tc.base + (int64_t)c * CHV + sub * 32;
+            for (int x = threadIdx.x; x < 32 * D; x += blockDim.x) {
+                const int i = x >> 5, s = x & 31;
+                const double t = p.t[(int64_t)i * p.t_ld + s0 + s];
+                double em, ep;
+                exp_pair(eps * t, p.exp_tab, em, ep);
+                st[x] = t;
+                sp[x] = cpos * em;
+                sn[x] = cneg * em;
+                se[x] = ep;
+            }
+            __syncthreads();
+            for (int q = q0 + warp; q < q1; q += kWarps) {
+                const int i = __ldg(p.slot_kij + 3 * q + 1), j = __ldg(p.slot_kij + 3 * q + 2);
+                const double a = (st[i * 32 + lane] >= st[j * 32 + lane]) ? sp[i * 32 + lane] : sn[i * 32 + lane];
+                __stcg(gt + (int64_t)q * CHV + sub * 32 + lane, (Prop)(a * se[j * 32 + lane]));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- phase: one level
+
+__device__ __forceinline__ int level_items(const WalkParams& p, const LevelDesc& ld, const TileCtx& tc) {
+    const int rows_per_item = kWarps * p.rows_per_warp;
+    return tc.nch * ((ld.width + rows_per_item - 1) / rows_per_item);
+}
+
+// Store the V accumulated samples of row r (or, in the sink level, the per-sample results).
+// `off` = position of this lane's first sample inside the chunk.
+template <int MODE, int V, int CHV>
+__device__ __forceinline__ void store_row(const WalkParams& p, bool sink, typename Traits<MODE>::Val* child, int c,
+                                          int width, int r, const TileCtx& tc, int off,
+                                          const typename Traits<MODE>::Val (&acc)[V]) {
+    using Tr = Traits<MODE>;
+    using Val = typename Tr::Val;
+    if (sink) {
+        using Out = typename Tr::SinkAcc;
+        Out* R = static_cast<Out*>(p.R);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int64_t s = tc.base + (int64_t)c * CHV + off + v;
+            if (s < p.S) R[s] = (Out)acc[v];
+        }
+    } else {
+        VecT<Val, V> out;
+#pragma unroll
+        for (int v = 0; v < V; ++v) out.v[v] = acc[v];
+        store_cg<Val, V>(child + ((int64_t)c * width + r) * CHV + off, out);
+    }
+}
+
+// Sink row in FP32 mixed mode: in-edges accumulated as exact double products in double.
+// pc / gc already point at this lane's samples of the chunk.
+template <int V, int CHV>
+__device__ __forceinline__ void sink_row_mixed(const WalkParams& p, const float* pc, const float* gc, int beg, int end,
+                                               int c, const TileCtx& tc, int off) {
+    double acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.0;
+    for (int e = beg; e < end; ++e) {
+        const int2 m = __ldg(p.edges + e);
+        const VecT<float, V> pv = load_cg<float, V>(pc + (int64_t)m.x * CHV);
+        const VecT<float, V> gv = load_ca<float, V>(gc + (int64_t)m.y * CHV);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += (double)pv.v[v] * (double)gv.v[v];   // exact product
+    }
+    double* R = static_cast<double*>(p.R);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int64_t s = tc.base + (int64_t)c * CHV + off + v;
+        if (s < p.S) R[s] = acc[v];
+    }
+}
+
+// Wide layout (CHV = 32*V).  Item = (chunk, block of kWarps * rows_per_warp rows),
+// chunk-major.  A warp takes rows_per_warp (<= 31) consecutive rows, whose in-edges
+// form one contiguous CSR range; it streams that range in windows of 32 edges
+// (metadata loaded by the lanes, broadcast by shuffles), keeps U edges' parent and
+// propagator loads in flight, and closes a row (store, reset) at its last in-edge.
+// Every row is the sum of its in-edges in CSR order, one multiply-add per edge per
+// sample.
+template <int MODE, int V>
+__device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, const TileCtx& tc, int item) {
+    using Tr = Traits<MODE>;
+    using Val = typename Tr::Val;
+    using Prop = typename Tr::Prop;
+    constexpr int CHV = 32 * V;
+    constexpr int U = 4;
+    const LevelDesc ld = p.levels[l];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rpw = p.rows_per_warp;
+    const int rows_per_item = kWarps * rpw;
+    const int nrb = (ld.width + rows_per_item - 1) / rows_per_item;
+    const int c = item / nrb;
+    const int rb = item - c * nrb;
+    const bool sink = (l == p.L - 1);
+    const int off = lane * V;
+    const Val* pc = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * ld.prev_width * CHV + off;
+    Val* child = static_cast<Val*>(p.slab[l & 1]);
+    const Prop* gc = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV + off;
+    const int r0 = rb * rows_per_item + warp * rpw;
+    if (r0 >= ld.width) return;
+    const int nr = min(rpw, ld.width - r0);
+    if constexpr (MODE == COS_MODE_FP32_MIXED) {
+        if (sink) {
+            for (int r = r0; r < r0 + nr; ++r) {
+                const int node = ld.row_begin + r;
+                sink_row_mixed<V, CHV>(p, pc, gc, __ldg(p.row_ptr + node), __ldg(p.row_ptr + node + 1), c, tc, off);
+            }
+            return;
+        }
+    }
+    // lane j <= nr holds rp_j = row_ptr of row r0 + j
+    const int rp = (lane <= nr) ? __ldg(p.row_ptr + ld.row_begin + r0 + lane) : 0;
+    const int rp_next = __shfl_down_sync(0xffffffffu, rp, 1);
+    const int beg = __shfl_sync(0xffffffffu, rp, 0);
+    const int end = __shfl_sync(0xffffffffu, rp, nr);
+    const unsigned nonempty = __ballot_sync(0xffffffffu, lane < nr && rp_next > rp);
+    const unsigned empty = __ballot_sync(0xffffffffu, lane < nr && rp_next == rp);
+    Val acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+    for (unsigned m = empty; m; m &= m - 1)   // rows without in-edges hold 0
+        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(m) - 1, tc, off, acc);
+    unsigned rows_left = nonempty;
+    for (int w0 = beg; w0 < end; w0 += 32) {
+        const int n = min(32, end - w0);
+        const int2 meta = (lane < n) ? __ldg(p.edges + w0 + lane) : make_int2(0, 0);
+        // bit q set <=> edge w0+q is the last in-edge of its row
+        const int pos = rp_next - 1 - w0;
+        const unsigned ends = __reduce_or_sync(
+            0xffffffffu, (lane < nr && rp_next > rp && pos >= 0 && pos < 32) ? (1u << pos) : 0u);
+        for (int q0 = 0; q0 < n; q0 += U) {
+            VecT<Val, V> pv[U];
+            VecT<Prop, V> gv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u;
+                const int src = __shfl_sync(0xffffffffu, meta.x, q & 31);
+                pv[u] = load_cg<Val, V>(pc + (int64_t)(q < n ? src : 0) * CHV);
+                if constexpr (!Tr::kCount) {
+                    const int slot = __shfl_sync(0xffffffffu, meta.y, q & 31);
+                    gv[u] = load_ca<Prop, V>(gc + (int64_t)(q < n ? slot : 0) * CHV);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u;
+                if (q < n) {
+                    if constexpr (Tr::kCount) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] += pv[u].v[v];
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = madd(pv[u].v[v], gv[u].v[v], acc[v]);
+                    }
+                    if ((ends >> q) & 1u) {
+                        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(rows_left) - 1, tc, off, acc);
+                        rows_left &= rows_left - 1;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Grouped layout (CHV = 32).  Same items and the same per-row order as the wide
+// layout; a warp's rows are split into V groups of consecutive rows and each group
+// of 32/V lanes streams the CSR edge range of its own rows.
+template <int MODE, int V>
+__device__ __forceinline__ void item_level_grouped(const WalkParams& p, int l, const TileCtx& tc, int item) {
+    using Tr = Traits<MODE>;
+    using Val = typename Tr::Val;
+    using Prop = typename Tr::Prop;
+    constexpr int CHV = 32;
+    constexpr int LPR = 32 / V;   // lanes per row
+    constexpr int U = 4;          // edges in flight per group
+    const LevelDesc ld = p.levels[l];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane / LPR, gl = lane - gid * LPR;
+    const int off = gl * V;
+    const int rpw = p.rows_per_warp;
+    const int rows_per_item = kWarps * rpw;
+    const int nrb = (ld.width + rows_per_item - 1) / rows_per_item;
+    const int c = item / nrb;
+    const int rb = item - c * nrb;
+    const bool sink = (l == p.L - 1);
+    const Val* pc = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * ld.prev_width * CHV + off;
+    Val* child = static_cast<Val*>(p.slab[l & 1]);
+    const Prop* gc = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV + off;
+    const int r0 = rb * rows_per_item + warp * rpw;
+    if (r0 >= ld.width) return;
+    const int nr = min(rpw, ld.width - r0);
+    if constexpr (MODE == COS_MODE_FP32_MIXED) {
+        if (sink) {
+            if (gid == 0)
+                for (int r = r0; r < r0 + nr; ++r) {
+                    const int node = ld.row_begin + r;
+                    sink_row_mixed<V, CHV>(p, pc, gc, __ldg(p.row_ptr + node), __ldg(p.row_ptr + node + 1), c, tc, off);
+                }
+            return;
+        }
+    }
+    // lane j <= nr holds rp_j = row_ptr of row r0 + j
+    const int rp = (lane <= nr) ? __ldg(p.row_ptr + ld.row_begin + r0 + lane) : 0;
+    const int rp_next = __shfl_down_sync(0xffffffffu, rp, 1);
+    const unsigned nonempty = __ballot_sync(0xffffffffu, lane < nr && rp_next > rp);
+    // rows [ga, gb) (relative to r0) belong to this lane's group
+    const int ga = (gid * nr) / V, gb = ((gid + 1) * nr) / V;
+    const int ebeg = __shfl_sync(0xffffffffu, rp, ga);
+    const int eend = __shfl_sync(0xffffffffu, rp, gb);
+    const unsigned group_rows = ((1u << gb) - 1u) & ~((1u << ga) - 1u);
+    Val acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+    for (unsigned m = group_rows & ~nonempty; m; m &= m - 1)   // rows without in-edges hold 0
+        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(m) - 1, tc, off, acc);
+    unsigned rows_left = group_rows & nonempty;
+    int cur = rows_left ? __ffs(rows_left) - 1 : 0;
+    int cur_end = __shfl_sync(0xffffffffu, rp, (cur + 1) & 31);
+    const int len = eend - ebeg;
+    int maxlen = len;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+    for (int i0 = 0; i0 < maxlen; i0 += U) {
+        VecT<Val, V> pv[U];
+        VecT<Prop, V> gv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = ebeg + i0 + u;
+            const int2 m = (i0 + u < len) ? __ldg(p.edges + e) : make_int2(0, 0);
+            pv[u] = load_cg<Val, V>(pc + (int64_t)m.x * CHV);
+            if constexpr (!Tr::kCount) gv[u] = load_ca<Prop, V>(gc + (int64_t)m.y * CHV);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = ebeg + i0 + u;
+            const bool valid = (i0 + u < len);
+            if (valid) {
+                if constexpr (Tr::kCount) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] += pv[u].v[v];
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] = madd(pv[u].v[v], gv[u].v[v], acc[v]);
+                }
+            }
+            const bool closes = valid && (e + 1 == cur_end);
+            if (closes) {
+                store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + cur, tc, off, acc);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+                rows_left &= rows_left - 1;
+                cur = rows_left ? __ffs(rows_left) - 1 : cur;
+            }
+            // every lane takes part in the shuffle; only closing groups change their row end
+            const int next_end = __shfl_sync(0xffffffffu, rp, (cur + 1) & 31);
+            if (closes) cur_end = next_end;
+        }
+    }
+}
+
+template <int MODE, int V, int LAYOUT>
+__device__ __forceinline__ void item_level(const WalkParams& p, int l, const TileCtx& tc, int item) {
+    if constexpr (LAYOUT == LAYOUT_WIDE) item_level_wide<MODE, V>(p, l, tc, item);
+    else item_level_grouped<MODE, V>(p, l, tc, item);
+}
+
+// ---------------------------------------------------------------- phase: sample reduction
+
+// Compensated partial sums of R over blocks of kReduceBlock samples, in index order:
+// lane q sums its 128 consecutive samples, lane partials are then added in lane order.
+// Item = kWarps consecutive blocks (one per warp).
+__device__ __forceinline__ int partial_items(const WalkParams& p) {
+    const int64_t nblk = (p.S + kReduceBlock - 1) / kReduceBlock;
+    return (int)((nblk + kWarps - 1) / kWarps);
+}
+
+template <int MODE>
+__device__ __forceinline__ void item_partials(const WalkParams& p, int item) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nblk = (p.S + kReduceBlock - 1) / kReduceBlock;
+    const int64_t b = (int64_t)item * kWarps + warp;
+    if (b >= nblk) return;
+    constexpr int per_lane = kReduceBlock / 32;
+    double sum = 0.0, comp = 0.0;
+    const int64_t s0 = b * kReduceBlock + (int64_t)lane * per_lane;
+    for (int q = 0; q < per_lane; ++q) {
+        const int64_t s = s0 + q;
+        if (s >= p.S) break;
+        double x;
+        if constexpr (MODE == COS_MODE_COUNT_I64) x = (double)static_cast<const long long*>(p.R)[s];
+        else x = static_cast<const double*>(p.R)[s];
+        neumaier_add(sum, comp, x);
+    }
+    const double mine = sum + comp;
+    double bs = 0.0, bc = 0.0;
+    for (int q = 0; q < 32; ++q) neumaier_add(bs, bc, __shfl_sync(0xffffffffu, mine, q));
+    if (lane == 0) p.partials[b] = bs + bc;
+}
+
+// Final compensated sum of the partials in block order; the mean over samples.
+__device__ __forceinline__ void item_final(const WalkParams& p) {
+    if (threadIdx.x != 0) return;
+    const int64_t nblk = (p.S + kReduceBlock - 1) / kReduceBlock;
+    double sum = 0.0, comp = 0.0;
+    for (int64_t b = 0; b < nblk; ++b) neumaier_add(sum, comp, p.partials[b]);
+    p.ctrl->sum = sum;
+    p.ctrl->comp = comp;
+    p.ctrl->mean = p.S > 0 ? (sum + comp) / (double)p.S : 0.0;
+    if (p.mean_out) *p.mean_out = p.ctrl->mean;
+}
+
+}  // namespace cosgpu

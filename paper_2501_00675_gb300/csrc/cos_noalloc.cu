@@ -86,7 +86,7 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     if (off > (size_t)COS_STATIC_SCRATCH_BYTES)
         return set_error(COS_ERR_INVALID, "num_samples %lld exceeds the static scratch limit", (long long)S);
     const size_t per_sample = 2 * val * (size_t)gv.Wmax +
-                              (mode == COS_MODE_COUNT_I64 ? 0 : val * (size_t)gv.P + 2 * sizeof(double) * gv.K * gv.D);
+                              (mode == COS_MODE_COUNT_I64 ? 0 : val * (size_t)gv.P);
     const size_t room = (size_t)COS_STATIC_SCRATCH_BYTES - off - 5 * 256;
     int64_t tile = (int64_t)(room / per_sample) / ch * ch;
     if (tile < ch)
@@ -107,16 +107,14 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     if (mode != COS_MODE_COUNT_I64) {
         p.gtab = b + off;
         off += align256(val * gv.P * tile);
-        p.fac_m = reinterpret_cast<double*>(b + off);
-        off += align256(sizeof(double) * gv.K * gv.D * tile);
-        p.fac_p = reinterpret_cast<double*>(b + off);
-        off += align256(sizeof(double) * gv.K * gv.D * tile);
     }
     if (off > (size_t)COS_STATIC_SCRATCH_BYTES) return set_error(COS_ERR_INVALID, "static scratch layout overflow");
     p.levels = gv.levels;
     p.row_ptr = gv.row_ptr;
     p.edges = gv.edges;
     p.slot_kij = gv.slot_kij;
+    p.kind_slot = gv.kind_slot;
+    p.exp_tab = gv.exp_tab;
     p.L = gv.L;
     p.P = gv.P;
     p.K = gv.K;
@@ -132,7 +130,7 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     p.timeout_ns = 10000LL * 1000000LL;
 
     int per_sm = 0, sms = 0;
-    const int dev_max = max_coresident_blocks(mode, vec, gv.device);
+    const int dev_max = max_coresident_blocks(mode, vec, 1, gv.D, gv.device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gv.device);
     if (dev_max <= 0 || sms <= 0) return set_error(COS_ERR_CUDA, "cannot query occupancy");
     per_sm = dev_max / sms;
@@ -141,7 +139,7 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     cudaError_t e = cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), st);
     if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "clear control block: %s", cudaGetErrorString(e));
     char msg[256] = {0};
-    rc = launch_walk(mode, vec, p, sms * per_sm, st, msg, sizeof(msg));
+    rc = launch_walk(mode, vec, 1, p, sms * per_sm, st, msg, sizeof(msg));
     if (rc != COS_OK) return set_error(rc, "walker launch failed: %s", msg);
     if (!mean_out) return COS_OK;
     Ctrl c;

@@ -1,0 +1,308 @@
+"""Continuous-batching evaluation server on one GPU.
+
+Requests are (resident graph, number of samples, sample seed).  The server keeps
+the graph structures resident (created once; every in-flight request on a graph
+uses its own handle from ``cos_graph_share``, so several requests on one graph
+run at once), admits requests in arrival order while their device memory fits a
+budget, and keeps several persistent batched launches (``cos_batch_*``) in
+flight on separate streams: requests that arrive while others run are admitted
+as memory frees up and go into the next launch, whose work items start on the SMs
+as the running launch drains.  Latency is measured from submission to the moment
+the launch that carried the request is seen complete.
+
+The evaluation itself runs in the CUDA library; this module only schedules.
+``AdmissionController`` holds the host-side policy and has no GPU dependency.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+from typing import Deque, Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+# ---------------------------------------------------------------------------- policy (no GPU)
+
+@dataclasses.dataclass
+class RequestSpec:
+    graph_id: int
+    num_samples: int
+    seed: int
+
+
+@dataclasses.dataclass
+class Request:
+    spec: RequestSpec
+    need_bytes: int
+    t_submit: float
+    rid: int
+    t_admit: float = 0.0
+    t_launch: float = 0.0
+    t_done: float = 0.0
+    status: str = "queued"        # queued | admitted | running | done | shed | failed
+    mean: float = float("nan")
+    result = None                 # device tensor of per-sample values
+    error: Optional[str] = None
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+
+class AdmissionController:
+    """FIFO admission under a device-memory budget with a bounded wait queue.
+
+    offer():  enqueue, or shed at once when the queue is full or the request can
+              never fit the budget.
+    admit():  pop queued requests in arrival order while their memory fits what is
+              left of the budget (head-of-line: a request that does not fit yet
+              blocks the ones behind it, so large requests are not starved).
+    release(): return a finished request's memory.
+    """
+
+    def __init__(self, budget_bytes: int, max_queue: int = 1024):
+        self.budget = int(budget_bytes)
+        self.max_queue = int(max_queue)
+        self.in_use = 0
+        self.peak = 0
+        self.queue: Deque[Request] = collections.deque()
+        self.shed = 0
+        self.admitted = 0
+
+    def offer(self, req: Request) -> bool:
+        if req.need_bytes > self.budget or len(self.queue) >= self.max_queue:
+            req.status = "shed"
+            self.shed += 1
+            return False
+        self.queue.append(req)
+        return True
+
+    def admit(self, max_n: int) -> List[Request]:
+        out = []
+        while self.queue and len(out) < max_n and self.in_use + self.queue[0].need_bytes <= self.budget:
+            r = self.queue.popleft()
+            self.in_use += r.need_bytes
+            self.peak = max(self.peak, self.in_use)
+            r.status = "admitted"
+            out.append(r)
+        self.admitted += len(out)
+        return out
+
+    def release(self, req: Request):
+        self.in_use -= req.need_bytes
+        assert self.in_use >= 0
+
+
+def latency_summary(reqs: Sequence[Request]) -> Dict[str, float]:
+    lat = np.array([r.latency for r in reqs if r.status == "done"])
+    if lat.size == 0:
+        return {"completed": 0}
+    return {"completed": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "max_ms": float(lat.max() * 1e3)}
+
+
+# ---------------------------------------------------------------------------- GPU server
+
+def request_times(torch, spec: RequestSpec, num_times: int, beta: float):
+    """Synthetic sample times of a request, drawn on the device from its seed: a
+    [D][S_pad] buffer (S_pad = S rounded up to 128) of U[0, beta) values."""
+    s_pad = max(128, (spec.num_samples + 127) // 128 * 128)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(int(spec.seed))
+    return torch.rand((num_times, s_pad), generator=gen, device="cuda", dtype=torch.float64) * beta
+
+
+class Server:
+    """See the module docstring.
+
+    graphs:       resident graphs, list of (binding.Graph, eps[K]) -- the pool
+    mode:         evaluation mode of every request
+    budget_bytes: device memory that admitted requests may hold at once
+    max_batch:    requests per launch
+    streams:      launches kept in flight
+    tile_samples: tile of samples per request (bounds each request's workspace)
+    single:       one request per launch through cos_evaluate (the plain path)
+    """
+
+    def __init__(self, graphs, mode: int, budget_bytes: int = 150 << 30, max_batch: int = 64, streams: int = 2,
+                 tile_samples: int = 8192, max_queue: int = 4096, single: bool = False, beta: float = 10.0,
+                 workspace_bytes: int = 1 << 30):
+        import torch
+        from . import binding as cg
+        self.torch = torch
+        self.cg = cg
+        self.graphs = [g for g, _ in graphs]
+        self.eps = [np.ascontiguousarray(e, dtype=np.float64) for _, e in graphs]
+        self.info = [g.info() for g in self.graphs]
+        self.mode = mode
+        self.beta = beta
+        self.single = single
+        self.max_batch = 1 if single else max_batch
+        self.tile = tile_samples
+        self.ws_bytes = workspace_bytes
+        self.ctrl = AdmissionController(budget_bytes, max_queue)
+        self.views: Dict[int, List] = collections.defaultdict(list)
+        self.n_streams = 1 if single else streams
+        self.slots = []
+        for _ in range(self.n_streams):
+            st = torch.cuda.Stream()
+            self.slots.append({"stream": st, "batch": None, "event": None, "reqs": None})
+        self.requests: List[Request] = []
+        self._lock = threading.Lock()
+        self._inbox: Deque[Request] = collections.deque()
+        self._rid = 0
+        self.units_done = 0.0
+
+    # -- memory model: workspace of one tile + the request's times and results
+    def tile_for(self, graph_id: int) -> int:
+        inf = self.info[graph_id]
+        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"] + 24 * inf["K"] * inf["D"]
+        t = max(128, min(self.tile, (self.ws_bytes // psb) // 128 * 128))
+        return int(t)
+
+    def need_bytes(self, graph_id: int, num_samples: int) -> int:
+        """Device memory a request holds while in flight: its handle's workspace (one tile of
+        samples, sized for the double-precision layout), its times [D][S_pad] and its results."""
+        inf = self.info[graph_id]
+        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"] + 24 * inf["K"] * inf["D"]
+        s_pad = (num_samples + 127) // 128 * 128
+        return int(psb * self.tile_for(graph_id) + (8 << 20) + s_pad * inf["D"] * 8 + 16 * num_samples)
+
+    def submit(self, spec: RequestSpec) -> Request:
+        with self._lock:
+            self._rid += 1
+            req = Request(spec, self.need_bytes(spec.graph_id, spec.num_samples), time.perf_counter(), self._rid)
+            self._inbox.append(req)
+            self.requests.append(req)
+        return req
+
+    def _view(self, gid: int):
+        pool = self.views[gid]
+        if pool:
+            return pool.pop()
+        v = self.graphs[gid].share()
+        v.set_tuning(tile_samples=self.tile_for(gid))
+        return v
+
+    def _launch(self, slot, reqs: List[Request]):
+        torch, cg = self.torch, self.cg
+        st = slot["stream"]
+        views, outs = [], []
+        with torch.cuda.stream(st):
+            for r in reqs:
+                g = self.graphs[r.spec.graph_id]
+                D = self.info[r.spec.graph_id]["D"]
+                t = request_times(torch, r.spec, D, self.beta)
+                v = self._view(r.spec.graph_id)
+                v.set_samples(t, self.eps[r.spec.graph_id], self.beta, cg.COS_T_BORROW,
+                              num_samples=r.spec.num_samples, stream=st)
+                dt = torch.int64 if self.mode == cg.COS_MODE_COUNT_I64 else torch.float64
+                out = torch.empty(max(r.spec.num_samples, 1), dtype=dt, device="cuda")
+                r.result = out[:r.spec.num_samples]
+                r._t = t
+                r._view = v
+                views.append(v)
+                outs.append(out)
+                r.t_launch = time.perf_counter()
+                r.status = "running"
+            if self.single:
+                views[0].evaluate(self.mode, out=outs[0], want_mean=False, stream=st)
+            else:
+                if slot["batch"] is None:
+                    slot["batch"] = cg.Batch(views, self.mode, outs)
+                else:
+                    slot["batch"].reset(views, outs)
+                slot["batch"].launch(stream=st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        slot["event"] = ev
+        slot["reqs"] = reqs
+
+    def _finish(self, slot):
+        reqs = slot["reqs"]
+        now = time.perf_counter()
+        try:
+            if self.single:
+                means = [reqs[0]._view.get_result(stream=slot["stream"])]
+            else:
+                means = slot["batch"].results(stream=slot["stream"])
+            for r, m in zip(reqs, means):
+                r.mean = float(m)
+                r.status = "done"
+        except Exception as exc:  # kernel-side error: report on every request of the launch
+            for r in reqs:
+                r.status = "failed"
+                r.error = str(exc)
+        for r in reqs:
+            r.t_done = now
+            self.views[r.spec.graph_id].append(r._view)
+            r._view = None
+            r._t = None
+            self.ctrl.release(r)
+            if r.status == "done":
+                self.units_done += float(self.info[r.spec.graph_id]["E"]) * r.spec.num_samples
+        slot["event"] = None
+        slot["reqs"] = None
+
+    def step(self) -> bool:
+        """One scheduling pass; returns True if anything is queued or in flight."""
+        with self._lock:
+            while self._inbox:
+                self.ctrl.offer(self._inbox.popleft())
+        for slot in self.slots:
+            if slot["event"] is not None and slot["event"].query():
+                self._finish(slot)
+        for slot in self.slots:
+            if slot["event"] is None:
+                reqs = self.ctrl.admit(self.max_batch)
+                if not reqs:
+                    break
+                now = time.perf_counter()
+                for r in reqs:
+                    r.t_admit = now
+                self._launch(slot, reqs)
+        busy = any(s["event"] is not None for s in self.slots)
+        return busy or bool(self.ctrl.queue) or bool(self._inbox)
+
+    def drain(self, timeout_s: float = 600.0):
+        t0 = time.perf_counter()
+        while self.step():
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError("server did not drain")
+            time.sleep(0.0002)
+
+    def close(self):
+        for slot in self.slots:
+            if slot["event"] is not None:
+                slot["event"].synchronize()
+                self._finish(slot)
+            if slot["batch"] is not None:
+                slot["batch"].close()
+        for pool in self.views.values():
+            for v in pool:
+                v.close()
+        self.views.clear()
+
+
+def poisson_run(server: Server, specs: Sequence[RequestSpec], rate_per_s: float, duration_s: float,
+                seed: int = 0) -> Tuple[List[Request], float]:
+    """Submit specs at Poisson arrival times (rate_per_s) for at most duration_s while the
+    scheduling loop runs in this thread; then drain.  Returns (requests, wall seconds)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_per_s, size=len(specs))
+    arrivals = np.cumsum(gaps)
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(specs) and arrivals[k] <= duration_s:
+        now = time.perf_counter() - t0
+        while k < len(specs) and arrivals[k] <= now and arrivals[k] <= duration_s:
+            server.submit(specs[k])
+            k += 1
+        server.step()
+        time.sleep(0.0001)
+    server.drain()
+    return list(server.requests), time.perf_counter() - t0

@@ -1,0 +1,147 @@
+"""Batched uneven launch: many graphs of different size and sample count in one
+persistent, CUDA-graph-captured launch.  Every graph's per-sample results must
+be bitwise identical to evaluating it alone with the same launch shape (the sum
+order at each node and the sample reduction order do not depend on the mix), and
+within the oracle tolerance."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from workloads import batched, complete_layered_graph, tiny  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_00675_gb300 as cg
+    from paper_2501_00675_gb300 import _build
+    _build.build()
+    cg.load_library()
+    return cg
+
+
+def _setup(cg, wls):
+    graphs = []
+    for w in wls:
+        gr = cg.Graph.from_workload_graph(w.graph)
+        gr.set_samples(torch.from_numpy(w.samples.t).cuda(), w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+        graphs.append(gr)
+    return graphs
+
+
+def _outs(wls, mode):
+    dt = torch.int64 if mode == 2 else torch.float64
+    return [torch.full((w.samples.num_samples,), -5, dtype=dt, device="cuda") for w in wls]
+
+
+@pytest.fixture(scope="module")
+def mix():
+    return batched(num_graphs=9, max_nodes=3e4, max_samples=20000, min_samples=700)
+
+
+@pytest.mark.parametrize("mode,tuning", [
+    (1, {}), (0, {}), (2, {}),
+    (1, {"samples_per_lane": 4, "layout": 2, "rows_per_warp": 8}),
+    (0, {"samples_per_lane": 1, "rows_per_warp": 4, "tile_samples": 2048}),
+])
+def test_batch_matches_single_graph_bitwise(cg, mix, mode, tuning):
+    graphs = _setup(cg, mix)
+    outs = _outs(mix, mode)
+    b = cg.Batch(graphs, mode, outs)
+    if tuning:
+        b.set_tuning(**tuning)
+    b.launch()
+    means = b.results()
+    used = b.get_tuning()
+    for w, gr, o, m in zip(mix, graphs, outs, means):
+        single = torch.empty_like(o)
+        gr.set_tuning(samples_per_lane=used["samples_per_lane"], layout=used["layout"],
+                      rows_per_warp=used["rows_per_warp"], tile_samples=tuning.get("tile_samples", 0))
+        ms = gr.evaluate(mode, out=single)
+        np.testing.assert_array_equal(o.cpu().numpy(), single.cpu().numpy())
+        assert m == ms
+    b.close()
+    for gr in graphs:
+        gr.close()
+
+
+def test_batch_against_oracle_and_replay(cg, mix):
+    graphs = _setup(cg, mix)
+    outs = _outs(mix, 1)
+    b = cg.Batch(graphs, 1, outs)
+    b.launch()
+    first = [o.cpu().numpy().copy() for o in outs]
+    m1 = b.results()
+    for o in outs:
+        o.fill_(0)
+    b.launch()                                   # replay of the captured CUDA graph
+    m2 = b.results()
+    np.testing.assert_array_equal(m1, m2)
+    for w, o, f in zip(mix, outs, first):
+        np.testing.assert_array_equal(o.cpu().numpy(), f)
+        idx = np.unique(np.r_[0, w.samples.num_samples - 1, np.random.default_rng(1).integers(0, w.samples.num_samples, 24)])
+        R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[idx])
+        assert np.all(np.abs(f[idx] - R) <= TOL[1] * A)
+    b.close()
+    for gr in graphs:
+        gr.close()
+
+
+def test_batch_autotune_keeps_results(cg, mix):
+    sub = mix[:4]
+    graphs = _setup(cg, sub)
+    outs = _outs(sub, 1)
+    b = cg.Batch(graphs, 1, outs)
+    best = b.autotune()
+    assert best["samples_per_lane"] in (1, 2, 4) and best["layout"] in (1, 2) and 1 <= best["rows_per_warp"] <= 31
+    b.launch()
+    b.results()
+    for w, gr, o in zip(sub, graphs, outs):
+        R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[:64])
+        assert np.all(np.abs(o.cpu().numpy()[:64] - R) <= TOL[1] * A)
+    b.close()
+    for gr in graphs:
+        gr.close()
+
+
+def test_batch_with_empty_sample_set_and_tiny_graphs(cg):
+    wls = [tiny(num_samples=0), tiny(seed=5, num_samples=33), tiny(seed=6, num_samples=1)]
+    graphs = _setup(cg, wls)
+    outs = [None, torch.empty(33, dtype=torch.float64, device="cuda"), torch.empty(1, dtype=torch.float64, device="cuda")]
+    b = cg.Batch(graphs, 0, outs)
+    b.launch()
+    means = b.results()
+    assert means[0] == 0.0
+    for w, o, m in zip(wls[1:], outs[1:], means[1:]):
+        R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+        assert np.all(np.abs(o.cpu().numpy() - R) <= TOL[0] * A)
+        assert abs(m - oracle.neumaier_mean(R)) <= TOL[0] * A.mean()
+    b.close()
+    for gr in graphs:
+        gr.close()
+
+
+def test_batch_rejects_duplicates_and_reports_overflow(cg):
+    w = tiny(num_samples=40)
+    g1 = _setup(cg, [w])[0]
+    with pytest.raises(cg.CosError) as ei:
+        cg.Batch([g1, g1], 0)
+    assert ei.value.code == cg.COS_ERR_INVALID
+    big = cg.Graph.from_workload_graph(complete_layered_graph([1] + [256] * 8 + [1]))
+    big.set_samples(torch.zeros((16, 1), dtype=torch.float64, device="cuda"), np.array([0.0]), 10.0,
+                    cg.COS_T_SAMPLE_MAJOR)
+    b = cg.Batch([g1, big], 2)
+    b.launch()
+    with pytest.raises(cg.CosError) as ei:
+        b.results()
+    assert ei.value.code == cg.COS_ERR_OVERFLOW
+    b.close()
+    g1.close()
+    big.close()

@@ -105,7 +105,8 @@ def test_figure_graph_count(cg):
 def test_medium_multi_tile_ragged_fp64(cg):
     w = medium(num_samples=5000)
     R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
-    for tuning in ({"tile_samples": 1024}, {"tile_samples": 640, "samples_per_lane": 1}):
+    for tuning in ({"tile_samples": 1024}, {"tile_samples": 640, "samples_per_lane": 1},
+                   {"tile_samples": 1024, "layout": 2, "samples_per_lane": 2}):
         Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 0, tuning)
         check_fp(Rg, mg, R, A, 0)
 
@@ -231,7 +232,9 @@ def test_results_independent_of_launch_shape(cg):
     w = medium(num_samples=3000)
     ref = None
     for tuning in ({}, {"samples_per_lane": 1}, {"samples_per_lane": 4, "tile_samples": 512},
-                   {"samples_per_lane": 2, "rows_per_warp": 4, "blocks_per_sm": 1}):
+                   {"samples_per_lane": 2, "rows_per_warp": 4, "blocks_per_sm": 1},
+                   {"samples_per_lane": 4, "layout": 2, "rows_per_warp": 28},
+                   {"samples_per_lane": 2, "layout": 2, "rows_per_warp": 5, "tile_samples": 1000}):
         for mode in (0, 1):
             Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode, tuning)
             if ref is None:
@@ -289,7 +292,7 @@ def test_barrier_timeout_is_reported_and_context_survives(cg, monkeypatch):
     gr.set_tuning(timeout_ms=200)
     t = torch.from_numpy(w.samples.t).cuda()
     gr.set_samples(t, w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
-    monkeypatch.setenv("COS_TEST_SKIP_BARRIER_PHASE", "3")
+    monkeypatch.setenv("COS_TEST_SKIP_BARRIER_PHASE", "4")   # the barrier after level 1
     t0 = time.time()
     with pytest.raises(cg.CosError) as ei:
         gr.evaluate(0)
@@ -300,4 +303,21 @@ def test_barrier_timeout_is_reported_and_context_survives(cg, monkeypatch):
     o = torch.empty(256, dtype=torch.float64, device="cuda")
     m = gr.evaluate(0, out=o)
     check_fp(o.cpu().numpy(), m, R, A, 0)
+    gr.close()
+
+
+def test_table_driven_exponentials_within_two_ulp(cg):
+    # the propagator phase's e^{-x}, e^{+x} (Tang's table-driven method) against libm
+    gr = cg.Graph.from_workload_graph(tiny().graph)
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.uniform(-40, 40, 200000), rng.uniform(-600, 600, 20000),
+                        np.array([0.0, 1e-300, -1e-300, 1e-9, np.log(2) / 128, -np.log(2) / 128, 20.0, -20.0])])
+    xd = torch.from_numpy(x).cuda()
+    em = torch.empty_like(xd)
+    ep = torch.empty_like(xd)
+    assert cg.load_library().cos_selftest_exp(gr.handle, x.size, xd.data_ptr(), em.data_ptr(), ep.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    for got, ref in ((em.cpu().numpy(), np.exp(-x)), (ep.cpu().numpy(), np.exp(x))):
+        rel = np.abs(got - ref) / ref
+        assert rel.max() <= 4.5e-16, rel.max()
     gr.close()
