@@ -55,19 +55,23 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving"], default="medium")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving", "batched"], default="medium")
+    ap.add_argument("--num-graphs", type=int, default=64, help="batched: graphs in the launch")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--pool-size", type=int, default=128, help="serving: resident graphs")
     ap.add_argument("--max-nodes", type=float, default=2e6, help="serving: largest graph")
     ap.add_argument("--max-queue", type=int, default=256, help="serving: bounded wait queue (excess is shed)")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: device memory budget")
+    ap.add_argument("--sweep-rates", type=str, default="", help="serving: extra sustainable rates, e.g. 4,8")
+    ap.add_argument("--sweep-duration", type=float, default=30.0, help="serving: seconds per extra rate")
     ap.add_argument("--mode", choices=sorted(MODES), default=None)
     ap.add_argument("--samples", type=int, default=None, help="samples per GPU (default: the workload's)")
     ap.add_argument("--tuning", type=str, default="", help="JSON dict passed to cos_set_tuning")
     ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -311,6 +315,21 @@ def run_ours(args, rank, world, local):
         e2e = {"value": units / e_total, "unit": "edge·sample updates/s",
                "h2d_bytes_per_step": int(S * D * 8 + K * 8), "d2h_bytes_per_step": int(S * 8)}
 
+    # error of the timed run's results against the FP64 oracle, relative to sum |paths|
+    err = None
+    if rank == 0 and not args.no_oracle_check:
+        import oracle
+        idx = np.unique(np.r_[0, S - 1, np.linspace(0, S - 1, 30).astype(np.int64)])
+        R_or, A_or = oracle.evaluate(g, s.eps, s.beta, s.t[idx])
+        got = out.cpu().numpy()[idx]
+        if mode == 2:
+            cnt, _ = oracle.count_paths(g)
+            err = {"bit_exact": bool(np.all(got == cnt)), "samples_checked": int(idx.size)}
+        else:
+            rel = np.abs(got - R_or) / A_or
+            err = {"max_err_over_abs_path_sum": float(rel.max()), "median_err_over_abs_path_sum": float(np.median(rel)),
+                   "tolerance": 1e-12 if mode == 0 else 1e-5, "samples_checked": int(idx.size)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, n, dt = oracle_rate(g, s, args.cpu_baseline_seconds)
@@ -329,11 +348,94 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed between timed steps (512 MB write); working set larger than L2",
                    "tuning": tuning},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
-        "clocks": clk, "walk_ms_per_launch": statistics.mean(walk_ms), "mean_R": mean,
+        "clocks": clk, "walk_ms_per_launch": statistics.mean(walk_ms), "mean_R": mean, "error_vs_oracle": err,
     }
     if other is not None:
         line["roofline_secondary"] = other
     return line
+
+
+# ------------------------------------------------------------------ batched uneven
+
+def run_batched(args, rank, world, local):
+    """64 graphs of uneven order and sample count in one persistent, CUDA-graph-captured
+    launch (mixed mode), launch shape picked by the autotuner on a capped-sample copy;
+    compared with the same graphs evaluated one after another."""
+    import torch
+    import paper_2501_00675_gb300 as cg
+    from workloads import batched
+
+    torch.cuda.set_device(local)
+    cg.load_library(build_if_missing=True)
+    mode = MODES[args.mode or "mixed"]
+    t0 = time.perf_counter()
+    wls = batched(seed=3 + 1000 * rank, num_graphs=args.num_graphs)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    graphs, outs, probe = [], [], []
+    for w in wls:
+        g = cg.Graph.from_workload_graph(w.graph)
+        inf = g.info()
+        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"]          # workspace bytes per sample of a tile
+        g.set_tuning(tile_samples=int(max(128, min(65536, (2 << 30) // psb // 128 * 128))))   # <= 2 GB per graph
+        g.set_samples(torch.from_numpy(w.samples.t).cuda(), w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+        graphs.append(g)
+        outs.append(torch.empty(w.samples.num_samples, dtype=torch.float64, device="cuda"))
+        cap = min(w.samples.num_samples, 16384)
+        h = g.share()
+        h.set_tuning(tile_samples=min(16384, g.get_tuning(mode)["tile_samples"]))
+        h.set_samples(torch.from_numpy(w.samples.t[:cap].copy()).cuda(), w.samples.eps, w.samples.beta,
+                      cg.COS_T_SAMPLE_MAJOR)
+        probe.append(h)
+    units = float(sum(w.graph.num_edges * w.samples.num_samples for w in wls))
+    tb = cg.Batch(probe, mode)
+    best = tb.autotune()
+    tb.close()
+    for h in probe:
+        h.close()
+    b = cg.Batch(graphs, mode, outs)
+    b.set_tuning(samples_per_lane=best["samples_per_lane"], rows_per_warp=best["rows_per_warp"], layout=best["layout"])
+    for _ in range(max(args.warmup, 2)):           # second launch captures the CUDA graph
+        b.launch(stream)
+    b.results(stream)
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.launch(stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    b.results(stream)
+    # the same graphs one after another through cos_evaluate, same launch shape
+    seq = []
+    for g in graphs:
+        g.set_tuning(samples_per_lane=best["samples_per_lane"], rows_per_warp=best["rows_per_warp"],
+                     layout=best["layout"])
+    for rep in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for g, o in zip(graphs, outs):
+            g.evaluate(mode, out=o, want_mean=False, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        seq.append(e0.elapsed_time(e1))
+    b.close()
+    for g in graphs:
+        g.close()
+    if rank != 0:
+        return None
+    t_b = min(ms) / 1e3
+    return {
+        "metric": "edge·sample updates/s", "value": units / t_b, "unit": "edge·sample updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": min(ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.mode or "mixed"], "data": "synthetic",
+        "config": {"workload": f"batched uneven: {len(wls)} graphs, order n~U{{2..8}}, L=2n+2, N logU[1e3,1e6], "
+                               "fan-in U{1..4}, K=16, D=L, samples logU[4096,2^20], one persistent "
+                               "CUDA-graph-captured launch", "autotuned": best, "generation_s": gen_s,
+                   "edge_samples": units},
+        "sequential_ms": min(seq), "batched_speedup_vs_sequential": min(seq) / min(ms),
+    }
 
 
 # ------------------------------------------------------------------ serving
@@ -358,18 +460,26 @@ def run_serving(args, rank, world, local):
     sizes = np.exp(rng.uniform(np.log(1e3), np.log(1e6), n_spec)).astype(np.int64)
     specs = [RequestSpec(int(g), int(sz), 10_000 + q) for q, (g, sz) in enumerate(zip(gids, sizes))]
     budget = int(args.budget_gb * (1 << 30))
-    out = {}
-    for name, kw in (("batched_mixed", dict(mode=cg.COS_MODE_FP32_MIXED, max_batch=64, streams=2)),
-                     ("plain_fp64", dict(mode=cg.COS_MODE_FP64, single=True))):
-        srv = Server(pool, budget_bytes=budget, max_queue=args.max_queue, **kw)
-        reqs, wall = poisson_run(srv, specs, rate_per_s=args.rate, duration_s=args.duration, seed=rank)
-        summ = latency_summary(reqs)
-        summ.update({"offered": len(reqs), "shed": int(sum(r.status == "shed" for r in reqs)),
-                     "failed": int(sum(r.status == "failed" for r in reqs)), "wall_s": wall,
-                     "edge_sample_updates_per_s": srv.units_done / wall,
-                     "peak_admitted_gb": srv.ctrl.peak / (1 << 30)})
-        out[name] = summ
-        srv.close()
+
+    def one(rate, duration):
+        res = {}
+        for name, kw in (("batched_mixed", dict(mode=cg.COS_MODE_FP32_MIXED, max_batch=64, streams=2)),
+                         ("plain_fp64", dict(mode=cg.COS_MODE_FP64, single=True))):
+            srv = Server(pool, budget_bytes=budget, max_queue=args.max_queue, **kw)
+            reqs, wall = poisson_run(srv, specs, rate_per_s=rate, duration_s=duration, seed=rank)
+            summ = latency_summary(reqs)
+            summ.update({"offered": len(reqs), "shed": int(sum(r.status == "shed" for r in reqs)),
+                         "failed": int(sum(r.status == "failed" for r in reqs)), "wall_s": wall,
+                         "edge_sample_updates_per_s": srv.units_done / wall,
+                         "peak_admitted_gb": srv.ctrl.peak / (1 << 30)})
+            res[name] = summ
+            srv.close()
+        return res
+
+    out = one(args.rate, args.duration)
+    sweep = {}
+    for r in [float(x) for x in args.sweep_rates.split(",") if x.strip()]:
+        sweep[f"{r:g}_req_per_s"] = one(r, args.sweep_duration)
     for g, _ in pool:
         g.close()
     if rank != 0:
@@ -383,7 +493,7 @@ def run_serving(args, rank, world, local):
                                f"{args.pool_size} leveled DAGs, N logU[1e3,{args.max_nodes:g}], geometric fan-in "
                                f"1..6, K=32, D=L; samples per request logU[1e3,1e6]; budget {args.budget_gb:g} GB; "
                                f"queue bound {args.max_queue}", "pool_build_s": build_s},
-        "serving": out,
+        "serving": out, "rate_sweep": sweep,
     }
 
 
@@ -442,12 +552,14 @@ def main(argv=None):
         else:
             dist.init_process_group(backend=backend)
     if args.impl == "reference":
-        if args.workload == "serving":
-            line = {"impl": "reference", "unavailable": "the serving workload has no CPU reference arm"} if rank == 0 else None
+        if args.workload in ("serving", "batched"):
+            line = {"impl": "reference", "unavailable": f"the {args.workload} workload has no CPU reference arm"} if rank == 0 else None
         else:
             line = run_reference(args, rank, world)
     elif args.workload == "serving":
         line = run_serving(args, rank, world, local)
+    elif args.workload == "batched":
+        line = run_batched(args, rank, world, local)
     else:
         line = run_ours(args, rank, world, local)
     if line is not None:

@@ -77,7 +77,7 @@ enum cos_t_flags {
  *   level_width[L]     host, W_l >= 1, W_0 = W_{L-1} = 1, N = sum W_l < 2^31
  *   level_edge_count[L] host, [0] == 0, [l] >= 0, E = sum < 2^31
  *   edges[E][5]        host, int32 rows (src, dst, kind, i, j) as above
- *   num_kinds K >= 1, num_times D >= 1 (kind < K, i, j < D)
+ *   num_kinds K >= 1, 1 <= num_times D <= 192 (kind < K, i, j < D)
  *   out                receives the handle; untouched on error
  * The caller keeps ownership of its arrays; they are not referenced afterwards.
  * Errors: COS_ERR_INVALID (any violation, message names it), COS_ERR_OOM, COS_ERR_CUDA.

@@ -328,7 +328,7 @@ int plan(cos_batch* b) {
     if (!k) return set_error(COS_ERR_INVALID, "no batch kernel for samples_per_lane %d", b->resolved.samples_per_lane);
     int dmax = 1;
     for (const WalkParams& p : b->params) dmax = std::max(dmax, p.D);
-    const int smem = walk_smem_bytes(mode, dmax);
+    const int smem = walk_smem_bytes(mode, b->resolved.samples_per_lane, b->resolved.layout, dmax);
     if (prepare_kernel_attrs(k, smem) != COS_OK) return set_error(COS_ERR_CUDA, "cannot set dynamic shared memory");
     b->smem = smem;
     int per_sm = 0, sms = 0;

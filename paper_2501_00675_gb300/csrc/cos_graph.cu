@@ -177,6 +177,7 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
     if (!level_width || !level_edge_count) return fail(COS_ERR_INVALID, "level arrays are NULL");
     if (num_levels < 2) return fail(COS_ERR_INVALID, "num_levels must be >= 2 (got %d)", num_levels);
     if (num_kinds < 1 || num_times < 1) return fail(COS_ERR_INVALID, "num_kinds and num_times must be >= 1");
+    if (num_times > 192) return fail(COS_ERR_INVALID, "num_times must be <= 192 (got %d)", num_times);
     if ((int64_t)num_kinds * num_times > (1LL << 24)) return fail(COS_ERR_INVALID, "num_kinds * num_times too large");
     const int32_t L = num_levels;
     std::vector<int64_t> off(L + 1, 0);
@@ -440,6 +441,9 @@ static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* til
         const char* env = getenv("COS_TIMEOUT_MS");
         t.timeout_ms = (env && atoi(env) > 0) ? atoi(env) : 10000;
     }
+    // the propagator phase keeps 4 x D x (32 * samples_per_lane) doubles in shared memory
+    while (t.samples_per_lane > 1 && t.layout == 1 && walk_smem_bytes(mode, t.samples_per_lane, t.layout, g->D) > (160 << 10))
+        t.samples_per_lane /= 2;
     int dev_max = max_coresident_blocks(mode, t.samples_per_lane, t.layout, g->D, g->device);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);

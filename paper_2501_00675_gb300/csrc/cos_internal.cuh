@@ -104,7 +104,7 @@ int launch_walk(int mode, int vec, int layout, const WalkParams& p, int grid, cu
 int max_coresident_blocks(int mode, int vec, int layout, int D, int device);
 // Dynamic shared memory of a launch (the propagator phase keeps 32 samples x D times
 // in shared memory), and the once-per-kernel opt-in to sizes above 48 KB.
-int walk_smem_bytes(int mode, int D);
+int walk_smem_bytes(int mode, int vec, int layout, int D);
 int prepare_kernel_attrs(const void* kernel, int smem_bytes);
 // e^{-x} and e^{+x} with the evaluator's table-driven exponentials (self test).
 int launch_exp_pair(const double* x, int64_t n, const double* tab, double* em, double* ep, cudaStream_t stream);

@@ -80,6 +80,33 @@ __device__ __forceinline__ VecT<T, V> load_ca(const T* ptr) {  // L1-cacheable c
     return *reinterpret_cast<const VecT<T, V>*>(ptr);
 }
 
+// Streaming store (evict first): a level's node values are read again only by the
+// next level, after the whole slab has been written, so they should not displace the
+// parent runs and propagator runs that the current level re-reads from L2.
+template <typename T, int V>
+__device__ __forceinline__ void store_cs(T* ptr, const VecT<T, V>& x) {
+    constexpr int bytes = sizeof(T) * V;
+    if constexpr (bytes == 32) {
+        uint4 a, b;
+        memcpy(&a, &x.v[0], 16);
+        memcpy(&b, reinterpret_cast<const char*>(&x.v[0]) + 16, 16);
+        __stcs(reinterpret_cast<uint4*>(ptr), a);
+        __stcs(reinterpret_cast<uint4*>(ptr) + 1, b);
+    } else if constexpr (bytes == 16) {
+        uint4 a;
+        memcpy(&a, &x.v[0], 16);
+        __stcs(reinterpret_cast<uint4*>(ptr), a);
+    } else if constexpr (bytes == 8) {
+        uint2 a;
+        memcpy(&a, &x.v[0], 8);
+        __stcs(reinterpret_cast<uint2*>(ptr), a);
+    } else {
+        unsigned a;
+        memcpy(&a, &x.v[0], 4);
+        __stcs(reinterpret_cast<unsigned*>(ptr), a);
+    }
+}
+
 template <typename T, int V>
 __device__ __forceinline__ void store_cg(T* ptr, const VecT<T, V>& x) {
     constexpr int bytes = sizeof(T) * V;
@@ -196,6 +223,46 @@ __device__ __forceinline__ void exp_pair(double x, const double* __restrict__ ta
     em = __hiloint2double(__double2hiint(vm) - (m << 20), __double2loint(vm));
 }
 
+// ---------------------------------------------------------------- float-float helpers
+
+// Leading 24 significant bits of a double as a float, by truncation with integer
+// operations only (no FP64 conversion); exact for 0 and for |x| in [2^-126, 2^127).
+__device__ __forceinline__ float trunc_to_float(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (e == 0) return 0.0f;
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned mant = (unsigned)(b >> 29) & 0x7fffffu;
+    return __uint_as_float(sign | ((e - 1023u + 127u) << 23) | mant);
+}
+
+// The float value f as a double, exactly, with integer operations only (normal f or 0).
+__device__ __forceinline__ double float_to_double_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// x = hi + lo with hi, lo floats (about 48 significant bits), one DADD.
+__device__ __forceinline__ float2 split_ff(double x) {
+    const float hi = trunc_to_float(x);
+    return make_float2(hi, trunc_to_float(x - float_to_double_exact(hi)));
+}
+
+// Product of two float-float numbers rounded to float: the exact leading product
+// hi*hi plus its rounding error (FMA) plus the cross terms, summed once.
+__device__ __forceinline__ float mul_ff(float2 a, float2 b) {
+    const float x = a.x * b.x;
+    float e = fmaf(a.x, b.x, -x);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    return x + e;
+}
+
 // ---------------------------------------------------------------- phase: propagators
 
 // Item = (chunk, kind k); count mode: item = chunk (root values only).
@@ -205,12 +272,12 @@ __device__ __forceinline__ int prop_items(const WalkParams& p, const TileCtx& tc
     return tc.nch * p.K;
 }
 
-// Shared memory of one propagator item: times and exponentials of 32 samples.
-__host__ __device__ constexpr int prop_smem_bytes(int D) { return 4 * 32 * 8 * D; }
+// Shared memory of one propagator item: times and exponentials of the chunk's samples.
+__host__ __device__ constexpr int prop_smem_bytes(int D, int chv) { return 4 * 8 * D * chv; }
 
-// For each 32-sample run of the chunk: load t_i, form e^{-eps_k t_i} (times the tau >= 0
-// and tau < 0 prefactors) and e^{+eps_k t_i} for every time i in shared memory, then
-// write every propagator slot q = (k, i, j) of this kind:
+// Load the chunk's t_i for every time i, form e^{-eps_k t_i} (times the tau >= 0 and
+// tau < 0 prefactors) and e^{+eps_k t_i} in shared memory, then write every propagator
+// slot q = (k, i, j) of this kind:
 //   G[c][q][s] = (t_i >= t_j ? coef+ : coef-) e^{-eps_k t_i} e^{+eps_k t_j}
 // formed in double, rounded once to the propagator type.  The kind-k slots are the
 // contiguous range [kind_slot[k], kind_slot[k+1]).  The first kind also writes the
@@ -228,17 +295,45 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
             static_cast<typename Tr::Val*>(p.slab[0])[(int64_t)c * CHV + v] = (typename Tr::Val)1;
     if constexpr (!Tr::kCount) {
         const int D = p.D;
-        double* st = sm;              // [D][32] times
-        double* sp = sm + 32 * D;     // [D][32] coef+ e^{-eps t}
-        double* sn = sm + 64 * D;     // [D][32] coef- e^{-eps t}
-        double* se = sm + 96 * D;     // [D][32] e^{+eps t}
         const double eps = p.eps[k], cpos = p.coef[k], cneg = p.coef[p.K + k];
+        const int64_t s0 = tc.base + (int64_t)c * CHV;
         const int q0 = __ldg(p.kind_slot + k), q1 = __ldg(p.kind_slot + k + 1);
         Prop* gt = static_cast<Prop*>(p.gtab) + (int64_t)c * p.P * CHV;
-        for (int sub = 0; sub < CHV / 32; ++sub) {
-            const int64_t s0 = tc.base + (int64_t)c * CHV + sub * 32;
-            for (int x = threadIdx.x; x < 32 * D; x += blockDim.x) {
-                const int i = x >> 5, s = x & 31;
+        // FP32 mode with factors inside float range (|eps| beta <= 60): the products are
+        // formed from float-float halves in FP32 arithmetic, which rounds the (about
+        // 48-bit) product once to float, instead of a double product and a conversion.
+        if (MODE == COS_MODE_FP32_MIXED && fabs(eps) * p.beta <= 60.0) {
+            double* st = sm;                                              // [D][CHV] times
+            float2* fp_ = reinterpret_cast<float2*>(sm + CHV * D);        // [D][CHV] coef+ e^{-eps t}
+            float2* fn_ = fp_ + CHV * D;                                  // [D][CHV] coef- e^{-eps t}
+            float2* fe_ = fn_ + CHV * D;                                  // [D][CHV] e^{+eps t}
+            for (int x = threadIdx.x; x < CHV * D; x += blockDim.x) {
+                const int i = x / CHV, s = x - i * CHV;
+                const double t = p.t[(int64_t)i * p.t_ld + s0 + s];
+                double em, ep;
+                exp_pair(eps * t, p.exp_tab, em, ep);
+                st[x] = t;
+                fp_[x] = split_ff(cpos * em);
+                fn_[x] = split_ff(cneg * em);
+                fe_[x] = split_ff(ep);
+            }
+            __syncthreads();
+            for (int q = q0 + warp; q < q1; q += kWarps) {
+                const int i = __ldg(p.slot_kij + 3 * q + 1), j = __ldg(p.slot_kij + 3 * q + 2);
+#pragma unroll
+                for (int v = 0; v < CHV / 32; ++v) {
+                    const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
+                    const float2 a = (st[xi] >= st[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
+                    __stcg(reinterpret_cast<float*>(gt) + (int64_t)q * CHV + v * 32 + lane, mul_ff(a, fe_[xj]));
+                }
+            }
+        } else {
+            double* st = sm;                  // [D][CHV] times
+            double* sp = sm + CHV * D;        // [D][CHV] coef+ e^{-eps t}
+            double* sn = sm + 2 * CHV * D;    // [D][CHV] coef- e^{-eps t}
+            double* se = sm + 3 * CHV * D;    // [D][CHV] e^{+eps t}
+            for (int x = threadIdx.x; x < CHV * D; x += blockDim.x) {
+                const int i = x / CHV, s = x - i * CHV;
                 const double t = p.t[(int64_t)i * p.t_ld + s0 + s];
                 double em, ep;
                 exp_pair(eps * t, p.exp_tab, em, ep);
@@ -250,11 +345,15 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
             __syncthreads();
             for (int q = q0 + warp; q < q1; q += kWarps) {
                 const int i = __ldg(p.slot_kij + 3 * q + 1), j = __ldg(p.slot_kij + 3 * q + 2);
-                const double a = (st[i * 32 + lane] >= st[j * 32 + lane]) ? sp[i * 32 + lane] : sn[i * 32 + lane];
-                __stcg(gt + (int64_t)q * CHV + sub * 32 + lane, (Prop)(a * se[j * 32 + lane]));
+#pragma unroll
+                for (int v = 0; v < CHV / 32; ++v) {
+                    const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
+                    const double a = (st[xi] >= st[xj]) ? sp[xi] : sn[xi];   // tau = t_i - t_j >= 0 ?
+                    __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)(a * se[xj]));
+                }
             }
-            __syncthreads();
         }
+        __syncthreads();   // the next item reuses the shared memory
     }
 }
 
@@ -285,7 +384,7 @@ __device__ __forceinline__ void store_row(const WalkParams& p, bool sink, typena
         VecT<Val, V> out;
 #pragma unroll
         for (int v = 0; v < V; ++v) out.v[v] = acc[v];
-        store_cg<Val, V>(child + ((int64_t)c * width + r) * CHV + off, out);
+        store_cs<Val, V>(child + ((int64_t)c * width + r) * CHV + off, out);
     }
 }
 

@@ -147,8 +147,8 @@ const void* select_kernel(int mode, int vec, int layout) {
 
 }  // namespace
 
-int walk_smem_bytes(int mode, int D) {
-    return mode == COS_MODE_COUNT_I64 ? 0 : prop_smem_bytes(D);
+int walk_smem_bytes(int mode, int vec, int layout, int D) {
+    return mode == COS_MODE_COUNT_I64 ? 0 : prop_smem_bytes(D, layout == 2 ? 32 : 32 * vec);
 }
 
 // Opt every kernel instance into its dynamic shared-memory size (once per process).
@@ -161,7 +161,7 @@ int prepare_kernel_attrs(const void* k, int smem) {
 int max_coresident_blocks(int mode, int vec, int layout, int D, int device) {
     const void* k = select_kernel(mode, vec, layout);
     if (!k) return 0;
-    const int smem = walk_smem_bytes(mode, D);
+    const int smem = walk_smem_bytes(mode, vec, layout, D);
     if (prepare_kernel_attrs(k, smem) != COS_OK) return 0;
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess) return 0;
@@ -176,7 +176,7 @@ int launch_walk(int mode, int vec, int layout, const WalkParams& p, int grid, cu
         snprintf(msg, msglen, "no kernel for mode %d, vector width %d, layout %d", mode, vec, layout);
         return COS_ERR_INVALID;
     }
-    const int smem = walk_smem_bytes(mode, p.D);
+    const int smem = walk_smem_bytes(mode, vec, layout, p.D);
     if (prepare_kernel_attrs(k, smem) != COS_OK) {
         snprintf(msg, msglen, "cannot set dynamic shared memory %d", smem);
         return COS_ERR_CUDA;
