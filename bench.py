@@ -176,7 +176,8 @@ def profiled_traffic(kernel_tag: str):
     try:
         with open(path) as f:
             d = json.load(f)
-        return d.get(kernel_tag)
+        v = d.get(kernel_tag)
+        return v.get("bytes_per_launch") if isinstance(v, dict) else v
     except (OSError, ValueError):
         return None
 

@@ -117,8 +117,10 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
  * Evaluate the path sum of every attached sample (Fig. 1; Sec. II.C): one
  * persistent cooperative kernel computes, tile of samples by tile, the propagator
  * table, walks the levels in order with a grid-wide barrier between levels,
- * writes the sink value per sample, and finally reduces the samples.  Allocates nothing; may be captured in a CUDA
- * graph when mean_out is NULL.
+ * writes the sink value per sample, and finally reduces the samples.  Allocates
+ * nothing when per_sample_out is given (without it, the first evaluation of a
+ * larger sample set allocates an internal result buffer); may be captured in a
+ * CUDA graph when mean_out is NULL and per_sample_out is given.
  *   mode            cos_mode
  *   per_sample_out  device pointer or NULL: double[S] (FP64, FP32_MIXED) or
  *                   int64[S] (COUNT_I64), index = sample index

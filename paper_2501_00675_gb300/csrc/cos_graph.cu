@@ -324,15 +324,23 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
         for (int64_t q = 0; q < P; ++q) ks[(size_t)slot_kij[3 * q] + 1]++;
         for (int32_t k = 0; k < num_kinds; ++k) ks[(size_t)k + 1] += ks[(size_t)k];
         // 2^{j/64} and 2^{-j/64}, j = 0..63, for the table-driven exponentials
-        std::vector<double> tab(128);
+        // followed by the same values as float-float pairs (hi, lo) for the FP32 path
+        std::vector<double> tab(128 + 128);
+        float* tff = reinterpret_cast<float*>(tab.data() + 128);
         for (int j = 0; j < 64; ++j) {
-            tab[(size_t)j] = (double)std::exp2l((long double)j / 64.0L);
-            tab[(size_t)j + 64] = (double)std::exp2l(-(long double)j / 64.0L);
+            const long double vp = std::exp2l((long double)j / 64.0L), vm = std::exp2l(-(long double)j / 64.0L);
+            tab[(size_t)j] = (double)vp;
+            tab[(size_t)j + 64] = (double)vm;
+            const float hp = (float)vp, hm = (float)vm;
+            tff[2 * j] = hp;
+            tff[2 * j + 1] = (float)(vp - (long double)hp);
+            tff[2 * (64 + j)] = hm;
+            tff[2 * (64 + j) + 1] = (float)(vm - (long double)hm);
         }
         if ((e = cudaMalloc(&g->d_kind_slot, sizeof(int32_t) * (num_kinds + 1))) != cudaSuccess) return cleanup_fail(e, "cudaMalloc kind slots");
-        if ((e = cudaMalloc(&g->d_exp_tab, sizeof(double) * 128)) != cudaSuccess) return cleanup_fail(e, "cudaMalloc exp table");
+        if ((e = cudaMalloc(&g->d_exp_tab, sizeof(double) * tab.size())) != cudaSuccess) return cleanup_fail(e, "cudaMalloc exp table");
         if ((e = cudaMemcpy(g->d_kind_slot, ks.data(), sizeof(int32_t) * (num_kinds + 1), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy kind slots");
-        if ((e = cudaMemcpy(g->d_exp_tab, tab.data(), sizeof(double) * 128, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy exp table");
+        if ((e = cudaMemcpy(g->d_exp_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy exp table");
     }
     if ((e = cudaMemcpy(g->d_levels, lv.data(), sizeof(LevelDesc) * L, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy levels");
     if ((e = cudaMemcpy(g->d_row_ptr, row_ptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e, "copy row_ptr");
@@ -505,14 +513,9 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
     const int64_t nblk = std::max<int64_t>((S + kReduceBlock - 1) / kReduceBlock, 1);
     if (nblk > g->partial_cap) {
         dfree(g->d_partials);
-        COS_CUDA(cudaMalloc(&g->d_partials, sizeof(double) * nblk), "cudaMalloc partials");
-        g->partial_cap = nblk;
-    }
-    if (std::max<int64_t>(S, 1) > g->R_cap) {
-        if (g->d_R) cudaFree(g->d_R);
-        g->d_R = nullptr;
-        COS_CUDA(cudaMalloc(&g->d_R, sizeof(double) * std::max<int64_t>(S, 1)), "cudaMalloc R");
-        g->R_cap = std::max<int64_t>(S, 1);
+        const int64_t cap = std::max<int64_t>(nblk, 1024);   // room for 4M samples without regrowth
+        COS_CUDA(cudaMalloc(&g->d_partials, sizeof(double) * cap), "cudaMalloc partials");
+        g->partial_cap = cap;
     }
     // Workspace arena: enough for the FP64 mode over all samples, up to the budget.
     {
@@ -711,6 +714,14 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
     p.beta = g->beta;
     p.S = g->S;
     p.t_ld = g->t_ld;
+    if (!per_sample_out && std::max<int64_t>(g->S, 1) > g->R_cap) {
+        // no caller buffer: the per-sample values go to an internal buffer (allocated on first need)
+        if (g->d_R) cudaFree(g->d_R);
+        g->d_R = nullptr;
+        g->R_cap = 0;
+        COS_CUDA(cudaMalloc(&g->d_R, sizeof(double) * std::max<int64_t>(g->S, 1)), "cudaMalloc R");
+        g->R_cap = std::max<int64_t>(g->S, 1);
+    }
     p.R = per_sample_out ? per_sample_out : g->d_R;
     p.partials = g->d_partials;
     p.ctrl = g->d_ctrl;

@@ -53,7 +53,8 @@ struct WalkParams {
     void* gtab;                // [nchunk][P][CH] propagator table of the tile
     double* coef;              // [2K]: -1/(1+e^{-beta eps_k}) (tau >= 0), 1/(1+e^{beta eps_k}) (tau < 0)
     const int32_t* kind_slot;  // [K+1]: slots of kind k are [kind_slot[k], kind_slot[k+1])
-    const double* exp_tab;     // [128]: 2^{j/64}, then 2^{-j/64}, j = 0..63
+    const double* exp_tab;     // [128]: 2^{j/64}, then 2^{-j/64}, j = 0..63; followed by the same
+                               // 128 values as float-float (hi, lo) pairs (256 floats)
     void* R;                   // [S] sink value per sample (double, or int64 in count mode)
     double* partials;          // [ceil(S/4096)] compensated partial sums
     Ctrl* ctrl;

@@ -226,11 +226,12 @@ __device__ __forceinline__ void exp_pair(double x, const double* __restrict__ ta
 // ---------------------------------------------------------------- float-float helpers
 
 // Leading 24 significant bits of a double as a float, by truncation with integer
-// operations only (no FP64 conversion); exact for 0 and for |x| in [2^-126, 2^127).
+// operations only (no FP64 conversion); |x| below 2^-126 gives a signed zero.  The
+// callers keep |x| below 2^127.
 __device__ __forceinline__ float trunc_to_float(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-    if (e == 0) return 0.0f;
+    if (e < 1023u - 126u) return __uint_as_float((unsigned)(b >> 32) & 0x80000000u);
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
     const unsigned mant = (unsigned)(b >> 29) & 0x7fffffu;
     return __uint_as_float(sign | ((e - 1023u + 127u) << 23) | mant);
@@ -261,6 +262,52 @@ __device__ __forceinline__ float mul_ff(float2 a, float2 b) {
     e = fmaf(a.x, b.y, e);
     e = fmaf(a.y, b.x, e);
     return x + e;
+}
+
+// Float-float product of two float-float numbers (about 46 significant bits).
+__device__ __forceinline__ float2 mul_ff2(float2 a, float2 b) {
+    const float x = a.x * b.x;
+    float e = fmaf(a.x, b.x, -x);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float hi = x + e;
+    return make_float2(hi, e - (hi - x));
+}
+
+// 2^m * (hi, lo) by exponent arithmetic; hi must stay normal (the callers keep it
+// within 2^{+-100}); a lo that would leave the normal range becomes zero.
+__device__ __forceinline__ float2 ldexp_ff(float2 v, int m) {
+    const unsigned sh = (unsigned)m << 23;
+    const float hi = __uint_as_float(__float_as_uint(v.x) + sh);
+    const int elo = (int)((__float_as_uint(v.y) >> 23) & 0xffu) + m;
+    const float lo = (elo <= 0 || elo >= 255) ? 0.0f : __uint_as_float(__float_as_uint(v.y) + sh);
+    return make_float2(hi, lo);
+}
+
+// e^{-x} and e^{+x} as float-float values accurate to about 1e-10 relative, for
+// |x| <= 30: the reduction x = (64 m + j) ln2/64 + r is done in double (one rounding
+// of n, two FMAs), everything after it in FP32 -- r is below 0.0055, so its float
+// rounding and the float polynomial (even and odd parts through r^4 and r^3) change
+// e^{+-r} by less than 1e-9 relative; 2^{+-j/64} comes from a float-float table
+// `tff` ([0..63] = 2^{j/64}, [64..127] = 2^{-j/64}, each as (hi, lo)).
+__device__ __forceinline__ void exp_pair_ff(double x, const float2* __restrict__ tff, float2& em, float2& ep) {
+    const float nf = rintf(trunc_to_float(x) * 92.33248261689366f);
+    const double nd = (double)(int)nf;
+    double r = fma(-nd, 0.01083042469326756, x);
+    r = fma(-nd, 2.9815858269852933e-12, r);
+    const int n = (int)nf;
+    const float rf = trunc_to_float(r);
+    const float r2 = rf * rf;
+    const float even = r2 * fmaf(r2, 1.0f / 24.0f, 0.5f);
+    const float odd = rf * fmaf(r2, 1.0f / 6.0f, 1.0f);
+    const int j = n & 63, m = n >> 6;
+    const float2 tp = tff[j], tm = tff[64 + j];
+    // T (1 + p) = T_hi + (T_lo + T_hi p), renormalised
+    const float pp = even + odd, pm = even - odd;
+    const float wp = fmaf(tp.x, pp, tp.y), wm = fmaf(tm.x, pm, tm.y);
+    const float hp = tp.x + wp, hm = tm.x + wm;
+    ep = ldexp_ff(make_float2(hp, wp - (hp - tp.x)), m);
+    em = ldexp_ff(make_float2(hm, wm - (hm - tm.x)), -m);
 }
 
 // ---------------------------------------------------------------- phase: propagators
@@ -299,35 +346,49 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
         const int64_t s0 = tc.base + (int64_t)c * CHV;
         const int q0 = __ldg(p.kind_slot + k), q1 = __ldg(p.kind_slot + k + 1);
         Prop* gt = static_cast<Prop*>(p.gtab) + (int64_t)c * p.P * CHV;
-        // FP32 mode with factors inside float range (|eps| beta <= 60): the products are
-        // formed from float-float halves in FP32 arithmetic, which rounds the (about
-        // 48-bit) product once to float, instead of a double product and a conversion.
-        if (MODE == COS_MODE_FP32_MIXED && fabs(eps) * p.beta <= 60.0) {
+        // FP32 mode with every factor and its low half inside the normal float range
+        // (|eps| beta <= 30, so factors lie within e^{+-60}): exponentials,
+        // prefactors and products in float-float FP32 arithmetic (about 1e-10 relative
+        // before the single rounding of G to float), instead of double operations on
+        // GB300's slow FP64 pipe.
+        bool use_ff = (MODE == COS_MODE_FP32_MIXED && fabs(eps) * p.beta <= 30.0);
+        if (use_ff) {
             double* st = sm;                                              // [D][CHV] times
             float2* fp_ = reinterpret_cast<float2*>(sm + CHV * D);        // [D][CHV] coef+ e^{-eps t}
             float2* fn_ = fp_ + CHV * D;                                  // [D][CHV] coef- e^{-eps t}
             float2* fe_ = fn_ + CHV * D;                                  // [D][CHV] e^{+eps t}
+            const float2 cp2 = split_ff(cpos), cn2 = split_ff(cneg);
+            const float2* tff = reinterpret_cast<const float2*>(p.exp_tab + 128);
+            bool out_of_range = false;   // times outside [-beta, beta]: take the double path
             for (int x = threadIdx.x; x < CHV * D; x += blockDim.x) {
                 const int i = x / CHV, s = x - i * CHV;
                 const double t = p.t[(int64_t)i * p.t_ld + s0 + s];
-                double em, ep;
-                exp_pair(eps * t, p.exp_tab, em, ep);
+                const double arg = eps * t;
+                if (!(fabs(arg) <= 30.0)) {
+                    out_of_range = true;
+                    continue;
+                }
+                float2 em, ep;
+                exp_pair_ff(arg, tff, em, ep);
                 st[x] = t;
-                fp_[x] = split_ff(cpos * em);
-                fn_[x] = split_ff(cneg * em);
-                fe_[x] = split_ff(ep);
+                fp_[x] = mul_ff2(cp2, em);
+                fn_[x] = mul_ff2(cn2, em);
+                fe_[x] = ep;
             }
-            __syncthreads();
-            for (int q = q0 + warp; q < q1; q += kWarps) {
-                const int i = __ldg(p.slot_kij + 3 * q + 1), j = __ldg(p.slot_kij + 3 * q + 2);
+            use_ff = !__syncthreads_or(out_of_range);
+            if (use_ff) {
+                for (int q = q0 + warp; q < q1; q += kWarps) {
+                    const int i = __ldg(p.slot_kij + 3 * q + 1), j = __ldg(p.slot_kij + 3 * q + 2);
 #pragma unroll
-                for (int v = 0; v < CHV / 32; ++v) {
-                    const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
-                    const float2 a = (st[xi] >= st[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
-                    __stcg(reinterpret_cast<float*>(gt) + (int64_t)q * CHV + v * 32 + lane, mul_ff(a, fe_[xj]));
+                    for (int v = 0; v < CHV / 32; ++v) {
+                        const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
+                        const float2 a = (st[xi] >= st[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
+                        __stcg(reinterpret_cast<float*>(gt) + (int64_t)q * CHV + v * 32 + lane, mul_ff(a, fe_[xj]));
+                    }
                 }
             }
-        } else {
+        }
+        if (!use_ff) {
             double* st = sm;                  // [D][CHV] times
             double* sp = sm + CHV * D;        // [D][CHV] coef+ e^{-eps t}
             double* sn = sm + 2 * CHV * D;    // [D][CHV] coef- e^{-eps t}

@@ -43,6 +43,7 @@ class Request:
     t_launch: float = 0.0
     t_done: float = 0.0
     status: str = "queued"        # queued | admitted | running | done | shed | failed
+    charged: int = 0
     mean: float = float("nan")
     result = None                 # device tensor of per-sample values
     error: Optional[str] = None
@@ -55,12 +56,18 @@ class Request:
 class AdmissionController:
     """FIFO admission under a device-memory budget with a bounded wait queue.
 
-    offer():  enqueue, or shed at once when the queue is full or the request can
-              never fit the budget.
-    admit():  pop queued requests in arrival order while their memory fits what is
-              left of the budget (head-of-line: a request that does not fit yet
-              blocks the ones behind it, so large requests are not starved).
-    release(): return a finished request's memory.
+    offer():   enqueue, or shed at once when the queue is full or the request can
+               never fit the budget.
+    admit():   pop queued requests in arrival order while their memory fits what is
+               left of the budget (head-of-line: a request that does not fit yet
+               blocks the ones behind it, so large requests are not starved).
+               `cost(r)` gives the bytes admitting r charges now (default
+               r.need_bytes), `can_run(r)` vetoes a request that lacks another
+               resource, and `reclaim(n)` may free up to n bytes of idle memory
+               (returns what it freed) before the head is refused; `on_admit(r)`
+               runs right after r is admitted (e.g. to take the resources that
+               `cost` and `can_run` looked at).
+    release(): return bytes (default: the request's own charge).
     """
 
     def __init__(self, budget_bytes: int, max_queue: int = 1024):
@@ -80,19 +87,30 @@ class AdmissionController:
         self.queue.append(req)
         return True
 
-    def admit(self, max_n: int) -> List[Request]:
+    def admit(self, max_n: int, cost=None, can_run=None, reclaim=None, on_admit=None) -> List[Request]:
         out = []
-        while self.queue and len(out) < max_n and self.in_use + self.queue[0].need_bytes <= self.budget:
-            r = self.queue.popleft()
-            self.in_use += r.need_bytes
+        while self.queue and len(out) < max_n:
+            r = self.queue[0]
+            if can_run is not None and not can_run(r):
+                break
+            need = r.need_bytes if cost is None else cost(r)
+            if self.in_use + need > self.budget and reclaim is not None:
+                self.in_use -= reclaim(self.in_use + need - self.budget)
+            if self.in_use + need > self.budget:
+                break
+            self.queue.popleft()
+            self.in_use += need
             self.peak = max(self.peak, self.in_use)
+            r.charged = need
             r.status = "admitted"
+            if on_admit is not None:
+                on_admit(r)
             out.append(r)
         self.admitted += len(out)
         return out
 
-    def release(self, req: Request):
-        self.in_use -= req.need_bytes
+    def release(self, req: Optional[Request] = None, nbytes: Optional[int] = None):
+        self.in_use -= int(nbytes if nbytes is not None else req.need_bytes)
         assert self.in_use >= 0
 
 
@@ -130,7 +148,7 @@ class Server:
 
     def __init__(self, graphs, mode: int, budget_bytes: int = 150 << 30, max_batch: int = 64, streams: int = 2,
                  tile_samples: int = 8192, max_queue: int = 4096, single: bool = False, beta: float = 10.0,
-                 workspace_bytes: int = 1 << 30):
+                 workspace_bytes: int = 512 << 20, handles_per_graph: int = 2):
         import torch
         from . import binding as cg
         self.torch = torch
@@ -144,8 +162,14 @@ class Server:
         self.max_batch = 1 if single else max_batch
         self.tile = tile_samples
         self.ws_bytes = workspace_bytes
+        self.handles_per_graph = handles_per_graph
         self.ctrl = AdmissionController(budget_bytes, max_queue)
+        # per graph: idle handles (cos_graph_share), and how many are in use; idle handles
+        # keep their workspace charged to the budget until they are evicted (LRU)
         self.views: Dict[int, List] = collections.defaultdict(list)
+        self.busy: Dict[int, int] = collections.defaultdict(int)
+        self.idle_lru: "collections.OrderedDict" = collections.OrderedDict()
+        self.evicted = 0
         self.n_streams = 1 if single else streams
         self.slots = []
         for _ in range(self.n_streams):
@@ -160,17 +184,45 @@ class Server:
     # -- memory model: workspace of one tile + the request's times and results
     def tile_for(self, graph_id: int) -> int:
         inf = self.info[graph_id]
-        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"] + 24 * inf["K"] * inf["D"]
+        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"]
         t = max(128, min(self.tile, (self.ws_bytes // psb) // 128 * 128))
         return int(t)
 
-    def need_bytes(self, graph_id: int, num_samples: int) -> int:
-        """Device memory a request holds while in flight: its handle's workspace (one tile of
-        samples, sized for the double-precision layout), its times [D][S_pad] and its results."""
+    def handle_bytes(self, graph_id: int) -> int:
+        """Device memory of one evaluation handle of a graph: workspace of one tile of samples
+        (sized for the double-precision layout) and small buffers."""
         inf = self.info[graph_id]
-        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"] + 24 * inf["K"] * inf["D"]
-        s_pad = (num_samples + 127) // 128 * 128
-        return int(psb * self.tile_for(graph_id) + (8 << 20) + s_pad * inf["D"] * 8 + 16 * num_samples)
+        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"]
+        return int(psb * ((self.tile_for(graph_id) + 127) // 128 * 128) + (8 << 20) + (1 << 20))
+
+    def io_bytes(self, graph_id: int, num_samples: int) -> int:
+        """Device memory of a request's own times [D][S_pad] and results [S]."""
+        s_pad = max(128, (num_samples + 127) // 128 * 128)
+        return int(s_pad * self.info[graph_id]["D"] * 8 + 8 * max(num_samples, 1))
+
+    def need_bytes(self, graph_id: int, num_samples: int) -> int:
+        """Upper bound of what admitting a request can charge (a new handle + its buffers)."""
+        return self.handle_bytes(graph_id) + self.io_bytes(graph_id, num_samples)
+
+    # -- admission callbacks
+    def _cost(self, r: Request) -> int:
+        g = r.spec.graph_id
+        return self.io_bytes(g, r.spec.num_samples) + (0 if self.views[g] else self.handle_bytes(g))
+
+    def _can_run(self, r: Request) -> bool:
+        g = r.spec.graph_id
+        return bool(self.views[g]) or self.busy[g] < self.handles_per_graph
+
+    def _reclaim(self, nbytes: int) -> int:
+        """Destroy least recently used idle handles until nbytes are freed."""
+        freed = 0
+        while freed < nbytes and self.idle_lru:
+            (g, vid), v = self.idle_lru.popitem(last=False)
+            self.views[g].remove(v)
+            v.close()
+            freed += self.handle_bytes(g)
+            self.evicted += 1
+        return freed
 
     def submit(self, spec: RequestSpec) -> Request:
         with self._lock:
@@ -180,13 +232,24 @@ class Server:
             self.requests.append(req)
         return req
 
+    def _take_view(self, r: Request):
+        r._view = self._view(r.spec.graph_id)
+
     def _view(self, gid: int):
+        self.busy[gid] += 1
         pool = self.views[gid]
         if pool:
-            return pool.pop()
+            v = pool.pop()
+            self.idle_lru.pop((gid, id(v)), None)
+            return v
         v = self.graphs[gid].share()
         v.set_tuning(tile_samples=self.tile_for(gid))
         return v
+
+    def _return_view(self, gid: int, v):
+        self.busy[gid] -= 1
+        self.views[gid].append(v)
+        self.idle_lru[(gid, id(v))] = v
 
     def _launch(self, slot, reqs: List[Request]):
         torch, cg = self.torch, self.cg
@@ -197,7 +260,7 @@ class Server:
                 g = self.graphs[r.spec.graph_id]
                 D = self.info[r.spec.graph_id]["D"]
                 t = request_times(torch, r.spec, D, self.beta)
-                v = self._view(r.spec.graph_id)
+                v = r._view
                 v.set_samples(t, self.eps[r.spec.graph_id], self.beta, cg.COS_T_BORROW,
                               num_samples=r.spec.num_samples, stream=st)
                 dt = torch.int64 if self.mode == cg.COS_MODE_COUNT_I64 else torch.float64
@@ -239,10 +302,10 @@ class Server:
                 r.error = str(exc)
         for r in reqs:
             r.t_done = now
-            self.views[r.spec.graph_id].append(r._view)
+            self._return_view(r.spec.graph_id, r._view)   # its workspace stays charged while idle
             r._view = None
             r._t = None
-            self.ctrl.release(r)
+            self.ctrl.release(nbytes=self.io_bytes(r.spec.graph_id, r.spec.num_samples))
             if r.status == "done":
                 self.units_done += float(self.info[r.spec.graph_id]["E"]) * r.spec.num_samples
         slot["event"] = None
@@ -258,7 +321,8 @@ class Server:
                 self._finish(slot)
         for slot in self.slots:
             if slot["event"] is None:
-                reqs = self.ctrl.admit(self.max_batch)
+                reqs = self.ctrl.admit(self.max_batch, cost=self._cost, can_run=self._can_run,
+                                       reclaim=self._reclaim, on_admit=self._take_view)
                 if not reqs:
                     break
                 now = time.perf_counter()
@@ -286,6 +350,7 @@ class Server:
             for v in pool:
                 v.close()
         self.views.clear()
+        self.idle_lru.clear()
 
 
 def poisson_run(server: Server, specs: Sequence[RequestSpec], rate_per_s: float, duration_s: float,

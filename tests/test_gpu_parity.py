@@ -321,3 +321,18 @@ def test_table_driven_exponentials_within_two_ulp(cg):
         rel = np.abs(got - ref) / ref
         assert rel.max() <= 4.5e-16, rel.max()
     gr.close()
+
+
+def test_mixed_mode_wide_energy_range_and_time_fallback(cg):
+    # |eps| beta > 30 takes the double propagator path, |eps| beta <= 30 the float-float
+    # path; times slightly beyond beta push a float-float item onto the double path.
+    rng = np.random.default_rng(17)
+    g = make_graph([1, 5, 9, 9, 6, 1], FaninSpec("uniform", 3), 6, 5, rng)
+    eps = np.array([-7.5, -2.9, -0.3, 0.8, 2.95, 6.0])
+    for hi in (10.0, 11.0):
+        t = rng.uniform(0.0, hi, size=(700, 5))
+        R, A = oracle.evaluate(g, eps, 10.0, t)
+        Rg, mg = run_gpu(cg, g, eps, 10.0, t, 1)
+        check_fp(Rg, mg, R, A, 1)
+        Rg, mg = run_gpu(cg, g, eps, 10.0, t, 0)
+        check_fp(Rg, mg, R, A, 0)

@@ -62,3 +62,27 @@ def test_latency_summary():
     s = latency_summary(rs)
     assert s["completed"] == 100
     assert abs(s["p50_ms"] - 50.5) < 1e-6 and 99 < s["p99_ms"] <= 100
+
+
+def test_reclaim_and_resource_veto():
+    ac = AdmissionController(budget_bytes=100, max_queue=10)
+    for i in range(3):
+        ac.offer(_req(i, 50))
+    idle = [30, 30]                                   # memory held by idle handles, reclaimable
+
+    def reclaim(n):
+        freed = 0
+        while freed < n and idle:
+            freed += idle.pop()
+        return freed
+
+    ac.in_use = 60                                    # two idle handles charged
+    got = ac.admit(10, cost=lambda r: 40, reclaim=reclaim)
+    assert [r.rid for r in got] == [0, 1] and ac.in_use == 80 and idle == []
+    assert ac.admit(10, cost=lambda r: 40, reclaim=reclaim) == []     # nothing left to reclaim
+    ac.release(nbytes=40)
+    blocked = ac.admit(10, cost=lambda r: 10, can_run=lambda r: False)
+    assert blocked == [] and len(ac.queue) == 1       # vetoed head stays queued
+    seen = []
+    assert [r.rid for r in ac.admit(10, cost=lambda r: 10, on_admit=seen.append)] == [2]
+    assert [r.rid for r in seen] == [2] and ac.peak <= 100
