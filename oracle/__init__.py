@@ -93,14 +93,21 @@ def propagator(eps: float, beta: float, tau) -> np.ndarray:
     return out
 
 
+SIGN_BIT = 1 << 30          # kind bit 30: the edge closes a fermion loop (factor times -1)
+KIND_MASK = SIGN_BIT - 1
+
+
 def edge_weights(graph, eps: np.ndarray, beta: float, t_sample: np.ndarray) -> np.ndarray:
-    """Per-edge factors w_e = G_{k_e}(t_{i_e} - t_{j_e}) for one sample (t_sample[D])."""
+    """Per-edge factors w_e = +-G_{k_e}(t_{i_e} - t_{j_e}) for one sample (t_sample[D]);
+    the sign is - for edges whose kind has bit 30 set (Sec. II.C, fermion loops)."""
     e = graph.edges
     tau = t_sample[e[:, 3]] - t_sample[e[:, 4]]
+    kind = e[:, 2] & KIND_MASK
     out = np.empty(e.shape[0])
-    for k in np.unique(e[:, 2]):
-        m = e[:, 2] == k
+    for k in np.unique(kind):
+        m = kind == k
         out[m] = propagator(eps[k], beta, tau[m])
+    out[(e[:, 2] & SIGN_BIT) != 0] *= -1.0
     return out
 
 

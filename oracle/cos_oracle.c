@@ -23,6 +23,11 @@
  * branch.  The paper writes no formula for G (Fig. 1 caption only names the
  * Green's function G_ab), so this definition is the workload's.
  *
+ * An edge whose kind field has bit 30 set closes a fermion loop: its factor is
+ * additionally multiplied by -1 (Sec. II.C, "Numerical stability": the edge
+ * operation checks whether the result must be multiplied by -1).  Bits 0..29 hold
+ * the kind.
+ *
  * Arithmetic is IEEE double with no contraction (build with -ffp-contract=off)
  * so results are the same on every host.  Path counts use 128-bit integers and
  * report overflow past 2^63-1; the int64 result wraps modulo 2^64.
@@ -49,6 +54,9 @@ void cos_oracle_propagator_array(double eps, double beta, const double* tau, dou
     for (int64_t q = 0; q < n; ++q) out[q] = cos_oracle_propagator(eps, beta, tau[q]);
 }
 
+#define COS_ORACLE_SIGN_BIT 0x40000000
+#define COS_ORACLE_KIND_MASK 0x3fffffff
+
 static int check_graph(int32_t L, const int64_t* widths, const int64_t* counts, const int32_t* edges,
                        int32_t K, int32_t D, int64_t* N_out, int64_t* E_out) {
     if (L < 2) return -1;
@@ -58,7 +66,7 @@ static int check_graph(int32_t L, const int64_t* widths, const int64_t* counts, 
     for (int64_t e = 0; e < E; ++e) {
         const int32_t* r = edges + 5 * e;
         if (r[0] < 0 || r[0] >= N || r[1] < 0 || r[1] >= N) return -1;
-        if (K > 0 && (r[2] < 0 || r[2] >= K)) return -1;
+        if (r[2] < 0 || (K > 0 && (r[2] & COS_ORACLE_KIND_MASK) >= K)) return -1;
         if (D > 0 && (r[3] < 0 || r[3] >= D || r[4] < 0 || r[4] >= D)) return -1;
     }
     *N_out = N; *E_out = E;
@@ -111,7 +119,8 @@ int cos_oracle_eval(int32_t L, const int64_t* widths, const int64_t* counts, con
                 for (int64_t e = 0; e < E; ++e) {
                     const int32_t* r = edges + 5 * e;
                     double tau = ts[r[3]] - ts[r[4]];
-                    double w = cos_oracle_propagator(eps[r[2]], beta, tau);
+                    double w = cos_oracle_propagator(eps[r[2] & COS_ORACLE_KIND_MASK], beta, tau);
+                    if (r[2] & COS_ORACLE_SIGN_BIT) w = -w;   /* closes a fermion loop */
                     v[r[1]] += v[r[0]] * w;
                     if (a) a[r[1]] += a[r[0]] * fabs(w);
                 }

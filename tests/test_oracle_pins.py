@@ -231,3 +231,44 @@ def test_neumaier_sum_matches_exact_sum():
     for x in cases:
         assert oracle.neumaier_sum(x) == math.fsum(x)
     assert oracle.neumaier_mean(np.array([])) == 0.0
+
+
+# ---------------------------------------------------------------- fermion-loop sign (kind bit 30)
+
+def _with_signs(g, mask):
+    from workloads import Graph
+    e = g.edges.copy()
+    e[mask, 2] |= oracle.SIGN_BIT
+    return Graph(g.widths, g.edge_counts, e, g.num_kinds, g.num_times)
+
+
+def test_sign_flag_on_one_level_negates_every_path():
+    # every root-to-sink path crosses each level exactly once, so flagging all edges
+    # into one level multiplies every path, hence R, by -1 (A is unchanged)
+    g, eps, t = _random_graph(31, [1, 4, 7, 7, 3, 1], fmax=3)
+    R, A = oracle.evaluate(g, eps, 10.0, t)
+    lvl = np.repeat(np.arange(g.num_levels), g.edge_counts)
+    Rs, As = oracle.evaluate(_with_signs(g, lvl == 3), eps, 10.0, t)
+    np.testing.assert_array_equal(Rs, -R)
+    np.testing.assert_array_equal(As, A)
+    # two flagged levels cancel
+    R2, _ = oracle.evaluate(_with_signs(g, (lvl == 2) | (lvl == 4)), eps, 10.0, t)
+    np.testing.assert_array_equal(R2, R)
+
+
+def test_sign_flags_against_brute_force_and_chain():
+    g, eps, t = _random_graph(32, [1, 3, 6, 6, 2, 1], fmax=3)
+    mask = np.random.default_rng(2).random(g.num_edges) < 0.4
+    gs = _with_signs(g, mask)
+    R, _ = oracle.evaluate(gs, eps, 10.0, t)
+    paths = oracle.brute_force_paths(gs)
+    for s in range(t.shape[0]):
+        w = oracle.edge_weights(gs, eps, 10.0, t[s])
+        r, a = oracle.brute_force_sum(paths, w)
+        assert abs(R[s] - r) <= 1e-14 * a
+    # chain with closed-form factors: one flagged edge flips the sign of the product
+    c = chain_graph([0, 0, 0], [0, 1, 0], [1, 0, 0], 1, 2)
+    tt = np.array([[1.5, 0.5]])
+    R0, _ = oracle.evaluate(c, np.array([math.log(2.0)]), 2.0, tt)
+    R1, _ = oracle.evaluate(_with_signs(c, np.array([False, True, False])), np.array([math.log(2.0)]), 2.0, tt)
+    assert R0[0] == pytest.approx((-0.4) * 0.4 * (-0.8), rel=1e-14) and R1[0] == -R0[0]
