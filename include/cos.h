@@ -14,9 +14,11 @@
  *     node N-1 the sink (N = sum of W_l).
  *   - Edges are the flattened per-level lists of Fig. 3: int32 rows
  *     (src, dst, kind, i, j), level-major (level_edge_count[l] rows for level l,
- *     in increasing l).  Every edge into level l has src in level l-1 and dst in
+ *     in increasing l).  Bit 30 of `kind` marks an edge that closes a fermion
+ *     loop: its factor is multiplied by -1 (Sec. II.C, "Numerical stability");
+ *     bits 0..29 hold the kind.  Every edge into level l has src in level l-1 and dst in
  *     level l.  Duplicate (src, dst) pairs are separate edges.
- *   - Edge factor for sample s: G_kind(t_{s,i} - t_{s,j}) with the free-fermion
+ *   - Edge factor for sample s: +-G_kind(t_{s,i} - t_{s,j}) with the free-fermion
  *     propagator G_k(tau) = -exp(-eps_k tau)/(1+exp(-beta eps_k)) for tau >= 0
  *     and G_k(tau) = -G_k(tau+beta) for tau < 0 (tau = 0 takes the first branch;
  *     the comparison is made on the double-precision times).
@@ -112,6 +114,27 @@ int cos_graph_share(cos_graph_t src, cos_graph_t* out);
  */
 int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t t_flags,
                     const double* eps, double beta, void* stream);
+
+/*
+ * Attach S Monte Carlo samples drawn on the device (the integration over vertex
+ * times by stochastic sampling, Sec. II.B; device-side sampling, Sec. IV): for
+ * sample n = first_sample + s and time i, t[s][i] = beta * u with u in [0, 1) taken
+ * from a counter-based generator -- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw,
+ * SC'11) with counter (n mod 2^32, n >> 32, i / 2, 0) and key (seed mod 2^32,
+ * seed >> 32), u = ((w1 << 32 | w0) >> 11) * 2^-53 for even i and the same from
+ * (w3, w2) for odd i.  Successive batches of one Monte Carlo run continue the
+ * stream by advancing first_sample; no host copy of times is needed.
+ * Errors: as cos_set_samples.
+ */
+int cos_set_samples_uniform(cos_graph_t g, int64_t num_samples, uint64_t seed, int64_t first_sample,
+                            const double* eps, double beta, void* stream);
+
+/*
+ * Copy the attached times to dst ([D][S] doubles, sample index fastest; device or
+ * host memory), asynchronously on stream -- e.g. to keep the samples a Monte Carlo
+ * batch was evaluated on.  Errors: COS_ERR_STATE without samples.
+ */
+int cos_copy_times(cos_graph_t g, double* dst, void* stream);
 
 /*
  * Evaluate the path sum of every attached sample (Fig. 1; Sec. II.C): one

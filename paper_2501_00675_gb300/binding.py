@@ -37,7 +37,7 @@ EXPORTED = ["cos_create_graph", "cos_set_samples", "cos_evaluate", "cos_get_resu
             "cos_set_tuning", "cos_get_tuning", "cos_set_trace", "cos_get_trace", "cos_evaluate_static",
             "cos_graph_share", "cos_batch_create", "cos_batch_reset", "cos_batch_set_tuning", "cos_batch_get_tuning", "cos_batch_autotune",
             "cos_batch_launch", "cos_batch_results", "cos_batch_destroy", "cos_evaluate_batch",
-            "cos_selftest_exp", "cos_destroy", "cos_last_error"]
+            "cos_selftest_exp", "cos_set_samples_uniform", "cos_copy_times", "cos_destroy", "cos_last_error"]
 
 _lock = threading.Lock()
 _lib = None
@@ -96,6 +96,8 @@ def load_library(build_if_missing: bool = False):
         lib.cos_batch_destroy.argtypes = [vp]
         lib.cos_evaluate_batch.argtypes = [i32, vp, i32, vp, vp, vp]
         lib.cos_selftest_exp.argtypes = [vp, i64, vp, vp, vp, vp]
+        lib.cos_set_samples_uniform.argtypes = [vp, i64, ctypes.c_uint64, i64, vp, f64, vp]
+        lib.cos_copy_times.argtypes = [vp, vp, vp]
         lib.cos_destroy.argtypes = [vp]
         lib.cos_last_error.restype = ctypes.c_char_p
         lib.cos_last_error.argtypes = []
@@ -177,6 +179,18 @@ class Graph:
         _check(load_library().cos_set_samples(self._h, int(num_samples), _ptr(t), int(t_flags), _ptr(eps),
                                               float(beta), _stream_handle(stream)))
         self.num_samples = int(num_samples)
+
+    def set_samples_uniform(self, num_samples: int, seed: int, eps, beta: float, first_sample: int = 0, stream=None):
+        """cos_set_samples_uniform: times drawn on the device by the counter-based generator."""
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        self._eps = eps
+        _check(load_library().cos_set_samples_uniform(self._h, int(num_samples), int(seed), int(first_sample),
+                                                      _ptr(eps), float(beta), _stream_handle(stream)))
+        self.num_samples = int(num_samples)
+
+    def copy_times(self, dst, stream=None):
+        """cos_copy_times into dst ([D][S] doubles, torch tensor or numpy array)."""
+        _check(load_library().cos_copy_times(self._h, _ptr(dst), _stream_handle(stream)))
 
     def evaluate(self, mode: int, out=None, want_mean: bool = True, stream=None, allow_overflow: bool = False):
         """Run cos_evaluate; returns the mean (float) if want_mean else None."""

@@ -63,6 +63,23 @@ void dfree(T*& p) {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+constexpr int32_t kSignBit = 0x40000000;   // kind bit 30: the edge closes a fermion loop
+constexpr int32_t kKindMask = 0x3fffffff;
+
+// Propagator slot key of an edge row (src, dst, kind|sign, i, j).
+int64_t edge_key(const int32_t* r, int32_t D) {
+    const int64_t kind = r[2] & kKindMask, neg = (r[2] & kSignBit) ? 1 : 0;
+    return (((kind * D) + r[3]) * D + r[4]) * 2 + neg;
+}
+
+// (kind, i, j | sign << 30) of a slot key.
+void decode_key(int64_t key, int32_t D, int32_t* kij) {
+    const int64_t neg = key & 1, rest = key >> 1;
+    kij[0] = (int32_t)(rest / ((int64_t)D * D));
+    kij[1] = (int32_t)((rest / D) % D);
+    kij[2] = (int32_t)(rest % D) | (neg ? kSignBit : 0);
+}
+
 // Device arrays of one graph structure, shared by every handle created from it with
 // cos_graph_share and freed with the last of them.
 struct SharedArrays {
@@ -198,7 +215,8 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
     const int64_t N = off[L];
 
     // Validate every edge against its level, and number the propagator slots.
-    const int64_t key_space = (int64_t)num_kinds * num_times * num_times;
+    // slot key = ((kind * D + i) * D + j) * 2 + fermion-loop sign (kind bit 30)
+    const int64_t key_space = (int64_t)num_kinds * num_times * num_times * 2;
     const bool dense = key_space <= (1LL << 22);
     std::vector<int32_t> dense_slot;
     if (dense) dense_slot.assign((size_t)key_space, -1);
@@ -212,11 +230,11 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
                 return fail(COS_ERR_INVALID, "edge %lld into level %d: src %d is not in level %d", (long long)q, l, r[0], l - 1);
             if (r[1] < off[l] || r[1] >= off[l + 1])
                 return fail(COS_ERR_INVALID, "edge %lld into level %d: dst %d is not in level %d", (long long)q, l, r[1], l);
-            if (r[2] < 0 || r[2] >= num_kinds)
-                return fail(COS_ERR_INVALID, "edge %lld: kind %d out of range [0,%d)", (long long)q, r[2], num_kinds);
+            if (r[2] < 0 || (r[2] & kKindMask) >= num_kinds)
+                return fail(COS_ERR_INVALID, "edge %lld: kind %d out of range [0,%d)", (long long)q, r[2] & kKindMask, num_kinds);
             if (r[3] < 0 || r[3] >= num_times || r[4] < 0 || r[4] >= num_times)
                 return fail(COS_ERR_INVALID, "edge %lld: time index out of range [0,%d)", (long long)q, num_times);
-            int64_t key = ((int64_t)r[2] * num_times + r[3]) * num_times + r[4];
+            int64_t key = edge_key(r, num_times);
             if (dense) dense_slot[(size_t)key] = 0;
             else keys.push_back(key);
         }
@@ -231,9 +249,7 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
         for (int64_t key = 0; key < key_space; ++key) {
             int32_t s = dense_slot[(size_t)key];
             if (s < 0) continue;
-            slot_kij[3 * s + 0] = (int32_t)(key / ((int64_t)num_times * num_times));
-            slot_kij[3 * s + 1] = (int32_t)((key / num_times) % num_times);
-            slot_kij[3 * s + 2] = (int32_t)(key % num_times);
+            decode_key(key, num_times, slot_kij.data() + 3 * s);
         }
     } else {
         std::sort(keys.begin(), keys.end());
@@ -241,10 +257,7 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
         P = (int64_t)keys.size();
         slot_kij.resize((size_t)(3 * P));
         for (int64_t s = 0; s < P; ++s) {
-            int64_t key = keys[(size_t)s];
-            slot_kij[3 * s + 0] = (int32_t)(key / ((int64_t)num_times * num_times));
-            slot_kij[3 * s + 1] = (int32_t)((key / num_times) % num_times);
-            slot_kij[3 * s + 2] = (int32_t)(key % num_times);
+            decode_key(keys[(size_t)s], num_times, slot_kij.data() + 3 * s);
         }
     }
 
@@ -263,7 +276,7 @@ int cos_create_graph(int32_t num_levels, const int64_t* level_width, const int64
         for (int64_t q = e0; q < e0 + level_edge_count[l]; ++q) {
             const int32_t* r = edges + 5 * q;
             int64_t pos = e0 + cnt[(size_t)(r[1] - off[l])]++;
-            int64_t key = ((int64_t)r[2] * num_times + r[3]) * num_times + r[4];
+            int64_t key = edge_key(r, num_times);
             int32_t slot = dense ? dense_slot[(size_t)key]
                                  : (int32_t)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
             csr[(size_t)pos] = make_int2((int32_t)(r[0] - off[l - 1]), slot);
@@ -563,6 +576,44 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
     g->t_ld = t_ld;
     g->beta = beta;
     g->has_samples = true;
+    return COS_OK;
+}
+
+int cos_set_samples_uniform(cos_graph_t g, int64_t num_samples, uint64_t seed, int64_t first_sample,
+                            const double* eps, double beta, void* stream) {
+    if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
+    if (num_samples < 0 || first_sample < 0) return fail(COS_ERR_INVALID, "num_samples and first_sample must be >= 0");
+    // attach as a borrowed empty sample set first (validates eps/beta, sizes the workspace) ...
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(COS_ERR_CUDA, "cannot select device %d", g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t t_ld = std::max<int64_t>(round_up(num_samples, 128), 128);
+    if (t_ld * g->D > g->t_cap) {
+        dfree(g->d_t);
+        COS_CUDA(cudaMalloc(&g->d_t, sizeof(double) * t_ld * g->D), "cudaMalloc t");
+        g->t_cap = t_ld * g->D;
+    }
+    int rc = cos_set_samples(g, num_samples, g->d_t, COS_T_BORROW, eps, beta, stream);
+    if (rc != COS_OK) return rc;
+    // ... then fill the graph's own time buffer with the counter-based draws
+    g->t_borrowed = nullptr;
+    COS_CUDA(cudaMemsetAsync(g->d_t, 0, sizeof(double) * t_ld * g->D, st), "clear t");
+    if (num_samples > 0) {
+        rc = launch_uniform_times(seed, first_sample, num_samples, g->D, beta, g->d_t, t_ld, st);
+        if (rc != COS_OK) return fail(rc, "sampler launch failed");
+    }
+    return COS_OK;
+}
+
+int cos_copy_times(cos_graph_t g, double* dst, void* stream) {
+    if (!g || !dst) return fail(COS_ERR_INVALID, "bad arguments");
+    if (!g->has_samples) return fail(COS_ERR_STATE, "no samples attached");
+    DeviceGuard dg(g->device);
+    const double* src = g->t_borrowed ? g->t_borrowed : g->d_t;
+    if (g->S > 0)
+        COS_CUDA(cudaMemcpy2DAsync(dst, sizeof(double) * g->S, src, sizeof(double) * g->t_ld, sizeof(double) * g->S,
+                                   g->D, cudaMemcpyDefault, (cudaStream_t)stream),
+                 "copy times");
     return COS_OK;
 }
 

@@ -40,7 +40,7 @@ struct WalkParams {
     const LevelDesc* levels;   // [L]
     const int32_t* row_ptr;    // [N+1], indexed by global node id
     const int2* edges;         // [E]: (src index inside previous level, propagator slot)
-    const int32_t* slot_kij;   // [3P]: (kind, i, j) per slot
+    const int32_t* slot_kij;   // [3P]: (kind, i, j | sign << 30) per slot
     int32_t L, P, K, D;
     // samples
     const double* t;           // [D][t_ld], sample index fastest, zero padded
@@ -109,6 +109,9 @@ int walk_smem_bytes(int mode, int vec, int layout, int D);
 int prepare_kernel_attrs(const void* kernel, int smem_bytes);
 // e^{-x} and e^{+x} with the evaluator's table-driven exponentials (self test).
 int launch_exp_pair(const double* x, int64_t n, const double* tab, double* em, double* ep, cudaStream_t stream);
+// Counter-based uniform times t[i][s] in [0, beta) for samples first..first+S-1.
+int launch_uniform_times(uint64_t seed, int64_t first, int64_t S, int32_t D, double beta, double* t, int64_t t_ld,
+                         cudaStream_t stream);
 // Transpose t from [S][D] (src_ld = D) into [D][t_ld].
 int launch_transpose(const double* src, int64_t S, int32_t D, double* dst, int64_t t_ld, cudaStream_t stream);
 

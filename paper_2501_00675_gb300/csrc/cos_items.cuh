@@ -327,7 +327,8 @@ __host__ __device__ constexpr int prop_smem_bytes(int D, int chv) { return 4 * 8
 // slot q = (k, i, j) of this kind:
 //   G[c][q][s] = (t_i >= t_j ? coef+ : coef-) e^{-eps_k t_i} e^{+eps_k t_j}
 // formed in double, rounded once to the propagator type.  The kind-k slots are the
-// contiguous range [kind_slot[k], kind_slot[k+1]).  The first kind also writes the
+// contiguous range [kind_slot[k], kind_slot[k+1]); bit 30 of a slot's j field marks a
+// fermion-loop edge, whose factor is negated.  The first kind also writes the
 // chunk's root values (node 0 holds 1, Fig. 1 caption).
 template <int MODE, int CHV>
 __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& tc, int item, double* sm) {
@@ -378,12 +379,15 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
             use_ff = !__syncthreads_or(out_of_range);
             if (use_ff) {
                 for (int q = q0 + warp; q < q1; q += kWarps) {
-                    const int i = __ldg(p.slot_kij + 3 * q + 1), j = __ldg(p.slot_kij + 3 * q + 2);
+                    const int i = __ldg(p.slot_kij + 3 * q + 1), jw = __ldg(p.slot_kij + 3 * q + 2);
+                    const int j = jw & 0x3fffffff;
+                    const unsigned smask = (jw & 0x40000000) ? 0x80000000u : 0u;   // closes a fermion loop
 #pragma unroll
                     for (int v = 0; v < CHV / 32; ++v) {
                         const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
                         const float2 a = (st[xi] >= st[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
-                        __stcg(reinterpret_cast<float*>(gt) + (int64_t)q * CHV + v * 32 + lane, mul_ff(a, fe_[xj]));
+                        __stcg(reinterpret_cast<float*>(gt) + (int64_t)q * CHV + v * 32 + lane,
+                               __uint_as_float(__float_as_uint(mul_ff(a, fe_[xj])) ^ smask));
                     }
                 }
             }
@@ -405,12 +409,16 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
             }
             __syncthreads();
             for (int q = q0 + warp; q < q1; q += kWarps) {
-                const int i = __ldg(p.slot_kij + 3 * q + 1), j = __ldg(p.slot_kij + 3 * q + 2);
+                const int i = __ldg(p.slot_kij + 3 * q + 1), jw = __ldg(p.slot_kij + 3 * q + 2);
+                const int j = jw & 0x3fffffff;
+                // closes a fermion loop: flip the sign bit (no extra FP64 operation)
+                const long long smask = (jw & 0x40000000) ? (long long)0x8000000000000000ULL : 0LL;
 #pragma unroll
                 for (int v = 0; v < CHV / 32; ++v) {
                     const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
                     const double a = (st[xi] >= st[xj]) ? sp[xi] : sn[xi];   // tau = t_i - t_j >= 0 ?
-                    __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)(a * se[xj]));
+                    const double g = __longlong_as_double(__double_as_longlong(a * se[xj]) ^ smask);
+                    __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
                 }
             }
         }

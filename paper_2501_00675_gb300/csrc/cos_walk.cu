@@ -108,6 +108,43 @@ __global__ void transpose_kernel(const double* __restrict__ src, int64_t S, int3
     }
 }
 
+// Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): counter (c0..c3),
+// key (k0, k1); each round multiplies c0 and c2 by the round constants and mixes the
+// high halves with c1, c3 and the key, which advances by the Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// t[2m][s], t[2m+1][s] for sample n = first + s: counter (n lo, n hi, m, 0), key = seed;
+// 53 bits of each word pair scaled to [0, beta).
+__global__ void uniform_times_kernel(unsigned long long seed, long long first, long long S, int D, double beta,
+                                     double* __restrict__ t, long long t_ld) {
+    const int pairs = (D + 1) / 2;
+    const long long total = S * pairs;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(q / S);
+        const long long s = q - (long long)m * S;
+        const unsigned long long n = (unsigned long long)(first + s);
+        const uint4 w = philox4x32_10(make_uint4((unsigned)n, (unsigned)(n >> 32), (unsigned)m, 0u), (unsigned)seed,
+                                      (unsigned)(seed >> 32));
+        const unsigned long long a = (((unsigned long long)w.y << 32) | w.x) >> 11;
+        const unsigned long long b = (((unsigned long long)w.w << 32) | w.z) >> 11;
+        t[(long long)(2 * m) * t_ld + s] = beta * ((double)a * 0x1.0p-53);
+        if (2 * m + 1 < D) t[(long long)(2 * m + 1) * t_ld + s] = beta * ((double)b * 0x1.0p-53);
+    }
+}
+
 __global__ void exp_pair_kernel(const double* __restrict__ x, int64_t n, const double* __restrict__ tab,
                                 double* __restrict__ em, double* __restrict__ ep) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
@@ -195,6 +232,14 @@ int launch_walk(int mode, int vec, int layout, const WalkParams& p, int grid, cu
 int launch_exp_pair(const double* x, int64_t n, const double* tab, double* em, double* ep, cudaStream_t stream) {
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152LL * 16);
     exp_pair_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(x, n, tab, em, ep);
+    return cudaGetLastError() == cudaSuccess ? COS_OK : COS_ERR_CUDA;
+}
+
+int launch_uniform_times(uint64_t seed, int64_t first, int64_t S, int32_t D, double beta, double* t, int64_t t_ld,
+                         cudaStream_t stream) {
+    const int64_t total = S * ((D + 1) / 2);
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152LL * 16);
+    uniform_times_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(seed, first, S, D, beta, t, t_ld);
     return cudaGetLastError() == cudaSuccess ? COS_OK : COS_ERR_CUDA;
 }
 

@@ -86,6 +86,14 @@ def _set1(a, i, val):
     return a
 
 
+def test_kind_sign_bit_is_accepted_and_bit_31_rejected(lib):
+    w, c, e = _fig()
+    e = e.copy()
+    e[3, 2] = -1                                  # bit 31: invalid
+    rc, msg = _create(lib, w, c, e)
+    assert rc == binding.COS_ERR_INVALID and "kind" in msg
+
+
 def test_non_consecutive_levels_rejected(lib):
     # an edge that skips a level (0 -> level 2) is invalid
     w = [1, 2, 2, 1]

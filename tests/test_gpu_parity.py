@@ -336,3 +336,47 @@ def test_mixed_mode_wide_energy_range_and_time_fallback(cg):
         check_fp(Rg, mg, R, A, 1)
         Rg, mg = run_gpu(cg, g, eps, 10.0, t, 0)
         check_fp(Rg, mg, R, A, 0)
+
+
+def test_fermion_loop_sign_flags(cg):
+    # kind bit 30 negates an edge's factor (Sec. II.C); flagged and unflagged edges of the
+    # same (kind, i, j) use distinct propagator slots
+    from workloads import Graph
+    w = medium(num_samples=900)
+    g = w.graph
+    e = g.edges.copy()
+    e[np.random.default_rng(8).random(g.num_edges) < 0.3, 2] |= oracle.SIGN_BIT
+    gs = Graph(g.widths, g.edge_counts, e, g.num_kinds, g.num_times)
+    R, A = oracle.evaluate(gs, w.samples.eps, w.samples.beta, w.samples.t)
+    for mode in (0, 1):
+        Rg, mg = run_gpu(cg, gs, w.samples.eps, w.samples.beta, w.samples.t, mode)
+        check_fp(Rg, mg, R, A, mode)
+    R0, _ = oracle.evaluate(g, w.samples.eps, w.samples.beta, w.samples.t)
+    assert not np.allclose(R, R0)                    # the flags matter
+    cnt, _ = oracle.count_paths(gs)
+    Rc, _ = run_gpu(cg, gs, w.samples.eps, w.samples.beta, w.samples.t, 2)
+    assert np.all(Rc == cnt)                         # counting ignores signs
+    gr = cg.Graph.from_workload_graph(gs)
+    assert gr.info()["P"] > cg.Graph.from_workload_graph(g).info()["P"]
+    gr.close()
+
+
+@pytest.mark.parametrize("first", [0, (1 << 32) - 100])
+def test_device_counter_times_match_and_evaluate(cg, first):
+    # the device sampler and the host generator implement the same counter-based
+    # draws independently: the times must agree bit for bit, the results within tolerance
+    from workloads import counter_times
+    w = tiny()
+    S, D = 3000, w.graph.num_times
+    t_host = counter_times(99, first, S, D, w.samples.beta)
+    gr = cg.Graph.from_workload_graph(w.graph)
+    gr.set_samples_uniform(S, 99, w.samples.eps, w.samples.beta, first_sample=first)
+    tdev = torch.empty((D, S), dtype=torch.float64, device="cuda")
+    gr.copy_times(tdev)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(tdev.cpu().numpy().T, t_host)
+    out = torch.empty(S, dtype=torch.float64, device="cuda")
+    m = gr.evaluate(0, out=out)
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, t_host)
+    check_fp(out.cpu().numpy(), m, R, A, 0)
+    gr.close()

@@ -67,3 +67,20 @@ def test_batched_and_pool_are_valid():
     for g, eps in serving_pool(pool_size=3, max_nodes=2e4):
         _check_graph(g, 6)
         assert eps.shape == (32,)
+
+
+def test_counter_times_uniform_and_continuable():
+    import scipy.stats as st
+    from workloads import counter_times
+    t = counter_times(2024, 0, 200000, 5, 10.0)
+    assert t.shape == (200000, 5) and t.min() >= 0.0 and t.max() < 10.0
+    for i in range(5):
+        assert st.kstest(t[:, i] / 10.0, "uniform").pvalue > 1e-3
+    assert abs(np.corrcoef(t[:-1, 0], t[1:, 0])[0, 1]) < 0.01          # neighbouring counters
+    assert abs(np.corrcoef(t[:, 0], t[:, 1])[0, 1]) < 0.01             # the two words of one counter
+    assert abs(np.corrcoef(t[:, 1], t[:, 2])[0, 1]) < 0.01             # neighbouring pairs
+    # a later batch continues the stream; another seed gives another stream; deterministic
+    np.testing.assert_array_equal(counter_times(2024, 150000, 50000, 5, 10.0), t[150000:])
+    assert not np.any(counter_times(2025, 0, 1000, 5, 10.0) == t[:1000])
+    np.testing.assert_array_equal(counter_times(2024, 0, 1000, 5, 10.0), t[:1000])
+    assert counter_times(7, 0, 0, 3, 1.0).shape == (0, 3)

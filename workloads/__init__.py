@@ -9,5 +9,5 @@ from .generate import (  # noqa: F401
     Graph, Samples, Workload, FaninSpec, make_graph, make_eps, make_times,
     tiny, medium, large, batched, serving_pool, complete_layered_graph,
     chain_graph, figure_graph, geometric_widths, widths_for_target,
-    WORKLOADS,
+    WORKLOADS, philox4x32_10, counter_times,
 )

@@ -305,3 +305,53 @@ def figure_graph() -> Graph:
 
 
 WORKLOADS: Dict[str, Callable[..., Workload]] = {"tiny": tiny, "medium": medium, "large": large}
+
+
+# ---------------------------------------------------------------------------- counter-based times
+
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11), vectorised over
+    numpy uint32 arrays: each round multiplies two words by the round constants,
+    mixes the high halves with the other words and the key, and bumps the key by the
+    Weyl constants between rounds."""
+    c0, c1, c2, c3 = (np.asarray(x, dtype=np.uint64) & 0xFFFFFFFF for x in (c0, c1, c2, c3))
+    k0 = np.uint64(k0 & 0xFFFFFFFF)
+    k1 = np.uint64(k1 & 0xFFFFFFFF)
+    mask = np.uint64(0xFFFFFFFF)
+    for r in range(10):
+        if r:
+            k0 = (k0 + np.uint64(_PHILOX_W0)) & mask
+            k1 = (k1 + np.uint64(_PHILOX_W1)) & mask
+        p0 = np.uint64(_PHILOX_M0) * c0
+        p1 = np.uint64(_PHILOX_M1) * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
+        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
+        c0, c1, c2, c3 = (hi1 ^ c1 ^ k0) & mask, lo1, (hi0 ^ c3 ^ k1) & mask, lo0
+    return c0, c1, c2, c3
+
+
+def counter_times(seed: int, first_sample: int, num_samples: int, num_times: int, beta: float) -> np.ndarray:
+    """Times t[s][i] ~ U[0, beta) from a counter-based generator: for sample index
+    n = first_sample + s and pair m = i // 2, Philox-4x32-10 with counter
+    (n mod 2^32, n >> 32, m, 0) and key (seed mod 2^32, seed >> 32) gives words w0..w3;
+    t[s][2m] = beta * ((w1 << 32 | w0) >> 11) * 2^-53 and t[s][2m+1] likewise from
+    (w3, w2).  Returns [S, D] float64."""
+    S, D = int(num_samples), int(num_times)
+    out = np.empty((S, D), dtype=np.float64)
+    if S == 0:
+        return out
+    n = np.arange(first_sample, first_sample + S, dtype=np.uint64)
+    lo, hi = n & np.uint64(0xFFFFFFFF), n >> np.uint64(32)
+    for m in range((D + 1) // 2):
+        w0, w1, w2, w3 = philox4x32_10(lo, hi, np.full(S, m, np.uint64), np.zeros(S, np.uint64),
+                                       seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+        a = ((w1 << np.uint64(32)) | w0) >> np.uint64(11)
+        b = ((w3 << np.uint64(32)) | w2) >> np.uint64(11)
+        out[:, 2 * m] = beta * (a.astype(np.float64) * 2.0 ** -53)
+        if 2 * m + 1 < D:
+            out[:, 2 * m + 1] = beta * (b.astype(np.float64) * 2.0 ** -53)
+    return out
