@@ -576,7 +576,8 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
 
 // Grouped layout (CHV = 32).  Same items and the same per-row order as the wide
 // layout; a warp's rows are split into V groups of consecutive rows and each group
-// of 32/V lanes streams the CSR edge range of its own rows.
+// of 32/V lanes streams the CSR edge range of its own rows, metadata in windows of
+// 32/V edges shuffled within the group, U edges' loads in flight per group.
 template <int MODE, int V>
 __device__ __forceinline__ void item_level_grouped(const WalkParams& p, int l, const TileCtx& tc, int item) {
     using Tr = Traits<MODE>;
@@ -626,46 +627,59 @@ __device__ __forceinline__ void item_level_grouped(const WalkParams& p, int l, c
     for (unsigned m = group_rows & ~nonempty; m; m &= m - 1)   // rows without in-edges hold 0
         store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(m) - 1, tc, off, acc);
     unsigned rows_left = group_rows & nonempty;
-    int cur = rows_left ? __ffs(rows_left) - 1 : 0;
-    int cur_end = __shfl_sync(0xffffffffu, rp, (cur + 1) & 31);
     const int len = eend - ebeg;
     int maxlen = len;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
-    for (int i0 = 0; i0 < maxlen; i0 += U) {
-        VecT<Val, V> pv[U];
-        VecT<Prop, V> gv[U];
+    // lane j < nr: the group owning row j, and that group's first edge
+    int gj = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = ebeg + i0 + u;
-            const int2 m = (i0 + u < len) ? __ldg(p.edges + e) : make_int2(0, 0);
-            pv[u] = load_cg<Val, V>(pc + (int64_t)m.x * CHV);
-            if constexpr (!Tr::kCount) gv[u] = load_ca<Prop, V>(gc + (int64_t)m.y * CHV);
-        }
+    for (int g = 1; g < V; ++g)
+        if (lane >= (g * nr) / V) gj = g;
+    const int ebeg_j = __shfl_sync(0xffffffffu, rp, (gj * nr) / V);
+    // each group streams its edges in windows of LPR: lane gl holds the metadata of edge
+    // ebeg + w0 + gl of its own group; shuffles within the group broadcast it
+    for (int w0 = 0; w0 < maxlen; w0 += LPR) {
+        const int2 meta = (w0 + gl < len) ? __ldg(p.edges + ebeg + w0 + gl) : make_int2(0, 0);
+        // bit g*LPR + q set <=> edge w0 + q of group g closes a row
+        const int pos = rp_next - 1 - (ebeg_j + w0);
+        const unsigned ends = __reduce_or_sync(
+            0xffffffffu, (lane < nr && rp_next > rp && pos >= 0 && pos < LPR) ? (1u << (gj * LPR + pos)) : 0u);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = ebeg + i0 + u;
-            const bool valid = (i0 + u < len);
-            if (valid) {
-                if constexpr (Tr::kCount) {
+        for (int q0 = 0; q0 < LPR; q0 += U) {
+            if (w0 + q0 >= maxlen) break;
+            VecT<Val, V> pv[U];
+            VecT<Prop, V> gv[U];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] += pv[u].v[v];
-                } else {
-#pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] = madd(pv[u].v[v], gv[u].v[v], acc[v]);
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u;
+                const bool valid = (w0 + q < len);
+                const int src = __shfl_sync(0xffffffffu, meta.x, q, LPR);
+                pv[u] = load_cg<Val, V>(pc + (int64_t)(valid ? src : 0) * CHV);
+                if constexpr (!Tr::kCount) {
+                    const int slot = __shfl_sync(0xffffffffu, meta.y, q, LPR);
+                    gv[u] = load_ca<Prop, V>(gc + (int64_t)(valid ? slot : 0) * CHV);
                 }
             }
-            const bool closes = valid && (e + 1 == cur_end);
-            if (closes) {
-                store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + cur, tc, off, acc);
 #pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = (Val)0;
-                rows_left &= rows_left - 1;
-                cur = rows_left ? __ffs(rows_left) - 1 : cur;
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u;
+                if (w0 + q < len) {
+                    if constexpr (Tr::kCount) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] += pv[u].v[v];
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = madd(pv[u].v[v], gv[u].v[v], acc[v]);
+                    }
+                    if ((ends >> (gid * LPR + q)) & 1u) {
+                        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(rows_left) - 1, tc, off, acc);
+                        rows_left &= rows_left - 1;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+                    }
+                }
             }
-            // every lane takes part in the shuffle; only closing groups change their row end
-            const int next_end = __shfl_sync(0xffffffffu, rp, (cur + 1) & 31);
-            if (closes) cur_end = next_end;
         }
     }
 }
@@ -678,8 +692,9 @@ __device__ __forceinline__ void item_level(const WalkParams& p, int l, const Til
 
 // ---------------------------------------------------------------- phase: sample reduction
 
-// Compensated partial sums of R over blocks of kReduceBlock samples, in index order:
-// lane q sums its 128 consecutive samples, lane partials are then added in lane order.
+// Compensated partial sums of R over blocks of kReduceBlock samples in a fixed order:
+// lane q adds samples q, q+32, q+64, ... of the block (coalesced loads, eight issued
+// ahead of the Neumaier adds), then the 32 lane partials are added in lane order.
 // Item = kWarps consecutive blocks (one per warp).
 __device__ __forceinline__ int partial_items(const WalkParams& p) {
     const int64_t nblk = (p.S + kReduceBlock - 1) / kReduceBlock;
@@ -693,15 +708,23 @@ __device__ __forceinline__ void item_partials(const WalkParams& p, int item) {
     const int64_t b = (int64_t)item * kWarps + warp;
     if (b >= nblk) return;
     constexpr int per_lane = kReduceBlock / 32;
+    constexpr int AHEAD = 8;
     double sum = 0.0, comp = 0.0;
-    const int64_t s0 = b * kReduceBlock + (int64_t)lane * per_lane;
-    for (int q = 0; q < per_lane; ++q) {
-        const int64_t s = s0 + q;
-        if (s >= p.S) break;
-        double x;
-        if constexpr (MODE == COS_MODE_COUNT_I64) x = (double)static_cast<const long long*>(p.R)[s];
-        else x = static_cast<const double*>(p.R)[s];
-        neumaier_add(sum, comp, x);
+    const int64_t s0 = b * kReduceBlock + lane;
+    for (int q0 = 0; q0 < per_lane; q0 += AHEAD) {
+        double x[AHEAD];
+#pragma unroll
+        for (int u = 0; u < AHEAD; ++u) {
+            const int64_t s = s0 + (int64_t)(q0 + u) * 32;
+            if (s < p.S) {
+                if constexpr (MODE == COS_MODE_COUNT_I64) x[u] = (double)static_cast<const long long*>(p.R)[s];
+                else x[u] = static_cast<const double*>(p.R)[s];
+            } else {
+                x[u] = 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < AHEAD; ++u) neumaier_add(sum, comp, x[u]);
     }
     const double mine = sum + comp;
     double bs = 0.0, bc = 0.0;
