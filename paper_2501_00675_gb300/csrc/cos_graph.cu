@@ -456,7 +456,7 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
 static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* tile_out) {
     cos_tuning t = g->tuning;
     if (t.samples_per_lane <= 0) t.samples_per_lane = default_vec(mode);
-    if (t.rows_per_warp <= 0) t.rows_per_warp = 16;
+    if (t.rows_per_warp <= 0) t.rows_per_warp = (mode == COS_MODE_FP64) ? 4 : 8;   // measured best on GB300
     if (t.layout <= 0) t.layout = 1;
     if (t.timeout_ms <= 0) {
         const char* env = getenv("COS_TIMEOUT_MS");
@@ -526,7 +526,7 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
     const int64_t nblk = std::max<int64_t>((S + kReduceBlock - 1) / kReduceBlock, 1);
     if (nblk > g->partial_cap) {
         dfree(g->d_partials);
-        const int64_t cap = std::max<int64_t>(nblk, 1024);   // room for 4M samples without regrowth
+        const int64_t cap = std::max<int64_t>(nblk, 4096);   // room for 4M samples without regrowth
         COS_CUDA(cudaMalloc(&g->d_partials, sizeof(double) * cap), "cudaMalloc partials");
         g->partial_cap = cap;
     }

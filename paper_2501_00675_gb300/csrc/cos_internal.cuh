@@ -56,7 +56,7 @@ struct WalkParams {
     const double* exp_tab;     // [128]: 2^{j/64}, then 2^{-j/64}, j = 0..63; followed by the same
                                // 128 values as float-float (hi, lo) pairs (256 floats)
     void* R;                   // [S] sink value per sample (double, or int64 in count mode)
-    double* partials;          // [ceil(S/4096)] compensated partial sums
+    double* partials;          // [ceil(S/kReduceBlock)] compensated partial sums
     Ctrl* ctrl;
     int64_t tile;              // samples per tile (multiple of CH)
     int32_t rows_per_warp;
@@ -70,7 +70,7 @@ struct WalkParams {
 
 constexpr int kThreads = 256;           // 8 warps per CTA
 constexpr int kWarps = kThreads / 32;
-constexpr int kReduceBlock = 4096;      // samples per compensated partial sum
+constexpr int kReduceBlock = 1024;      // samples per compensated partial sum
 
 // Device-resident view of a graph handle (read-only), for entry points that
 // evaluate an existing graph with scratch memory of their own.

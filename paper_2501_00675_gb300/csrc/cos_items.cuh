@@ -692,10 +692,28 @@ __device__ __forceinline__ void item_level(const WalkParams& p, int l, const Til
 
 // ---------------------------------------------------------------- phase: sample reduction
 
+// Error-free sum of two compensated values (Knuth's TwoSum on the leading parts, the
+// rounding error folded into the compensation); symmetric, so both lanes of a
+// shuffle pair obtain the same result.
+__device__ __forceinline__ void add_pair(double& s, double& c, double s2, double c2) {
+    const double x = s + s2;
+    const double z = x - s;
+    const double err = (s - (x - z)) + (s2 - z);
+    s = x;
+    c = (c + c2) + err;
+}
+
+// Compensated sum of one value per lane: pairwise over lanes (xor tree), every lane
+// ends with the same (sum, compensation).
+__device__ __forceinline__ void warp_sum(double& s, double& c) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) add_pair(s, c, __shfl_xor_sync(0xffffffffu, s, o), __shfl_xor_sync(0xffffffffu, c, o));
+}
+
 // Compensated partial sums of R over blocks of kReduceBlock samples in a fixed order:
-// lane q adds samples q, q+32, q+64, ... of the block (coalesced loads, eight issued
-// ahead of the Neumaier adds), then the 32 lane partials are added in lane order.
-// Item = kWarps consecutive blocks (one per warp).
+// lane q adds samples q, q+32, q+64, ... of the block with Neumaier compensation
+// (coalesced loads, all issued ahead of the adds), then the lanes are combined by an
+// error-free pairwise tree.  Item = kWarps consecutive blocks (one per warp).
 __device__ __forceinline__ int partial_items(const WalkParams& p) {
     const int64_t nblk = (p.S + kReduceBlock - 1) / kReduceBlock;
     return (int)((nblk + kWarps - 1) / kWarps);
@@ -708,40 +726,40 @@ __device__ __forceinline__ void item_partials(const WalkParams& p, int item) {
     const int64_t b = (int64_t)item * kWarps + warp;
     if (b >= nblk) return;
     constexpr int per_lane = kReduceBlock / 32;
-    constexpr int AHEAD = 8;
-    double sum = 0.0, comp = 0.0;
+    double x[per_lane];
     const int64_t s0 = b * kReduceBlock + lane;
-    for (int q0 = 0; q0 < per_lane; q0 += AHEAD) {
-        double x[AHEAD];
 #pragma unroll
-        for (int u = 0; u < AHEAD; ++u) {
-            const int64_t s = s0 + (int64_t)(q0 + u) * 32;
-            if (s < p.S) {
-                if constexpr (MODE == COS_MODE_COUNT_I64) x[u] = (double)static_cast<const long long*>(p.R)[s];
-                else x[u] = static_cast<const double*>(p.R)[s];
-            } else {
-                x[u] = 0.0;
-            }
+    for (int u = 0; u < per_lane; ++u) {
+        const int64_t s = s0 + (int64_t)u * 32;
+        if (s < p.S) {
+            if constexpr (MODE == COS_MODE_COUNT_I64) x[u] = (double)static_cast<const long long*>(p.R)[s];
+            else x[u] = static_cast<const double*>(p.R)[s];
+        } else {
+            x[u] = 0.0;
         }
-#pragma unroll
-        for (int u = 0; u < AHEAD; ++u) neumaier_add(sum, comp, x[u]);
     }
-    const double mine = sum + comp;
-    double bs = 0.0, bc = 0.0;
-    for (int q = 0; q < 32; ++q) neumaier_add(bs, bc, __shfl_sync(0xffffffffu, mine, q));
-    if (lane == 0) p.partials[b] = bs + bc;
+    double sum = 0.0, comp = 0.0;
+#pragma unroll
+    for (int u = 0; u < per_lane; ++u) neumaier_add(sum, comp, x[u]);
+    warp_sum(sum, comp);
+    if (lane == 0) p.partials[b] = sum + comp;
 }
 
-// Final compensated sum of the partials in block order; the mean over samples.
+// Final compensated sum of the block partials (lane-strided Neumaier, then the lane
+// tree) by warp 0 of one CTA; the mean over samples.
 __device__ __forceinline__ void item_final(const WalkParams& p) {
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     const int64_t nblk = (p.S + kReduceBlock - 1) / kReduceBlock;
     double sum = 0.0, comp = 0.0;
-    for (int64_t b = 0; b < nblk; ++b) neumaier_add(sum, comp, p.partials[b]);
-    p.ctrl->sum = sum;
-    p.ctrl->comp = comp;
-    p.ctrl->mean = p.S > 0 ? (sum + comp) / (double)p.S : 0.0;
-    if (p.mean_out) *p.mean_out = p.ctrl->mean;
+    for (int64_t b = lane; b < nblk; b += 32) neumaier_add(sum, comp, p.partials[b]);
+    warp_sum(sum, comp);
+    if (lane == 0) {
+        p.ctrl->sum = sum;
+        p.ctrl->comp = comp;
+        p.ctrl->mean = p.S > 0 ? (sum + comp) / (double)p.S : 0.0;
+        if (p.mean_out) *p.mean_out = p.ctrl->mean;
+    }
 }
 
 }  // namespace cosgpu
