@@ -181,7 +181,10 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *   timeout_ms        grid-barrier wait limit
  *   layout            1 = wide (a warp owns one row; chunks of 32*samples_per_lane
  *                     samples), 2 = grouped (a warp owns samples_per_lane rows, each
- *                     served by 32/samples_per_lane lanes; chunks of 32 samples)
+ *                     served by 32/samples_per_lane lanes; chunks of 32 samples),
+ *                     3 = wide with a bulk-copy ring (one lane stages whole parent
+ *                     and propagator runs in shared memory with cp.async.bulk on
+ *                     mbarriers, 8 edges in flight per warp)
  */
 typedef struct cos_tuning {
     int32_t samples_per_lane;

@@ -45,6 +45,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "cos.h")]
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                     "-I", os.path.join(ROOT, "include")]
+    if os.environ.get("COS_DEBUG_CHECKS"):   # device self-checks (bounds, alignment) that record and skip
+        flags += ["-DCOS_DEBUG_CHECKS"]
     objs = []
     jobs = []
     for src in SOURCES:

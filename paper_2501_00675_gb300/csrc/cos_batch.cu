@@ -99,15 +99,21 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V>()) batch_k
         switch (tk.kind) {
             case TK_COEF: item_coef(p); break;
             case TK_PROP: item_props<MODE, CHV>(p, tile_ctx<CHV>(p, tk.tix), item, smem); break;
-            case TK_LEVEL: item_level<MODE, V, LAYOUT>(p, tk.level, tile_ctx<CHV>(p, tk.tix), item); break;
+            case TK_LEVEL:
+                if (!item_level<MODE, V, LAYOUT>(p, tk.level, tile_ctx<CHV>(p, tk.tix), item,
+                                                 reinterpret_cast<unsigned char*>(smem)) &&
+                    (threadIdx.x & 31) == 0) {   // a bounded wait gave up: report it for the whole launch
+                    const int code = *(volatile int*)&p.ctrl->err;
+                    if (atomicCAS(&a.ctrl->err, 0, code ? code : KERR_BARRIER_TIMEOUT) == 0)
+                        a.ctrl->err_task = code > 100 ? p.ctrl->err_detail : cursor;
+                }
+                break;
             case TK_PARTIALS: item_partials<MODE>(p, item); break;
             default: item_final(p); break;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(a.done + cursor, 1u);
-        }
+        if (threadIdx.x == 0)   // release: the item's writes are visible before it is counted done
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.done + cursor) : "memory");
     }
 }
 
@@ -133,6 +139,7 @@ const void* select_batch_layout(int mode, int vec) {
 }
 
 const void* select_batch_kernel(int mode, int vec, int layout) {
+    if (layout == 3) return select_batch_layout<LAYOUT_BULK>(mode, vec);
     if (layout == 2) return select_batch_layout<LAYOUT_GROUPED>(mode, vec);
     if (layout == 1) return select_batch_layout<LAYOUT_WIDE>(mode, vec);
     return nullptr;
@@ -260,7 +267,7 @@ int plan(cos_batch* b) {
     cos_tuning force = b->tuning;
     if (force.samples_per_lane <= 0) force.samples_per_lane = (mode == COS_MODE_FP32_MIXED) ? 4 : 2;
     if (force.layout <= 0) force.layout = 1;
-    const int chv = force.layout == 2 ? 32 : 32 * force.samples_per_lane;
+    const int chv = force.layout == 2 ? 32 : 32 * force.samples_per_lane;   // wide and bulk: 32 * V
     cos_tuning first = force;
     b->params.assign((size_t)b->n, WalkParams{});
     b->counts_overflow.assign((size_t)b->n, 0);
@@ -448,7 +455,7 @@ int cos_batch_set_tuning(cos_batch_t b, const cos_tuning* t) {
     if (t->samples_per_lane > 0 && t->samples_per_lane != 1 && t->samples_per_lane != 2 && t->samples_per_lane != 4)
         return set_error(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
     if (t->rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
-    if (t->layout < 0 || t->layout > 2) return set_error(COS_ERR_INVALID, "layout must be 0, 1 or 2");
+    if (t->layout < 0 || t->layout > 3) return set_error(COS_ERR_INVALID, "layout must be 0, 1, 2 or 3");
     b->tuning = *t;
     b->planned = false;
     return COS_OK;
@@ -507,7 +514,8 @@ int cos_batch_results(cos_batch_t b, double* means, void* stream) {
     if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "batch results: %s", cudaGetErrorString(e));
     if (b->h_ctrl->err == KERR_BARRIER_TIMEOUT)
         return set_error(COS_ERR_TIMEOUT, "dependency wait timed out (task %d)", b->h_ctrl->err_task);
-    if (b->h_ctrl->err != 0) return set_error(COS_ERR_CUDA, "batch kernel error %d", b->h_ctrl->err);
+    if (b->h_ctrl->err != 0)
+        return set_error(COS_ERR_CUDA, "batch kernel error %d (detail %d)", b->h_ctrl->err, b->h_ctrl->err_task);
     if (means)
         for (int32_t g = 0; g < b->n; ++g) means[g] = b->h_means[g];
     if (b->mode == COS_MODE_COUNT_I64)
@@ -530,7 +538,7 @@ int cos_batch_autotune(cos_batch_t b, void* stream, cos_tuning* best_out) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = COS_OK;
-    const int layouts[] = {1, 2};
+    const int layouts[] = {1, 2, 3};
     for (int lay : layouts)
     for (int v : vecs) {
         if (b->mode == COS_MODE_FP64 && v == 4) continue;   // register-heavy; never faster in FP64

@@ -448,7 +448,8 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
         return fail(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
     if (t->rows_per_warp > 31) return fail(COS_ERR_INVALID, "rows_per_warp must be <= 31");
     if (t->blocks_per_sm > 32) return fail(COS_ERR_INVALID, "blocks_per_sm must be <= 32");
-    if (t->layout < 0 || t->layout > 2) return fail(COS_ERR_INVALID, "layout must be 0 (auto), 1 (wide) or 2 (grouped)");
+    if (t->layout < 0 || t->layout > 3)
+        return fail(COS_ERR_INVALID, "layout must be 0 (auto), 1 (wide), 2 (grouped) or 3 (wide, bulk-copy ring)");
     g->tuning = *t;
     return COS_OK;
 }
@@ -623,7 +624,7 @@ static int collect(cos_graph_t g, double* mean_out, cudaStream_t st) {
     COS_CUDA(cudaStreamSynchronize(st), "synchronize");
     g->last_status_pending = 0;
     if (c.err == KERR_BARRIER_TIMEOUT) return fail(COS_ERR_TIMEOUT, "grid barrier timed out (phase %d)", c.err_detail);
-    if (c.err != 0) return fail(COS_ERR_CUDA, "kernel reported error %d", c.err);
+    if (c.err != 0) return fail(COS_ERR_CUDA, "kernel reported error %d (detail %d)", c.err, c.err_detail);
     if (mean_out) *mean_out = c.mean;
     if (g->last_mode == COS_MODE_COUNT_I64 && g->count_overflow)
         return fail(COS_ERR_OVERFLOW, "path count exceeds 2^63-1; results wrap modulo 2^64");

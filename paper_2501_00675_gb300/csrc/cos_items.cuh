@@ -21,11 +21,11 @@
 
 namespace cosgpu {
 
-enum Layout : int { LAYOUT_WIDE = 0, LAYOUT_GROUPED = 1 };
+enum Layout : int { LAYOUT_WIDE = 0, LAYOUT_GROUPED = 1, LAYOUT_BULK = 2 };
 
 template <int V, int LAYOUT>
 __host__ __device__ constexpr int chunk_samples() {
-    return LAYOUT == LAYOUT_WIDE ? 32 * V : 32;
+    return LAYOUT == LAYOUT_GROUPED ? 32 : 32 * V;
 }
 
 __device__ __forceinline__ unsigned long long global_timer_ns() {
@@ -131,6 +131,80 @@ __device__ __forceinline__ void store_cg(T* ptr, const VecT<T, V>& x) {
     }
 }
 
+// ---------------------------------------------------------------- bulk copies (TMA engine)
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Make mbarrier initialisation visible to the asynchronous (bulk copy) proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Order this thread's earlier generic-proxy view of global memory before its later
+// bulk copies (node values written by other CTAs before the last grid barrier).
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Return the memory of an mbarrier object to ordinary use (required before the shared
+// memory is reused by anything but mbarrier operations or initialised again).
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+    unsigned v;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// One bulk copy global -> shared of `bytes` (multiple of 16, both addresses 16-byte
+// aligned), completing as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of `bar`: gives up after timeout_ns (checked every
+// 64 polls), recording KERR_BARRIER_TIMEOUT; returns false then.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, const WalkParams& p) {
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 63) {
+            const unsigned long long now = global_timer_ns();
+            if (t0 == 0) t0 = now;
+            else if ((long long)(now - t0) > p.timeout_ns || it > (1u << 30)) {
+                atomicCAS(&p.ctrl->err, 0, KERR_BARRIER_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- mode traits
 
 template <int MODE>
@@ -156,6 +230,20 @@ struct Traits<COS_MODE_COUNT_I64> {  // unit weights, sums modulo 2^64
     using SinkAcc = unsigned long long;
     static constexpr bool kCount = true;
 };
+
+// Bulk-copy ring of the level walk: edges in flight per warp, and the shared memory of
+// one CTA: kWarps x kRing mbarriers (8 B each) first, then per warp kRing slots of
+// parent run + propagator run.
+constexpr int kRing = 8;
+constexpr int kRingHeader = kWarps * kRing * 8;   // 512 B, a multiple of 128
+static_assert(kRingHeader % 128 == 0, "ring slots must stay 128-byte aligned");
+
+template <int MODE, int V>
+__host__ __device__ constexpr int bulk_ring_bytes() {
+    return kRingHeader + kWarps * kRing *
+                     (32 * V * (int)sizeof(typename Traits<MODE>::Val) +
+                      (Traits<MODE>::kCount ? 0 : 32 * V * (int)sizeof(typename Traits<MODE>::Prop)));
+}
 
 __device__ __forceinline__ double madd(double p, double g, double acc) { return fma(p, g, acc); }
 __device__ __forceinline__ float madd(float p, float g, float acc) { return fmaf(p, g, acc); }
@@ -684,10 +772,167 @@ __device__ __forceinline__ void item_level_grouped(const WalkParams& p, int l, c
     }
 }
 
+// Wide layout with a bulk-copy ring (CHV = 32*V).  Same items, rows and per-row order
+// as the wide layout; instead of every lane loading its V values, lane 0 of a warp
+// copies the whole parent run and propagator run of edge e + kRing into a ring slot
+// in shared memory with two bulk copies (the TMA engine) completing on the slot's
+// mbarrier, while the warp consumes edge e from shared memory.  kRing edges are in
+// flight per warp without holding registers.  Every wait is bounded (mbar_wait); on
+// a timeout the item drains its outstanding copies (bounded) and returns false.
+template <int MODE, int V>
+__device__ __forceinline__ bool item_level_bulk(const WalkParams& p, int l, const TileCtx& tc, int item,
+                                                unsigned char* smem) {
+    using Tr = Traits<MODE>;
+    using Val = typename Tr::Val;
+    using Prop = typename Tr::Prop;
+    constexpr int CHV = 32 * V;
+    constexpr unsigned RUNB = 32 * V * sizeof(Val);
+    constexpr unsigned GRUNB = Tr::kCount ? 0 : 32 * V * sizeof(Prop);
+    constexpr unsigned SLOTB = RUNB + GRUNB;
+    const LevelDesc ld = p.levels[l];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rpw = p.rows_per_warp;
+    const int rows_per_item = kWarps * rpw;
+    const int nrb = (ld.width + rows_per_item - 1) / rows_per_item;
+    const int c = item / nrb;
+    const int rb = item - c * nrb;
+    const bool sink = (l == p.L - 1);
+    const int off = lane * V;
+    const Val* pc0 = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * ld.prev_width * CHV;
+    Val* child = static_cast<Val*>(p.slab[l & 1]);
+    const Prop* gc0 = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV;
+    const int r0 = rb * rows_per_item + warp * rpw;
+    if (r0 >= ld.width) return true;
+    const int nr = min(rpw, ld.width - r0);
+    if constexpr (MODE == COS_MODE_FP32_MIXED) {
+        if (sink) {
+            for (int r = r0; r < r0 + nr; ++r) {
+                const int node = ld.row_begin + r;
+                sink_row_mixed<V, CHV>(p, pc0 + off, gc0 + off, __ldg(p.row_ptr + node), __ldg(p.row_ptr + node + 1), c,
+                                       tc, off);
+            }
+            return true;
+        }
+    }
+    // lane j <= nr holds rp_j = row_ptr of row r0 + j
+    const int rp = (lane <= nr) ? __ldg(p.row_ptr + ld.row_begin + r0 + lane) : 0;
+    const int rp_next = __shfl_down_sync(0xffffffffu, rp, 1);
+    const int beg = __shfl_sync(0xffffffffu, rp, 0);
+    const int end = __shfl_sync(0xffffffffu, rp, nr);
+    const unsigned nonempty = __ballot_sync(0xffffffffu, lane < nr && rp_next > rp);
+    const unsigned empty = __ballot_sync(0xffffffffu, lane < nr && rp_next == rp);
+    Val acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+    for (unsigned m = empty; m; m &= m - 1)   // rows without in-edges hold 0
+        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(m) - 1, tc, off, acc);
+    if (beg == end) return true;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem) + warp * kRing;
+    unsigned char* ring = smem + kRingHeader + (size_t)warp * kRing * SLOTB;
+    if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < kRing; ++r) mbar_init(bars + r, 1);
+        fence_mbar_init();
+        fence_proxy_async_global();
+    }
+    __syncwarp();
+    // metadata windows [wbase, wbase+32) and [wbase+32, wbase+64)
+    int wbase = beg;
+    int2 meta_a = (beg + lane < end) ? __ldg(p.edges + beg + lane) : make_int2(0, 0);
+    int2 meta_b = (beg + 32 + lane < end) ? __ldg(p.edges + beg + 32 + lane) : make_int2(0, 0);
+    auto ends_of = [&](int w0) {   // bit q set <=> edge w0+q is the last in-edge of its row
+        const int pos = rp_next - 1 - w0;
+        return __reduce_or_sync(0xffffffffu,
+                                (lane < nr && rp_next > rp && pos >= 0 && pos < 32) ? (1u << pos) : 0u);
+    };
+    unsigned ends = ends_of(wbase);
+    auto issue = [&](int e, int slot) {   // warp-uniform call; lane 0 issues the copies
+        const int o = e - wbase;
+        const int sa = __shfl_sync(0xffffffffu, meta_a.x, o & 31), sb = __shfl_sync(0xffffffffu, meta_b.x, o & 31);
+        const int ga = __shfl_sync(0xffffffffu, meta_a.y, o & 31), gb = __shfl_sync(0xffffffffu, meta_b.y, o & 31);
+        if (lane == 0) {
+            const int src = o < 32 ? sa : sb;
+            const int gslot = o < 32 ? ga : gb;
+            unsigned char* dst = ring + (size_t)slot * SLOTB;
+#ifdef COS_DEBUG_CHECKS
+            // self-check (debug builds): record the first violation and skip the copy
+            const unsigned long long sa_ = (unsigned long long)(pc0 + (int64_t)src * CHV);
+            const unsigned long long ga_ = Tr::kCount ? 0ull : (unsigned long long)(gc0 + (int64_t)gslot * CHV);
+            int bad = 0;
+            if (o < 0 || o >= 64) bad = 1;
+            else if (src < 0 || src >= ld.prev_width) bad = 2;
+            else if (!Tr::kCount && (gslot < 0 || gslot >= p.P)) bad = 3;
+            else if ((smem_u32(dst) & 15u) || (sa_ & 15ull) || (ga_ & 15ull)) bad = 4;
+            else if (smem_u32(dst) - smem_u32(smem) + SLOTB > dynamic_smem_bytes()) bad = 5;
+            else if (smem_u32(bars + slot) & 7u) bad = 6;
+            if (bad) {   // complete the slot's phase without a copy so that every wait stays short
+                if (atomicCAS(&p.ctrl->err, 0, 100 + bad) == 0) p.ctrl->err_detail = e;
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bars + slot)) : "memory");
+                return;
+            }
+#endif
+            mbar_arrive_expect_tx(bars + slot, SLOTB);
+            bulk_copy_g2s(dst, pc0 + (int64_t)src * CHV, RUNB, bars + slot);
+            if constexpr (!Tr::kCount) bulk_copy_g2s(dst + RUNB, gc0 + (int64_t)gslot * CHV, GRUNB, bars + slot);
+        }
+    };
+    const int n = end - beg;
+#pragma unroll
+    for (int j = 0; j < kRing; ++j)
+        if (j < n) issue(beg + j, j);
+    unsigned rows_left = nonempty;
+    for (int k = 0; k < n; ++k) {
+        const int e = beg + k;
+        const int slot = k & (kRing - 1);
+        if (!mbar_wait(bars + slot, (unsigned)(k / kRing) & 1u, p)) {
+            // drain: the copies issued for edges k+1 .. min(n, k+kRing)-1 (bounded waits)
+            for (int k2 = k + 1; k2 < min(n, k + kRing); ++k2)
+                (void)mbar_wait(bars + (k2 & (kRing - 1)), (unsigned)(k2 / kRing) & 1u, p);
+            return false;   // the kernel stops at its next barrier; the memory is not reused
+        }
+        const unsigned char* src = ring + (size_t)slot * SLOTB;
+        const VecT<Val, V> pv = *reinterpret_cast<const VecT<Val, V>*>(src + off * sizeof(Val));
+        if constexpr (Tr::kCount) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += pv.v[v];
+        } else {
+            const VecT<Prop, V> gv = *reinterpret_cast<const VecT<Prop, V>*>(src + RUNB + off * sizeof(Prop));
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = madd(pv.v[v], gv.v[v], acc[v]);
+        }
+        if ((ends >> (e - wbase)) & 1u) {
+            store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(rows_left) - 1, tc, off, acc);
+            rows_left &= rows_left - 1;
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+        }
+        if (e + 1 - wbase == 32) {   // slide the metadata windows
+            wbase += 32;
+            meta_a = meta_b;
+            meta_b = (wbase + 32 + lane < end) ? __ldg(p.edges + wbase + 32 + lane) : make_int2(0, 0);
+            ends = ends_of(wbase);
+        }
+        __syncwarp();   // every lane has read the slot before it is refilled
+        if (k + kRing < n) issue(e + kRing, slot);
+    }
+    __syncwarp();
+    if (lane == 0)   // every copy has landed: hand the memory back for other uses
+#pragma unroll
+        for (int r = 0; r < kRing; ++r) mbar_inval(bars + r);
+    __syncwarp();
+#ifdef COS_DEBUG_CHECKS
+    if (*(volatile int*)&p.ctrl->err > 100) return false;
+#endif
+    return true;
+}
+
 template <int MODE, int V, int LAYOUT>
-__device__ __forceinline__ void item_level(const WalkParams& p, int l, const TileCtx& tc, int item) {
+__device__ __forceinline__ bool item_level(const WalkParams& p, int l, const TileCtx& tc, int item,
+                                           unsigned char* smem) {
+    if constexpr (LAYOUT == LAYOUT_BULK) return item_level_bulk<MODE, V>(p, l, tc, item, smem);
     if constexpr (LAYOUT == LAYOUT_WIDE) item_level_wide<MODE, V>(p, l, tc, item);
     else item_level_grouped<MODE, V>(p, l, tc, item);
+    return true;
 }
 
 // ---------------------------------------------------------------- phase: sample reduction
@@ -726,21 +971,25 @@ __device__ __forceinline__ void item_partials(const WalkParams& p, int item) {
     const int64_t b = (int64_t)item * kWarps + warp;
     if (b >= nblk) return;
     constexpr int per_lane = kReduceBlock / 32;
-    double x[per_lane];
+    constexpr int AHEAD = 8;
     const int64_t s0 = b * kReduceBlock + lane;
-#pragma unroll
-    for (int u = 0; u < per_lane; ++u) {
-        const int64_t s = s0 + (int64_t)u * 32;
-        if (s < p.S) {
-            if constexpr (MODE == COS_MODE_COUNT_I64) x[u] = (double)static_cast<const long long*>(p.R)[s];
-            else x[u] = static_cast<const double*>(p.R)[s];
-        } else {
-            x[u] = 0.0;
-        }
-    }
     double sum = 0.0, comp = 0.0;
+#pragma unroll 1
+    for (int u0 = 0; u0 < per_lane; u0 += AHEAD) {
+        double x[AHEAD];
 #pragma unroll
-    for (int u = 0; u < per_lane; ++u) neumaier_add(sum, comp, x[u]);
+        for (int u = 0; u < AHEAD; ++u) {
+            const int64_t s = s0 + (int64_t)(u0 + u) * 32;
+            if (s < p.S) {
+                if constexpr (MODE == COS_MODE_COUNT_I64) x[u] = (double)static_cast<const long long*>(p.R)[s];
+                else x[u] = static_cast<const double*>(p.R)[s];
+            } else {
+                x[u] = 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < AHEAD; ++u) neumaier_add(sum, comp, x[u]);
+    }
     warp_sum(sum, comp);
     if (lane == 0) p.partials[b] = sum + comp;
 }

@@ -29,17 +29,18 @@ __device__ __noinline__ bool grid_sync(const WalkParams& p, unsigned long long& 
     epoch += 1;
     if (threadIdx.x == 0) {
         const unsigned long long target = epoch * (unsigned long long)gridDim.x;
-        __threadfence();
-        atomicAdd(&p.ctrl->barrier, 1ull);
+        // release: the CTA's writes (ordered before thread 0 by the block barrier) become
+        // visible before the arrival is counted; the acquire loads below pair with it
+        asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&p.ctrl->barrier) : "memory");
         int ok = 1;
         const unsigned long long t0 = global_timer_ns();
         for (unsigned long long spin = 0;; ++spin) {
             if (ld_acquire_gpu(&p.ctrl->barrier) >= target) break;
-            if (*(volatile int*)&p.ctrl->err != 0) {
-                ok = 0;
-                break;
-            }
-            if ((spin & 31) == 31) {
+            if ((spin & 15) == 15) {
+                if (*(volatile int*)&p.ctrl->err != 0) {
+                    ok = 0;
+                    break;
+                }
                 const long long waited = (long long)(global_timer_ns() - t0);
                 if (waited > p.timeout_ns || spin > (1ull << 32)) {
                     if (atomicCAS(&p.ctrl->err, 0, KERR_BARRIER_TIMEOUT) == 0) p.ctrl->err_detail = phase;
@@ -47,9 +48,8 @@ __device__ __noinline__ bool grid_sync(const WalkParams& p, unsigned long long& 
                     break;
                 }
             }
-            __nanosleep(40);
+            if (spin >= 32) __nanosleep(32);
         }
-        __threadfence();
         s_ok = ok;
         if (ok && p.trace && blockIdx.x == 0 && (long long)epoch < p.trace_cap) {
             p.trace[2 * epoch] = global_timer_ns();
@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<MODE, V>()) walk_kernel(c
         if (!grid_sync(p, epoch, 2)) return;
         for (int l = 1; l < p.L; ++l) {
             const int n = level_items(p, p.levels[l], tc);
-            for (int it = blockIdx.x; it < n; it += gridDim.x) item_level<MODE, V, LAYOUT>(p, l, tc, it);
+            for (int it = blockIdx.x; it < n; it += gridDim.x)
+                if (!item_level<MODE, V, LAYOUT>(p, l, tc, it, reinterpret_cast<unsigned char*>(smem))) break;
             if (!grid_sync(p, epoch, 3 + l)) return;
         }
     }
@@ -177,6 +178,7 @@ const void* select_kernel_layout(int mode, int vec) {
 }
 
 const void* select_kernel(int mode, int vec, int layout) {
+    if (layout == 3) return select_kernel_layout<LAYOUT_BULK>(mode, vec);
     if (layout == 2) return select_kernel_layout<LAYOUT_GROUPED>(mode, vec);
     if (layout == 1) return select_kernel_layout<LAYOUT_WIDE>(mode, vec);
     return nullptr;
@@ -184,8 +186,18 @@ const void* select_kernel(int mode, int vec, int layout) {
 
 }  // namespace
 
+template <int MODE>
+int ring_bytes(int vec) {
+    return vec == 1 ? bulk_ring_bytes<MODE, 1>() : vec == 2 ? bulk_ring_bytes<MODE, 2>() : bulk_ring_bytes<MODE, 4>();
+}
+
 int walk_smem_bytes(int mode, int vec, int layout, int D) {
-    return mode == COS_MODE_COUNT_I64 ? 0 : prop_smem_bytes(D, layout == 2 ? 32 : 32 * vec);
+    const int props = mode == COS_MODE_COUNT_I64 ? 0 : prop_smem_bytes(D, layout == 2 ? 32 : 32 * vec);
+    if (layout != 3) return props;
+    const int ring = mode == COS_MODE_FP64 ? ring_bytes<COS_MODE_FP64>(vec)
+                     : mode == COS_MODE_FP32_MIXED ? ring_bytes<COS_MODE_FP32_MIXED>(vec)
+                                                   : ring_bytes<COS_MODE_COUNT_I64>(vec);
+    return props > ring ? props : ring;
 }
 
 // Opt every kernel instance into its dynamic shared-memory size (once per process).

@@ -50,6 +50,8 @@ def mix():
     (1, {}), (0, {}), (2, {}),
     (1, {"samples_per_lane": 4, "layout": 2, "rows_per_warp": 8}),
     (0, {"samples_per_lane": 1, "rows_per_warp": 4, "tile_samples": 2048}),
+    (1, {"samples_per_lane": 4, "layout": 3, "rows_per_warp": 8}),
+    (2, {"samples_per_lane": 2, "layout": 3}),
 ])
 def test_batch_matches_single_graph_bitwise(cg, mix, mode, tuning):
     graphs = _setup(cg, mix)

@@ -106,7 +106,8 @@ def test_medium_multi_tile_ragged_fp64(cg):
     w = medium(num_samples=5000)
     R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
     for tuning in ({"tile_samples": 1024}, {"tile_samples": 640, "samples_per_lane": 1},
-                   {"tile_samples": 1024, "layout": 2, "samples_per_lane": 2}):
+                   {"tile_samples": 1024, "layout": 2, "samples_per_lane": 2},
+                   {"tile_samples": 768, "layout": 3, "samples_per_lane": 2}):
         Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 0, tuning)
         check_fp(Rg, mg, R, A, 0)
 
@@ -208,6 +209,12 @@ def test_wide_fanin_duplicates_dead_and_orphan_nodes(cg):
     cnt, _ = oracle.count_paths(g2)
     Rg, _ = run_gpu(cg, g2, eps, 10.0, t, 2)
     assert np.all(Rg == cnt)
+    for mode in (0, 1, 2):                          # the bulk-copy ring on the same graph
+        Rg, mg = run_gpu(cg, g2, eps, 10.0, t, mode, {"layout": 3})
+        if mode == 2:
+            assert np.all(Rg == cnt)
+        else:
+            check_fp(Rg, mg, R, A, mode)
 
 
 def test_count_overflow_reports_and_wraps(cg):
@@ -234,7 +241,9 @@ def test_results_independent_of_launch_shape(cg):
     for tuning in ({}, {"samples_per_lane": 1}, {"samples_per_lane": 4, "tile_samples": 512},
                    {"samples_per_lane": 2, "rows_per_warp": 4, "blocks_per_sm": 1},
                    {"samples_per_lane": 4, "layout": 2, "rows_per_warp": 28},
-                   {"samples_per_lane": 2, "layout": 2, "rows_per_warp": 5, "tile_samples": 1000}):
+                   {"samples_per_lane": 2, "layout": 2, "rows_per_warp": 5, "tile_samples": 1000},
+                   {"samples_per_lane": 4, "layout": 3, "rows_per_warp": 8},
+                   {"samples_per_lane": 1, "layout": 3, "rows_per_warp": 3, "tile_samples": 700}):
         for mode in (0, 1):
             Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode, tuning)
             if ref is None:
