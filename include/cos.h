@@ -185,6 +185,19 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *                     3 = wide with a bulk-copy ring (one lane stages whole parent
  *                     and propagator runs in shared memory with cp.async.bulk on
  *                     mbarriers, 8 edges in flight per warp)
+ *   schedule          1 = level-synchronous: one cooperative kernel, every level of a
+ *                     tile ends at a grid-wide barrier; 2 = windowed (Sec. II.C,
+ *                     asynchronous evaluation of levels): the chunks of each tile are
+ *                     cut into windows of window_chunks chunks, every window is its
+ *                     own chain (propagators, levels 1..L-1, continuing into the same
+ *                     window of the next tile), the chains are issued in wavefront
+ *                     order to a persistent work-queue kernel and each work item waits
+ *                     only for the previous phase of its own window, so about L
+ *                     windows are in flight and their node values and propagators
+ *                     can stay in L2.  Results are bitwise the same either way.
+ *                     Batched launches use windows when window_chunks > 0.
+ *   window_chunks     chunks (of 32*samples_per_lane samples, 32 in the grouped
+ *                     layout) per window in the windowed schedule
  */
 typedef struct cos_tuning {
     int32_t samples_per_lane;
@@ -193,6 +206,8 @@ typedef struct cos_tuning {
     int32_t blocks_per_sm;
     int32_t timeout_ms;
     int32_t layout;
+    int32_t schedule;
+    int32_t window_chunks;
 } cos_tuning;
 
 int cos_set_tuning(cos_graph_t g, const cos_tuning* tuning);

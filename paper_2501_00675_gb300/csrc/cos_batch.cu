@@ -4,15 +4,20 @@
 // every graph's work is cut into the same CTA-sized items as the single-graph
 // kernel and all graphs share one persistent grid.
 //
-// Plan: each graph contributes a chain of phase tasks -- coefficients, then per
-// tile of samples (exponential factors, propagator table, levels 1..L-1), then
-// partial sums and the final mean.  The chains are interleaved round-robin into
-// one task list; CTAs draw tickets from a global counter, a ticket names one item
-// of one task, and an item waits (bounded) until the previous task of its own
-// chain has completed all its items.  Tickets are handed out in list order and a
-// task only ever waits on an earlier task, so the lowest pending item can always
-// run: no co-residency is required.  The launch (counter reset + kernel) is
-// captured once into a CUDA graph and replayed.
+// Plan: each graph contributes its coefficients task, then per window of sample
+// chunks a chain of phase tasks -- per tile of samples: propagators, levels
+// 1..L-1 -- then partial sums (waiting for every window) and the final mean.
+// Without windows a tile is one window, so a graph is one chain.  With windows
+// (Sec. II.C: levels evaluated asynchronously) the window chains of a graph are
+// laid out in wavefront order (step d holds phase d - w of window w), so about L
+// windows are in flight and their node values and propagators are re-read while
+// still in L2.  The graphs' lists are interleaved round-robin into one task list;
+// CTAs draw tickets from a global counter, a ticket names one item of one task,
+// and an item waits (bounded) until the tasks it depends on have completed all
+// their items.  Tickets are handed out in list order and a task only ever waits
+// on earlier tasks, so the lowest pending item can always run: no co-residency is
+// required.  The launch (counter reset + kernel) is captured once into a CUDA
+// graph and replayed.
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -27,14 +32,16 @@ namespace {
 enum TaskKind : int32_t { TK_COEF = 0, TK_PROP = 1, TK_LEVEL = 3, TK_PARTIALS = 4, TK_FINAL = 5 };
 
 struct Task {
-    int32_t graph;   // index into the parameter array
+    int32_t graph;      // index into the parameter array
     int32_t kind;
     int32_t level;
-    int32_t dep;     // task that must be complete first (-1: none)
-    int64_t tix;     // tile index
-    int64_t first;   // first ticket of this task
+    int32_t dep;        // task that must be complete first (-1: none)
+    int64_t tix;        // tile index
+    int64_t first;      // first ticket of this task
     int32_t items;
-    int32_t pad;
+    int32_t c0;         // first chunk of the task's window within the tile
+    int32_t join_off;   // further tasks that must be complete: joins[join_off .. +join_cnt)
+    int32_t join_cnt;
 };
 
 struct BatchCtrl {
@@ -45,6 +52,7 @@ struct BatchCtrl {
 
 struct BatchArgs {
     const Task* tasks;
+    const int32_t* joins;
     int32_t ntasks;
     int32_t pad;
     int64_t total;
@@ -76,11 +84,14 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V>()) batch_k
         const int item = (int)(t - tk.first);
         if (threadIdx.x == 0) {
             int ok = 1;
-            if (tk.dep >= 0) {
-                const unsigned need = (unsigned)a.tasks[tk.dep].items;
-                const unsigned long long t0 = global_timer_ns();
-                for (unsigned long long spin = 0;; ++spin) {
-                    if (ld_acquire_gpu_u32(a.done + tk.dep) >= need) break;
+            const unsigned long long t0 = global_timer_ns();
+            unsigned long long spin = 0;
+            for (int q = -1; ok && q < tk.join_cnt; ++q) {   // the chain predecessor, then the joins
+                const int dep = q < 0 ? tk.dep : a.joins[tk.join_off + q];
+                if (dep < 0) continue;
+                const unsigned need = (unsigned)a.tasks[dep].items;
+                for (;; ++spin) {
+                    if (ld_acquire_gpu_u32(a.done + dep) >= need) break;
                     if (*(volatile int*)&a.ctrl->err != 0) { ok = 0; break; }
                     if ((spin & 31) == 31 &&
                         ((long long)(global_timer_ns() - t0) > a.timeout_ns || spin > (1ull << 32))) {
@@ -96,12 +107,13 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V>()) batch_k
         __syncthreads();
         if (!s_ok) return;
         const WalkParams& p = a.params[tk.graph];
+        TileCtx tc = tile_ctx<CHV>(p, tk.tix);
+        tc.c0 = tk.c0;
         switch (tk.kind) {
             case TK_COEF: item_coef(p); break;
-            case TK_PROP: item_props<MODE, CHV>(p, tile_ctx<CHV>(p, tk.tix), item, smem); break;
+            case TK_PROP: item_props<MODE, CHV>(p, tc, item, smem); break;
             case TK_LEVEL:
-                if (!item_level<MODE, V, LAYOUT>(p, tk.level, tile_ctx<CHV>(p, tk.tix), item,
-                                                 reinterpret_cast<unsigned char*>(smem)) &&
+                if (!item_level<MODE, V, LAYOUT>(p, tk.level, tc, item, reinterpret_cast<unsigned char*>(smem)) &&
                     (threadIdx.x & 31) == 0) {   // a bounded wait gave up: report it for the whole launch
                     const int code = *(volatile int*)&p.ctrl->err;
                     if (atomicCAS(&a.ctrl->err, 0, code ? code : KERR_BARRIER_TIMEOUT) == 0)
@@ -158,23 +170,26 @@ struct cos_batch {
     int32_t mode = 0;
     std::vector<cos_graph_t> graphs;
     std::vector<void*> outs;
-    cos_tuning tuning{0, 0, 0, 0, 0, 0};     // batch-level overrides (samples_per_lane, rows_per_warp, ...)
-    cos_tuning resolved{0, 0, 0, 0, 0, 0};
+    cos_tuning tuning{};     // batch-level overrides (samples_per_lane, rows_per_warp, ...)
+    cos_tuning resolved{};
     // host plan and its pinned staging copies
     std::vector<Task> tasks;
     std::vector<WalkParams> params;
     std::vector<int> counts_overflow;
+    std::vector<int32_t> joins;
     Task* h_tasks = nullptr;
+    int32_t* h_joins = nullptr;
     WalkParams* h_params = nullptr;
     double* h_means = nullptr;
     BatchCtrl* h_ctrl = nullptr;
     // device buffers (grow only)
     Task* d_tasks = nullptr;
+    int32_t* d_joins = nullptr;
     WalkParams* d_params = nullptr;
     unsigned* d_done = nullptr;
     double* d_means = nullptr;
     BatchCtrl* d_ctrl = nullptr;
-    size_t cap_tasks = 0, cap_graphs = 0;
+    size_t cap_tasks = 0, cap_graphs = 0, cap_joins = 0;
     int32_t ntasks = 0;
     int64_t total = 0;
     int grid = 0;
@@ -199,28 +214,43 @@ void drop_capture(cos_batch* b) {
 void free_buffers(cos_batch* b) {
     drop_capture(b);
     cudaFree(b->d_tasks);
+    cudaFree(b->d_joins);
     cudaFree(b->d_params);
     cudaFree(b->d_done);
     cudaFree(b->d_means);
     cudaFree(b->d_ctrl);
+    cudaFreeHost(b->h_joins);
     cudaFreeHost(b->h_tasks);
     cudaFreeHost(b->h_params);
     cudaFreeHost(b->h_means);
     cudaFreeHost(b->h_ctrl);
     b->d_tasks = nullptr;
+    b->d_joins = nullptr;
     b->d_params = nullptr;
     b->d_done = nullptr;
     b->d_means = nullptr;
     b->d_ctrl = nullptr;
     b->h_tasks = nullptr;
+    b->h_joins = nullptr;
     b->h_params = nullptr;
     b->h_means = nullptr;
     b->h_ctrl = nullptr;
-    b->cap_tasks = b->cap_graphs = 0;
+    b->cap_tasks = b->cap_graphs = b->cap_joins = 0;
 }
 
-int ensure_capacity(cos_batch* b, size_t ntasks, size_t ngraphs) {
+int ensure_capacity(cos_batch* b, size_t ntasks, size_t ngraphs, size_t njoins) {
     cudaError_t e = cudaSuccess;
+    if (njoins > b->cap_joins) {
+        cudaFree(b->d_joins);
+        cudaFreeHost(b->h_joins);
+        b->d_joins = nullptr;
+        b->h_joins = nullptr;
+        const size_t cap = std::max<size_t>(njoins, 2 * b->cap_joins);
+        if ((e = cudaMalloc(&b->d_joins, sizeof(int32_t) * cap)) != cudaSuccess ||
+            (e = cudaMallocHost(&b->h_joins, sizeof(int32_t) * cap)) != cudaSuccess)
+            return set_error(COS_ERR_OOM, "batch joins: %s", cudaGetErrorString(e));
+        b->cap_joins = cap;
+    }
     if (!b->d_ctrl) {
         if ((e = cudaMalloc(&b->d_ctrl, sizeof(BatchCtrl))) != cudaSuccess ||
             (e = cudaMallocHost(&b->h_ctrl, sizeof(BatchCtrl))) != cudaSuccess)
@@ -271,7 +301,9 @@ int plan(cos_batch* b) {
     cos_tuning first = force;
     b->params.assign((size_t)b->n, WalkParams{});
     b->counts_overflow.assign((size_t)b->n, 0);
-    std::vector<std::vector<Task>> chains((size_t)b->n);
+    // per graph: its tasks in issue order; dep and joins as indices into the same list
+    std::vector<std::vector<Task>> lists((size_t)b->n);
+    std::vector<std::vector<std::vector<int32_t>>> local_joins((size_t)b->n);
     for (int32_t g = 0; g < b->n; ++g) {
         cos_tuning tn;
         int rc = prepare_walk(b->graphs[(size_t)g], mode, &force, b->outs[(size_t)g], &b->params[(size_t)g], &tn);
@@ -280,9 +312,10 @@ int plan(cos_batch* b) {
         GraphView gv;
         graph_view(b->graphs[(size_t)g], &gv);
         b->counts_overflow[(size_t)g] = gv.count_overflow;
-        WalkParams& p = b->params[(size_t)g];
-        std::vector<Task>& ch = chains[(size_t)g];
-        auto push = [&](int32_t kind, int32_t level, int64_t tix, int64_t items) {
+        const WalkParams& p = b->params[(size_t)g];
+        std::vector<Task>& out = lists[(size_t)g];
+        std::vector<std::vector<int32_t>>& joins = local_joins[(size_t)g];
+        auto make = [&](int32_t kind, int32_t level, int64_t tix, int64_t items, int32_t c0) {
             Task t;
             memset(&t, 0, sizeof(t));
             t.graph = g;
@@ -290,35 +323,79 @@ int plan(cos_batch* b) {
             t.level = level;
             t.tix = tix;
             t.items = (int32_t)items;
+            t.c0 = c0;
             t.dep = -1;
-            ch.push_back(t);
+            return t;
         };
-        if (mode != COS_MODE_COUNT_I64) push(TK_COEF, 0, 0, 1);
-        const int64_t ntiles = (p.S + p.tile - 1) / p.tile;
+        auto emit = [&](const Task& t, std::vector<int32_t> js) {
+            out.push_back(t);
+            joins.push_back(std::move(js));
+            return (int32_t)out.size() - 1;
+        };
+        int32_t coef = -1;
+        if (mode != COS_MODE_COUNT_I64) coef = emit(make(TK_COEF, 0, 0, 1, 0), {});
+        // window chains: chunks [w*wch, (w+1)*wch) of every tile
+        const int64_t ntiles = p.S > 0 ? (p.S + p.tile - 1) / p.tile : 0;
+        const int nch_max = p.S > 0 ? div_up(std::min<int64_t>(p.tile, p.S), chv) : 0;
+        const int wch = force.window_chunks > 0 ? std::min(force.window_chunks, std::max(nch_max, 1)) : std::max(nch_max, 1);
+        const int nw = nch_max > 0 ? div_up(nch_max, wch) : 0;
+        const int rows_per_item = kWarps * p.rows_per_warp;
+        std::vector<std::vector<Task>> chains((size_t)nw);
         for (int64_t tix = 0; tix < ntiles; ++tix) {
-            const int64_t base = tix * p.tile;
-            const int64_t nsamp = std::min(p.tile, p.S - base);
+            const int64_t nsamp = std::min(p.tile, p.S - tix * p.tile);
             const int nch = div_up(nsamp, chv);
-            push(TK_PROP, 0, tix, mode == COS_MODE_COUNT_I64 ? nch : (int64_t)nch * p.K);
-            for (int l = 1; l < p.L; ++l) {
-                const int rows_per_item = kWarps * p.rows_per_warp;
-                push(TK_LEVEL, l, tix, (int64_t)nch * div_up(gv.widths_host[l], rows_per_item));
+            for (int w = 0; w < nw; ++w) {
+                const int c0 = w * wch;
+                if (c0 >= nch) break;
+                const int n_w = std::min(wch, nch - c0);
+                chains[(size_t)w].push_back(
+                    make(TK_PROP, 0, tix, mode == COS_MODE_COUNT_I64 ? n_w : (int64_t)n_w * p.K, c0));
+                for (int l = 1; l < p.L; ++l)
+                    chains[(size_t)w].push_back(
+                        make(TK_LEVEL, l, tix, (int64_t)n_w * div_up(gv.widths_host[l], rows_per_item), c0));
             }
         }
-        push(TK_PARTIALS, 0, 0, div_up(div_up(p.S, kReduceBlock), kWarps));
-        push(TK_FINAL, 0, 0, 1);
+        // wavefront: step d issues phase d - w of window w, oldest window first
+        std::vector<int32_t> last((size_t)nw, coef);
+        size_t maxlen = 0;
+        for (auto& ch : chains) maxlen = std::max(maxlen, ch.size());
+        for (size_t d = 0; d + 1 < maxlen + (size_t)nw; ++d)
+            for (int w = 0; w < nw; ++w) {
+                if ((size_t)w > d) break;
+                const size_t ph = d - (size_t)w;
+                if (ph >= chains[(size_t)w].size()) continue;
+                Task t = chains[(size_t)w][ph];
+                t.dep = last[(size_t)w];
+                last[(size_t)w] = emit(t, {});
+            }
+        // the sample reduction waits for every window; the final mean for the reduction
+        Task part = make(TK_PARTIALS, 0, 0, div_up(div_up(p.S, kReduceBlock), kWarps), 0);
+        part.dep = coef;
+        std::vector<int32_t> js;
+        for (int w = 0; w < nw; ++w)
+            if (last[(size_t)w] != coef) js.push_back(last[(size_t)w]);
+        const int32_t ip = emit(part, std::move(js));
+        Task fin = make(TK_FINAL, 0, 0, 1, 0);
+        fin.dep = ip;
+        emit(fin, {});
     }
-    // Round-robin interleave; each task depends on its predecessor in its chain.
+    // Round-robin interleave of the graphs' lists (each list keeps its order).
     b->tasks.clear();
-    std::vector<int32_t> last((size_t)b->n, -1);
+    b->joins.clear();
+    std::vector<std::vector<int32_t>> gidx((size_t)b->n);
     size_t longest = 0;
-    for (auto& ch : chains) longest = std::max(longest, ch.size());
+    for (auto& l : lists) longest = std::max(longest, l.size());
     for (size_t r = 0; r < longest; ++r)
         for (int32_t g = 0; g < b->n; ++g) {
-            if (r >= chains[(size_t)g].size()) continue;
-            Task t = chains[(size_t)g][r];
-            t.dep = last[(size_t)g];
-            last[(size_t)g] = (int32_t)b->tasks.size();
+            if (r >= lists[(size_t)g].size()) continue;
+            Task t = lists[(size_t)g][r];
+            std::vector<int32_t>& map = gidx[(size_t)g];
+            if (t.dep >= 0) t.dep = map[(size_t)t.dep];
+            const std::vector<int32_t>& js = local_joins[(size_t)g][r];
+            t.join_off = (int32_t)b->joins.size();
+            t.join_cnt = (int32_t)js.size();
+            for (int32_t q : js) b->joins.push_back(map[(size_t)q]);
+            map.push_back((int32_t)b->tasks.size());
             b->tasks.push_back(t);
         }
     int64_t first_ticket = 0;
@@ -331,6 +408,8 @@ int plan(cos_batch* b) {
     b->resolved = first;
     b->resolved.samples_per_lane = force.samples_per_lane;
     b->resolved.layout = force.layout;
+    b->resolved.schedule = force.window_chunks > 0 ? 2 : 1;
+    b->resolved.window_chunks = force.window_chunks;
     const void* k = select_batch_kernel(mode, b->resolved.samples_per_lane, b->resolved.layout);
     if (!k) return set_error(COS_ERR_INVALID, "no batch kernel for samples_per_lane %d", b->resolved.samples_per_lane);
     int dmax = 1;
@@ -346,7 +425,8 @@ int plan(cos_batch* b) {
     if (b->tuning.blocks_per_sm > 0) bps = std::min(bps, b->tuning.blocks_per_sm);
     b->resolved.blocks_per_sm = bps;
     b->grid = sms * bps;
-    int rc = ensure_capacity(b, std::max<size_t>(b->tasks.size(), 1), std::max<int32_t>(b->n, 1));
+    int rc = ensure_capacity(b, std::max<size_t>(b->tasks.size(), 1), std::max<int32_t>(b->n, 1),
+                             std::max<size_t>(b->joins.size(), 1));
     if (rc != COS_OK) return rc;
     for (int32_t g = 0; g < b->n; ++g) b->params[(size_t)g].mean_out = b->d_means + g;
     drop_capture(b);
@@ -364,6 +444,7 @@ int enqueue_run(cos_batch* b, cudaStream_t st) {
         return set_error(COS_ERR_CUDA, "reset batch counters: %s", cudaGetErrorString(e));
     BatchArgs a;
     a.tasks = b->d_tasks;
+    a.joins = b->d_joins;
     a.ntasks = b->ntasks;
     a.pad = 0;
     a.total = b->total;
@@ -386,6 +467,10 @@ int upload(cos_batch* b, cudaStream_t st) {
         memcpy(b->h_tasks, b->tasks.data(), sizeof(Task) * b->tasks.size());
         e = cudaMemcpyAsync(b->d_tasks, b->h_tasks, sizeof(Task) * b->tasks.size(), cudaMemcpyHostToDevice, st);
     }
+    if (e == cudaSuccess && !b->joins.empty()) {
+        memcpy(b->h_joins, b->joins.data(), sizeof(int32_t) * b->joins.size());
+        e = cudaMemcpyAsync(b->d_joins, b->h_joins, sizeof(int32_t) * b->joins.size(), cudaMemcpyHostToDevice, st);
+    }
     if (e == cudaSuccess && b->n) {
         memcpy(b->h_params, b->params.data(), sizeof(WalkParams) * b->n);
         e = cudaMemcpyAsync(b->d_params, b->h_params, sizeof(WalkParams) * b->n, cudaMemcpyHostToDevice, st);
@@ -407,6 +492,24 @@ struct DevGuard {
 };
 
 }  // namespace
+
+int cosgpu::launch_windowed(cos_graph_t g, cos_batch_t* cache, int mode, void* per_sample_out, const cos_tuning& tn,
+                                   cudaStream_t st) {
+    cos_batch* b = *cache;
+    if (!b) {
+        b = new (std::nothrow) cos_batch();
+        if (!b) return set_error(COS_ERR_OOM, "host allocation failed");
+        *cache = b;
+    }
+    b->mode = mode;
+    int rc = cos_batch_reset(b, 1, &g, &per_sample_out);
+    if (rc != COS_OK) return rc;
+    b->tuning = tn;
+    rc = plan(b);
+    if (rc == COS_OK) rc = upload(b, st);
+    if (rc == COS_OK) rc = enqueue_run(b, st);
+    return rc;
+}
 
 extern "C" {
 
@@ -456,6 +559,7 @@ int cos_batch_set_tuning(cos_batch_t b, const cos_tuning* t) {
         return set_error(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
     if (t->rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
     if (t->layout < 0 || t->layout > 3) return set_error(COS_ERR_INVALID, "layout must be 0, 1, 2 or 3");
+    if (t->window_chunks < 0) return set_error(COS_ERR_INVALID, "window_chunks must be >= 0");
     b->tuning = *t;
     b->planned = false;
     return COS_OK;

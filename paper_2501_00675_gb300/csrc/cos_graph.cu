@@ -135,11 +135,13 @@ struct cos_graph {
     int64_t partial_cap = 0;
     void* d_R = nullptr;            // internal per-sample output when the caller passes none
     int64_t R_cap = 0;
-    cos_tuning tuning{0, 0, 0, 0, 0, 0};
+    cos_tuning tuning{};
     int last_status_pending = 0;    // 1 while an evaluate has not been collected
     unsigned long long* d_trace = nullptr;   // per-barrier timestamps of the last evaluate
     int32_t trace_cap = 0;
     int last_mode = 0;
+    cos_batch_t wave = nullptr;     // one-graph batch of the windowed schedule (created on first use)
+    int last_wave = 0;              // the last evaluate ran the windowed schedule
 };
 
 namespace {
@@ -409,6 +411,8 @@ int cos_destroy(cos_graph_t g) {
     if (!g) return COS_OK;
     {
         DeviceGuard dg(g->device);
+        if (g->wave) cos_batch_destroy(g->wave);
+        g->wave = nullptr;
         if (g->arrays) {
             g->arrays.reset();   // frees the structure arrays with the last handle sharing them
         } else {
@@ -450,9 +454,15 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
     if (t->blocks_per_sm > 32) return fail(COS_ERR_INVALID, "blocks_per_sm must be <= 32");
     if (t->layout < 0 || t->layout > 3)
         return fail(COS_ERR_INVALID, "layout must be 0 (auto), 1 (wide), 2 (grouped) or 3 (wide, bulk-copy ring)");
+    if (t->schedule < 0 || t->schedule > 2)
+        return fail(COS_ERR_INVALID, "schedule must be 0 (auto), 1 (level-synchronous) or 2 (windowed)");
+    if (t->window_chunks < 0) return fail(COS_ERR_INVALID, "window_chunks must be >= 0");
     g->tuning = *t;
     return COS_OK;
 }
+
+// Schedule when the caller leaves it automatic: 1 level-synchronous, 2 windowed.
+static const int kDefaultSchedule = 1;
 
 static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* tile_out) {
     cos_tuning t = g->tuning;
@@ -486,6 +496,16 @@ static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* til
     }
     tile = std::min(tile, need);
     t.tile_samples = (int32_t)tile;
+    if (t.schedule <= 0) t.schedule = kDefaultSchedule;
+    if (t.window_chunks <= 0) {
+        // about L windows are in flight: size them so that their node values (two
+        // levels) and propagators take about half of L2
+        const size_t val = (mode == COS_MODE_FP32_MIXED) ? 4 : 8;
+        const size_t gt = (mode == COS_MODE_COUNT_I64) ? 0 : val;
+        const size_t per_chunk = (2 * val * (size_t)g->Wmax + gt * (size_t)g->P) * (size_t)ch;
+        const size_t l2 = (size_t)64 << 20;
+        t.window_chunks = (int32_t)std::max<size_t>(1, l2 / (std::max<size_t>(g->L, 1) * per_chunk));
+    }
     *out = t;
     *tile_out = tile;
     return COS_OK;
@@ -619,6 +639,14 @@ int cos_copy_times(cos_graph_t g, double* dst, void* stream) {
 }
 
 static int collect(cos_graph_t g, double* mean_out, cudaStream_t st) {
+    if (g->last_wave && g->wave) {   // windowed schedule: errors are in the batch's control block
+        double m = 0.0;
+        const int rc = cos_batch_results(g->wave, &m, st);
+        g->last_status_pending = 0;
+        if (rc != COS_OK && rc != COS_ERR_OVERFLOW) return rc;
+        if (mean_out) *mean_out = m;
+        return rc;
+    }
     Ctrl c;
     COS_CUDA(cudaMemcpyAsync(&c, g->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "read result");
     COS_CUDA(cudaStreamSynchronize(st), "synchronize");
@@ -646,13 +674,20 @@ int cos_evaluate(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean
         p.trace_cap = g->trace_cap;
         COS_CUDA(cudaMemsetAsync(g->d_trace, 0, sizeof(unsigned long long) * 2 * g->trace_cap, st), "reset trace");
     }
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    const int grid = sms * tn.blocks_per_sm;
     COS_CUDA(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), st), "reset control block");
-    char msg[256] = {0};
-    rc = launch_walk(mode, tn.samples_per_lane, tn.layout, p, grid, st, msg, sizeof(msg));
-    if (rc != COS_OK) return fail(rc, "walker launch failed: %s", msg);
+    if (tn.schedule == 2) {
+        rc = launch_windowed(g, &g->wave, mode, per_sample_out, tn, st);
+        if (rc != COS_OK) return rc;
+        g->last_wave = 1;
+    } else {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        const int grid = sms * tn.blocks_per_sm;
+        char msg[256] = {0};
+        rc = launch_walk(mode, tn.samples_per_lane, tn.layout, p, grid, st, msg, sizeof(msg));
+        if (rc != COS_OK) return fail(rc, "walker launch failed: %s", msg);
+        g->last_wave = 0;
+    }
     g->last_mode = mode;
     g->last_status_pending = 1;
     if (mean_out) return collect(g, mean_out, st);
@@ -779,6 +814,7 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
     p.ctrl = g->d_ctrl;
     p.tile = tile;
     p.rows_per_warp = tn.rows_per_warp;
+    p.wmax = (int32_t)g->Wmax;
     p.timeout_ns = (long long)tn.timeout_ms * 1000000LL;
     if (tn_out) *tn_out = tn;
     return COS_OK;

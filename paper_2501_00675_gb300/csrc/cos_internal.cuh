@@ -64,7 +64,7 @@ struct WalkParams {
     long long timeout_ns;
     unsigned long long* trace;   // optional: [2*trace_cap] (globaltimer ns, phase id) per barrier
     int32_t trace_cap;
-    int32_t pad2;
+    int32_t wmax;                // widest level: node-value slabs are [chunk][wmax rows][chunk samples]
     double* mean_out;            // optional second destination of the mean (batched launches)
 };
 
@@ -95,6 +95,11 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
                  cos_tuning* tn_out);
 // Records a message for cos_last_error() and returns code.
 int set_error(int code, const char* fmt, ...);
+// Windowed schedule of one graph (cos_batch.cu): plan the graph alone as a batch of
+// one with the resolved tuning `tn` (window_chunks > 0), upload it and launch the
+// work-queue kernel on `st`.  *cache holds the batch object between calls.
+int launch_windowed(cos_graph_t g, cos_batch_t* cache, int mode, void* per_sample_out, const cos_tuning& tn,
+                    cudaStream_t st);
 
 // Host launcher implemented in cos_walk.cu.  Returns COS_OK or COS_ERR_CUDA and
 // fills msg on failure.

@@ -5,7 +5,10 @@
 //
 // Layout (node x sample, App. A "Cache and locality"): the samples of a tile are
 // split into chunks of CHV consecutive samples.  Node values of one level are
-// stored [chunk][row][CHV], the propagator table [chunk][slot][CHV], exponential
+// stored [chunk][row][CHV] with a chunk stride of W_max rows whatever the level's
+// width, so that a chunk occupies the same region at every level of one slab parity
+// (windows of chunks at different levels never overlap), the propagator table
+// [chunk][slot][CHV], exponential
 // factors [K][D][tile].  Two level-walk layouts share this storage scheme:
 //   wide    (CHV = 32*V): a warp owns one row at a time, lane q holds samples
 //           [q*V, q*V+V) of the chunk; one warp instruction reads one contiguous run.
@@ -260,6 +263,7 @@ struct TileCtx {
     int64_t base;
     int64_t tile_n;
     int nch;
+    int c0;   // first chunk of the work item range (a window of chunks; 0 for a whole tile)
 };
 
 template <int CHV>
@@ -269,6 +273,7 @@ __device__ __forceinline__ TileCtx tile_ctx(const WalkParams& p, int64_t tix) {
     const int64_t n = min(p.tile, p.S - tc.base);
     tc.tile_n = (n + CHV - 1) / CHV * CHV;
     tc.nch = (int)(tc.tile_n / CHV);
+    tc.c0 = 0;
     return tc;
 }
 
@@ -424,11 +429,12 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
     using Prop = typename Tr::Prop;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nk = Tr::kCount ? 1 : p.K;
-    const int c = item / nk;
-    const int k = item - c * nk;
+    const int cl = item / nk;   // chunk within the item range
+    const int c = tc.c0 + cl;
+    const int k = item - cl * nk;
     if (warp == 0 && k == 0)
         for (int v = lane; v < CHV; v += 32)
-            static_cast<typename Tr::Val*>(p.slab[0])[(int64_t)c * CHV + v] = (typename Tr::Val)1;
+            static_cast<typename Tr::Val*>(p.slab[0])[(int64_t)c * p.wmax * CHV + v] = (typename Tr::Val)1;
     if constexpr (!Tr::kCount) {
         const int D = p.D;
         const double eps = p.eps[k], cpos = p.coef[k], cneg = p.coef[p.K + k];
@@ -525,7 +531,7 @@ __device__ __forceinline__ int level_items(const WalkParams& p, const LevelDesc&
 // `off` = position of this lane's first sample inside the chunk.
 template <int MODE, int V, int CHV>
 __device__ __forceinline__ void store_row(const WalkParams& p, bool sink, typename Traits<MODE>::Val* child, int c,
-                                          int width, int r, const TileCtx& tc, int off,
+                                          int r, const TileCtx& tc, int off,
                                           const typename Traits<MODE>::Val (&acc)[V]) {
     using Tr = Traits<MODE>;
     using Val = typename Tr::Val;
@@ -541,7 +547,7 @@ __device__ __forceinline__ void store_row(const WalkParams& p, bool sink, typena
         VecT<Val, V> out;
 #pragma unroll
         for (int v = 0; v < V; ++v) out.v[v] = acc[v];
-        store_cs<Val, V>(child + ((int64_t)c * width + r) * CHV + off, out);
+        store_cs<Val, V>(child + ((int64_t)c * p.wmax + r) * CHV + off, out);
     }
 }
 
@@ -587,11 +593,12 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
     const int rpw = p.rows_per_warp;
     const int rows_per_item = kWarps * rpw;
     const int nrb = (ld.width + rows_per_item - 1) / rows_per_item;
-    const int c = item / nrb;
-    const int rb = item - c * nrb;
+    const int cl = item / nrb;   // chunk within the item range
+    const int c = tc.c0 + cl;
+    const int rb = item - cl * nrb;
     const bool sink = (l == p.L - 1);
     const int off = lane * V;
-    const Val* pc = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * ld.prev_width * CHV + off;
+    const Val* pc = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * p.wmax * CHV + off;
     Val* child = static_cast<Val*>(p.slab[l & 1]);
     const Prop* gc = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV + off;
     const int r0 = rb * rows_per_item + warp * rpw;
@@ -617,7 +624,7 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = (Val)0;
     for (unsigned m = empty; m; m &= m - 1)   // rows without in-edges hold 0
-        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(m) - 1, tc, off, acc);
+        store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(m) - 1, tc, off, acc);
     unsigned rows_left = nonempty;
     for (int w0 = beg; w0 < end; w0 += 32) {
         const int n = min(32, end - w0);
@@ -651,7 +658,7 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
                         for (int v = 0; v < V; ++v) acc[v] = madd(pv[u].v[v], gv[u].v[v], acc[v]);
                     }
                     if ((ends >> q) & 1u) {
-                        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(rows_left) - 1, tc, off, acc);
+                        store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(rows_left) - 1, tc, off, acc);
                         rows_left &= rows_left - 1;
 #pragma unroll
                         for (int v = 0; v < V; ++v) acc[v] = (Val)0;
@@ -681,10 +688,11 @@ __device__ __forceinline__ void item_level_grouped(const WalkParams& p, int l, c
     const int rpw = p.rows_per_warp;
     const int rows_per_item = kWarps * rpw;
     const int nrb = (ld.width + rows_per_item - 1) / rows_per_item;
-    const int c = item / nrb;
-    const int rb = item - c * nrb;
+    const int cl = item / nrb;   // chunk within the item range
+    const int c = tc.c0 + cl;
+    const int rb = item - cl * nrb;
     const bool sink = (l == p.L - 1);
-    const Val* pc = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * ld.prev_width * CHV + off;
+    const Val* pc = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * p.wmax * CHV + off;
     Val* child = static_cast<Val*>(p.slab[l & 1]);
     const Prop* gc = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV + off;
     const int r0 = rb * rows_per_item + warp * rpw;
@@ -713,7 +721,7 @@ __device__ __forceinline__ void item_level_grouped(const WalkParams& p, int l, c
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = (Val)0;
     for (unsigned m = group_rows & ~nonempty; m; m &= m - 1)   // rows without in-edges hold 0
-        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(m) - 1, tc, off, acc);
+        store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(m) - 1, tc, off, acc);
     unsigned rows_left = group_rows & nonempty;
     const int len = eend - ebeg;
     int maxlen = len;
@@ -761,7 +769,7 @@ __device__ __forceinline__ void item_level_grouped(const WalkParams& p, int l, c
                         for (int v = 0; v < V; ++v) acc[v] = madd(pv[u].v[v], gv[u].v[v], acc[v]);
                     }
                     if ((ends >> (gid * LPR + q)) & 1u) {
-                        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(rows_left) - 1, tc, off, acc);
+                        store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(rows_left) - 1, tc, off, acc);
                         rows_left &= rows_left - 1;
 #pragma unroll
                         for (int v = 0; v < V; ++v) acc[v] = (Val)0;
@@ -794,11 +802,12 @@ __device__ __forceinline__ bool item_level_bulk(const WalkParams& p, int l, cons
     const int rpw = p.rows_per_warp;
     const int rows_per_item = kWarps * rpw;
     const int nrb = (ld.width + rows_per_item - 1) / rows_per_item;
-    const int c = item / nrb;
-    const int rb = item - c * nrb;
+    const int cl = item / nrb;   // chunk within the item range
+    const int c = tc.c0 + cl;
+    const int rb = item - cl * nrb;
     const bool sink = (l == p.L - 1);
     const int off = lane * V;
-    const Val* pc0 = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * ld.prev_width * CHV;
+    const Val* pc0 = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * p.wmax * CHV;
     Val* child = static_cast<Val*>(p.slab[l & 1]);
     const Prop* gc0 = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV;
     const int r0 = rb * rows_per_item + warp * rpw;
@@ -825,7 +834,7 @@ __device__ __forceinline__ bool item_level_bulk(const WalkParams& p, int l, cons
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = (Val)0;
     for (unsigned m = empty; m; m &= m - 1)   // rows without in-edges hold 0
-        store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(m) - 1, tc, off, acc);
+        store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(m) - 1, tc, off, acc);
     if (beg == end) return true;
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem) + warp * kRing;
     unsigned char* ring = smem + kRingHeader + (size_t)warp * kRing * SLOTB;
@@ -901,7 +910,7 @@ __device__ __forceinline__ bool item_level_bulk(const WalkParams& p, int l, cons
             for (int v = 0; v < V; ++v) acc[v] = madd(pv.v[v], gv.v[v], acc[v]);
         }
         if ((ends >> (e - wbase)) & 1u) {
-            store_row<MODE, V, CHV>(p, sink, child, c, ld.width, r0 + __ffs(rows_left) - 1, tc, off, acc);
+            store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(rows_left) - 1, tc, off, acc);
             rows_left &= rows_left - 1;
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[v] = (Val)0;

@@ -127,6 +127,7 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     p.R = per_sample_out;
     p.tile = tile;
     p.rows_per_warp = 1;
+    p.wmax = (int32_t)gv.Wmax;
     p.timeout_ns = 10000LL * 1000000LL;
 
     int per_sm = 0, sms = 0;

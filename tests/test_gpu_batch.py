@@ -52,6 +52,9 @@ def mix():
     (0, {"samples_per_lane": 1, "rows_per_warp": 4, "tile_samples": 2048}),
     (1, {"samples_per_lane": 4, "layout": 3, "rows_per_warp": 8}),
     (2, {"samples_per_lane": 2, "layout": 3}),
+    (1, {"window_chunks": 2}),
+    (0, {"window_chunks": 1, "tile_samples": 2048}),
+    (2, {"window_chunks": 3, "samples_per_lane": 1}),
 ])
 def test_batch_matches_single_graph_bitwise(cg, mix, mode, tuning):
     graphs = _setup(cg, mix)

@@ -153,14 +153,52 @@ def test_ragged_sample_counts(cg, S):
     w = tiny(num_samples=S)
     R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
     for mode in (0, 1):
-        Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode)
-        check_fp(Rg, mg, R, A, mode)
+        for tuning in (None, {"schedule": 2, "window_chunks": 1, "tile_samples": 256}):
+            Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode, tuning)
+            check_fp(Rg, mg, R, A, mode)
 
 
-def test_zero_samples(cg):
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_zero_samples(cg, schedule):
     w = tiny(num_samples=0)
-    Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 0)
+    Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 0, {"schedule": schedule})
     assert Rg.size == 0 and mg == 0.0
+
+
+def test_windowed_schedule_multi_tile_and_count(cg):
+    """Windows continue across tiles of samples (ragged last tile) and the sample
+    reduction waits for every window; count mode is bit-exact."""
+    w = medium(num_samples=5000)
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    for mode, tuning in ((0, {"tile_samples": 1024, "window_chunks": 3}),
+                         (1, {"tile_samples": 2048, "window_chunks": 1}),
+                         (0, {"tile_samples": 640, "samples_per_lane": 1, "window_chunks": 7})):
+        tuning = dict(tuning, schedule=2)
+        Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode, tuning)
+        check_fp(Rg, mg, R, A, mode)
+        base = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode, dict(tuning, schedule=1))
+        np.testing.assert_array_equal(Rg, base[0])
+        assert mg == base[1]
+    cnt, _ = oracle.count_paths(w.graph)
+    Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 2,
+                     {"schedule": 2, "window_chunks": 2, "tile_samples": 1500})
+    assert np.all(Rg == cnt) and mg == float(cnt)
+
+
+def test_schedule_tuning_resolution(cg):
+    w = tiny(num_samples=64)
+    gr = cg.Graph.from_workload_graph(w.graph)
+    gr.set_samples(torch.from_numpy(w.samples.t).cuda(), w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+    t = gr.get_tuning(0)
+    assert t["schedule"] in (1, 2) and t["window_chunks"] >= 1
+    gr.set_tuning(schedule=2, window_chunks=4)
+    t = gr.get_tuning(1)
+    assert t["schedule"] == 2 and t["window_chunks"] == 4
+    with pytest.raises(cg.CosError):
+        gr.set_tuning(schedule=3)
+    with pytest.raises(cg.CosError):
+        gr.set_tuning(window_chunks=-1)
+    gr.close()
 
 
 def test_two_level_graph_and_chain(cg):
@@ -243,7 +281,11 @@ def test_results_independent_of_launch_shape(cg):
                    {"samples_per_lane": 4, "layout": 2, "rows_per_warp": 28},
                    {"samples_per_lane": 2, "layout": 2, "rows_per_warp": 5, "tile_samples": 1000},
                    {"samples_per_lane": 4, "layout": 3, "rows_per_warp": 8},
-                   {"samples_per_lane": 1, "layout": 3, "rows_per_warp": 3, "tile_samples": 700}):
+                   {"samples_per_lane": 1, "layout": 3, "rows_per_warp": 3, "tile_samples": 700},
+                   {"schedule": 2, "window_chunks": 1},
+                   {"schedule": 2, "window_chunks": 3, "samples_per_lane": 2, "tile_samples": 1000},
+                   {"schedule": 2, "window_chunks": 5, "samples_per_lane": 4, "layout": 2, "rows_per_warp": 6},
+                   {"schedule": 2, "samples_per_lane": 4, "layout": 3, "window_chunks": 2}):
         for mode in (0, 1):
             Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode, tuning)
             if ref is None:
