@@ -176,7 +176,8 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  * Launch shape used by cos_evaluate.  Fields <= 0 mean "automatic".
  *   samples_per_lane  1, 2 or 4 consecutive samples per thread (vector width)
  *   tile_samples      samples per tile (rounded up to 32 * samples_per_lane)
- *   rows_per_warp     consecutive destination rows one warp takes per work item (<= 31)
+ *   rows_per_warp     consecutive destination rows one warp takes per work item (<= 31);
+ *                     automatic: 31 with the work queue, else 4 (FP64) or 16
  *   blocks_per_sm     persistent CTAs per SM (capped by occupancy)
  *   timeout_ms        grid-barrier wait limit
  *   layout            1 = wide (a warp owns one row; chunks of 32*samples_per_lane
@@ -186,18 +187,22 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *                     and propagator runs in shared memory with cp.async.bulk on
  *                     mbarriers, 8 edges in flight per warp)
  *   schedule          1 = level-synchronous: one cooperative kernel, every level of a
- *                     tile ends at a grid-wide barrier; 2 = windowed (Sec. II.C,
- *                     asynchronous evaluation of levels): the chunks of each tile are
- *                     cut into windows of window_chunks chunks, every window is its
- *                     own chain (propagators, levels 1..L-1, continuing into the same
- *                     window of the next tile), the chains are issued in wavefront
- *                     order to a persistent work-queue kernel and each work item waits
- *                     only for the previous phase of its own window, so about L
- *                     windows are in flight and their node values and propagators
- *                     can stay in L2.  Results are bitwise the same either way.
- *                     Batched launches use windows when window_chunks > 0.
+ *                     tile ends at a grid-wide barrier, work items assigned
+ *                     statically; 2 = work queue (Sec. II.C, asynchronous evaluation
+ *                     of levels): the persistent work-queue kernel of the batched
+ *                     launch, items drawn from a ticket counter, each waiting only for
+ *                     the previous phase of its own window of sample chunks.  The
+ *                     chunks of each tile are cut into windows of window_chunks
+ *                     chunks; every window is its own chain (propagators, levels
+ *                     1..L-1, continuing into the same window of the next tile) and
+ *                     the chains are issued in wavefront order, so about L windows
+ *                     are in flight.  Results are bitwise the same either way.
+ *                     Automatic: 2 in FP64 mode or when the widest level has at
+ *                     least 65536 nodes, else 1.  Batched launches always use the
+ *                     work queue, with windows when window_chunks > 0.
  *   window_chunks     chunks (of 32*samples_per_lane samples, 32 in the grouped
- *                     layout) per window in the windowed schedule
+ *                     layout) per window of the work-queue schedule; automatic: one
+ *                     window per tile
  */
 typedef struct cos_tuning {
     int32_t samples_per_lane;

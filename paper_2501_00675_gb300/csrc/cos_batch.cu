@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -29,7 +30,9 @@
 namespace cosgpu {
 namespace {
 
-enum TaskKind : int32_t { TK_COEF = 0, TK_PROP = 1, TK_LEVEL = 3, TK_PARTIALS = 4, TK_FINAL = 5 };
+// TK_STALL: a test-only task (COS_TEST_STALL_TASK) that is drawn but never counted
+// done, so that a dependency wait on it runs into its time limit.
+enum TaskKind : int32_t { TK_COEF = 0, TK_PROP = 1, TK_LEVEL = 3, TK_PARTIALS = 4, TK_FINAL = 5, TK_STALL = 6 };
 
 struct Task {
     int32_t graph;      // index into the parameter array
@@ -71,41 +74,51 @@ template <int MODE, int V, int LAYOUT>
 __global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V>()) batch_kernel(const BatchArgs a) {
     constexpr int CHV = chunk_samples<V, LAYOUT>();
     extern __shared__ __align__(16) double smem[];
-    __shared__ long long s_ticket;
+    // Tickets: thread 0 claims the next ticket while the current item runs and hands
+    // it over with the end-of-item barrier (double-buffered).  A claimed ticket is
+    // held only by a CTA that is running an earlier one, so the lowest unfinished
+    // ticket is always running and its dependencies (earlier tasks) are complete.
+    __shared__ long long s_ticket[2];
     __shared__ int s_ok;
-    int cursor = 0;
+    if (threadIdx.x == 0) s_ticket[0] = (long long)atomicAdd(&a.ctrl->ticket, 1ull);
+    __syncthreads();
+    int cursor = 0, buf = 0;
+    int ready = -1;   // the task whose dependencies this CTA has seen complete (they stay complete)
+    long long next = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_ticket = (long long)atomicAdd(&a.ctrl->ticket, 1ull);
-        __syncthreads();
-        const long long t = s_ticket;
+        const long long t = s_ticket[buf];
         if (t >= a.total) break;
         while (cursor + 1 < a.ntasks && a.tasks[cursor + 1].first <= t) ++cursor;
         const Task tk = a.tasks[cursor];
         const int item = (int)(t - tk.first);
-        if (threadIdx.x == 0) {
-            int ok = 1;
-            const unsigned long long t0 = global_timer_ns();
-            unsigned long long spin = 0;
-            for (int q = -1; ok && q < tk.join_cnt; ++q) {   // the chain predecessor, then the joins
-                const int dep = q < 0 ? tk.dep : a.joins[tk.join_off + q];
-                if (dep < 0) continue;
-                const unsigned need = (unsigned)a.tasks[dep].items;
-                for (;; ++spin) {
-                    if (ld_acquire_gpu_u32(a.done + dep) >= need) break;
-                    if (*(volatile int*)&a.ctrl->err != 0) { ok = 0; break; }
-                    if ((spin & 31) == 31 &&
-                        ((long long)(global_timer_ns() - t0) > a.timeout_ns || spin > (1ull << 32))) {
-                        if (atomicCAS(&a.ctrl->err, 0, KERR_BARRIER_TIMEOUT) == 0) a.ctrl->err_task = cursor;
-                        ok = 0;
-                        break;
+        if (threadIdx.x == 0) next = (long long)atomicAdd(&a.ctrl->ticket, 1ull);   // used after this item
+        if (cursor != ready) {   // uniform: every thread tracks the same cursor
+            if (threadIdx.x == 0) {
+                int ok = 1;
+                const unsigned long long t0 = global_timer_ns();
+                unsigned long long spin = 0;
+                for (int q = -1; ok && q < tk.join_cnt; ++q) {   // the chain predecessor, then the joins
+                    const int dep = q < 0 ? tk.dep : a.joins[tk.join_off + q];
+                    if (dep < 0) continue;
+                    const unsigned need = (unsigned)a.tasks[dep].items;
+                    for (;; ++spin) {
+                        if (ld_acquire_gpu_u32(a.done + dep) >= need) break;
+                        if (*(volatile int*)&a.ctrl->err != 0) { ok = 0; break; }
+                        if ((spin & 31) == 31 &&
+                            ((long long)(global_timer_ns() - t0) > a.timeout_ns || spin > (1ull << 32))) {
+                            if (atomicCAS(&a.ctrl->err, 0, KERR_BARRIER_TIMEOUT) == 0) a.ctrl->err_task = cursor;
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(64);
                     }
-                    __nanosleep(64);
                 }
+                s_ok = ok;
             }
-            s_ok = ok;
+            __syncthreads();
+            if (!s_ok) return;
+            ready = cursor;
         }
-        __syncthreads();
-        if (!s_ok) return;
         const WalkParams& p = a.params[tk.graph];
         TileCtx tc = tile_ctx<CHV>(p, tk.tix);
         tc.c0 = tk.c0;
@@ -121,11 +134,14 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V>()) batch_k
                 }
                 break;
             case TK_PARTIALS: item_partials<MODE>(p, item); break;
+            case TK_STALL: break;
             default: item_final(p); break;
         }
+        if (threadIdx.x == 0) s_ticket[buf ^ 1] = next;
         __syncthreads();
-        if (threadIdx.x == 0)   // release: the item's writes are visible before it is counted done
+        if (threadIdx.x == 0 && tk.kind != TK_STALL)   // release: the item's writes are visible first
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.done + cursor) : "memory");
+        buf ^= 1;
     }
 }
 
@@ -377,7 +393,9 @@ int plan(cos_batch* b) {
         const int32_t ip = emit(part, std::move(js));
         Task fin = make(TK_FINAL, 0, 0, 1, 0);
         fin.dep = ip;
-        emit(fin, {});
+        std::vector<int32_t> stall;
+        if (g == 0 && getenv("COS_TEST_STALL_TASK")) stall.push_back(emit(make(TK_STALL, 0, 0, 1, 0), {}));
+        emit(fin, std::move(stall));
     }
     // Round-robin interleave of the graphs' lists (each list keeps its order).
     b->tasks.clear();
@@ -635,7 +653,7 @@ int cos_batch_autotune(cos_batch_t b, void* stream, cos_tuning* best_out) {
     cudaStream_t st = (cudaStream_t)stream;
     const cos_tuning base = b->tuning;
     const int vecs[] = {1, 2, 4};
-    const int rpws[] = {4, 8, 16, 28};
+    const int rpws[] = {4, 8, 16, 31};
     float best_ms = 1e30f;
     cos_tuning best = base;
     cudaEvent_t e0, e1;

@@ -461,13 +461,14 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
     return COS_OK;
 }
 
-// Schedule when the caller leaves it automatic: 1 level-synchronous, 2 windowed.
-static const int kDefaultSchedule = 1;
-
 static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* tile_out) {
     cos_tuning t = g->tuning;
     if (t.samples_per_lane <= 0) t.samples_per_lane = default_vec(mode);
-    if (t.rows_per_warp <= 0) t.rows_per_warp = (mode == COS_MODE_FP64) ? 4 : 8;   // measured best on GB300
+    // Measured on GB300: the work queue (dynamic item assignment, dependency counters)
+    // is ahead in FP64 and on graphs with very wide levels; the cooperative kernel on
+    // the smaller FP32 and count walks.
+    if (t.schedule <= 0) t.schedule = (mode == COS_MODE_FP64 || g->Wmax >= 65536) ? 2 : 1;
+    if (t.rows_per_warp <= 0) t.rows_per_warp = t.schedule == 2 ? 31 : (mode == COS_MODE_FP64 ? 4 : 16);
     if (t.layout <= 0) t.layout = 1;
     if (t.timeout_ms <= 0) {
         const char* env = getenv("COS_TIMEOUT_MS");
@@ -496,16 +497,8 @@ static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* til
     }
     tile = std::min(tile, need);
     t.tile_samples = (int32_t)tile;
-    if (t.schedule <= 0) t.schedule = kDefaultSchedule;
-    if (t.window_chunks <= 0) {
-        // about L windows are in flight: size them so that their node values (two
-        // levels) and propagators take about half of L2
-        const size_t val = (mode == COS_MODE_FP32_MIXED) ? 4 : 8;
-        const size_t gt = (mode == COS_MODE_COUNT_I64) ? 0 : val;
-        const size_t per_chunk = (2 * val * (size_t)g->Wmax + gt * (size_t)g->P) * (size_t)ch;
-        const size_t l2 = (size_t)64 << 20;
-        t.window_chunks = (int32_t)std::max<size_t>(1, l2 / (std::max<size_t>(g->L, 1) * per_chunk));
-    }
+    // one window per tile unless asked: smaller windows (kept in L2) measured slower
+    if (t.window_chunks <= 0) t.window_chunks = (int32_t)(tile / ch);
     *out = t;
     *tile_out = tile;
     return COS_OK;

@@ -335,21 +335,25 @@ def test_evaluate_before_samples_is_state_error(cg):
     gr.close()
 
 
-def test_barrier_timeout_is_reported_and_context_survives(cg, monkeypatch):
-    # One CTA leaves before the first level barrier; the others' bounded waits run
-    # out and the launch ends with COS_ERR_TIMEOUT.  No GPU fault is involved.
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_barrier_timeout_is_reported_and_context_survives(cg, monkeypatch, schedule):
+    # Level-synchronous: one CTA leaves before the first level barrier and the
+    # others' bounded waits run out.  Work queue: the plan gets a task that never
+    # completes and the final item's bounded dependency wait runs out.  Either way
+    # the launch ends with COS_ERR_TIMEOUT; no GPU fault is involved.
     w = tiny(num_samples=256)
     gr = cg.Graph.from_workload_graph(w.graph)
-    gr.set_tuning(timeout_ms=200)
+    gr.set_tuning(timeout_ms=200, schedule=schedule)
     t = torch.from_numpy(w.samples.t).cuda()
     gr.set_samples(t, w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
-    monkeypatch.setenv("COS_TEST_SKIP_BARRIER_PHASE", "4")   # the barrier after level 1
+    hook = "COS_TEST_SKIP_BARRIER_PHASE" if schedule == 1 else "COS_TEST_STALL_TASK"
+    monkeypatch.setenv(hook, "4")   # schedule 1: the barrier after level 1
     t0 = time.time()
     with pytest.raises(cg.CosError) as ei:
         gr.evaluate(0)
     assert ei.value.code == cg.COS_ERR_TIMEOUT
     assert time.time() - t0 < 30
-    monkeypatch.delenv("COS_TEST_SKIP_BARRIER_PHASE")
+    monkeypatch.delenv(hook)
     R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
     o = torch.empty(256, dtype=torch.float64, device="cuda")
     m = gr.evaluate(0, out=o)
