@@ -10,6 +10,9 @@ Contents
     counts with 128-bit overflow detection, Neumaier summation.
   * ``brute_force_paths`` / ``brute_force_sum``: pure-Python enumeration of all
     root-to-sink paths (one path = one diagram, Sec. II.B) for tiny graphs.
+  * ``tabulated_propagator`` / ``evaluate_tabulated``: a user-tabulated G(tau) per
+    kind (linear interpolation on a uniform grid, one table per sign of tau), and
+    the DP with those factors.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (closed forms, brute force, library matrix products, propagator identities).
@@ -109,6 +112,58 @@ def edge_weights(graph, eps: np.ndarray, beta: float, t_sample: np.ndarray) -> n
         out[m] = propagator(eps[k], beta, tau[m])
     out[(e[:, 2] & SIGN_BIT) != 0] *= -1.0
     return out
+
+
+def tabulated_propagator(table: np.ndarray, tau_max: float, tau) -> np.ndarray:
+    """A user-tabulated propagator G(tau) for one kind (the general G of the Fig. 1
+    caption, given as numbers), elementwise over tau: table[0] holds the values at
+    tau_m = m*h, m = 0..T, h = tau_max/T, used for tau >= 0 (the tau = 0 branch of
+    the free propagator, decided by t_i >= t_j); table[1] holds the values at
+    tau_m = -tau_max + m*h, used for tau < 0.  Between nodes the value is the
+    linear interpolation of its two neighbours; outside [-tau_max, tau_max] the end
+    value.  Two halves keep the jump at tau = 0 (G(0+) - G(0-) = -1 for fermions)."""
+    table = np.asarray(table, dtype=np.float64)
+    if table.ndim != 2 or table.shape[0] != 2 or table.shape[1] < 2:
+        raise ValueError("table must be [2, T+1] with T >= 1")
+    T = table.shape[1] - 1
+    tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
+    pos = tau >= 0.0
+    out = np.empty_like(tau)
+    xs_pos = np.arange(T + 1) * (tau_max / T)
+    xs_neg = -tau_max + np.arange(T + 1) * (tau_max / T)
+    out[pos] = np.interp(tau[pos], xs_pos, table[0])
+    out[~pos] = np.interp(tau[~pos], xs_neg, table[1])
+    return out
+
+
+def tabulated_edge_weights(graph, tables: np.ndarray, tau_max: float, t_sample: np.ndarray) -> np.ndarray:
+    """Per-edge factors +-G_{k_e}(t_{i_e} - t_{j_e}) from tables[K, 2, T+1] for one sample."""
+    e = graph.edges
+    tau = t_sample[e[:, 3]] - t_sample[e[:, 4]]
+    kind = e[:, 2] & KIND_MASK
+    out = np.empty(e.shape[0])
+    for k in np.unique(kind):
+        m = kind == k
+        out[m] = tabulated_propagator(tables[k], tau_max, tau[m])
+    out[(e[:, 2] & SIGN_BIT) != 0] *= -1.0
+    return out
+
+
+def evaluate_tabulated(graph, tables: np.ndarray, tau_max: float, t: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """Per-sample sink values R[s] and A[s] = sum of |path| values with tabulated
+    propagators: the level-wise DP (``pathsum``) once per sample with that sample's
+    edge factors."""
+    tables = np.asarray(tables, dtype=np.float64)
+    if tables.ndim != 3 or tables.shape[0] < graph.num_kinds or tables.shape[1] != 2:
+        raise ValueError("tables must be [K, 2, T+1]")
+    S = t.shape[0]
+    R = np.empty(S)
+    A = np.empty(S)
+    for s in range(S):
+        w = tabulated_edge_weights(graph, tables, tau_max, t[s])
+        R[s] = pathsum(graph, w)[-1]
+        A[s] = pathsum(graph, np.abs(w))[-1]
+    return R, A
 
 
 def pathsum(graph, w: np.ndarray) -> np.ndarray:

@@ -272,3 +272,75 @@ def test_sign_flags_against_brute_force_and_chain():
     R0, _ = oracle.evaluate(c, np.array([math.log(2.0)]), 2.0, tt)
     R1, _ = oracle.evaluate(_with_signs(c, np.array([False, True, False])), np.array([math.log(2.0)]), 2.0, tt)
     assert R0[0] == pytest.approx((-0.4) * 0.4 * (-0.8), rel=1e-14) and R1[0] == -R0[0]
+
+
+# ------------------------------------------------------------------ tabulated propagators
+
+def test_tabulated_propagator_exact_on_piecewise_linear_tables():
+    # a table sampled from a + b*tau on each half is reproduced exactly between nodes
+    # (closed form), and the end values hold outside [-tau_max, tau_max]
+    rng = np.random.default_rng(11)
+    T, tau_max = 37, 7.5
+    a_pos, b_pos, a_neg, b_neg = rng.normal(size=4)
+    xs = np.arange(T + 1) * (tau_max / T)
+    tab = np.stack([a_pos + b_pos * xs, a_neg + b_neg * (xs - tau_max)])
+    tau = rng.uniform(-tau_max, tau_max, 4000)
+    got = oracle.tabulated_propagator(tab, tau_max, tau)
+    want = np.where(tau >= 0, a_pos + b_pos * tau, a_neg + b_neg * tau)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+    out = oracle.tabulated_propagator(tab, tau_max, np.array([tau_max * 1.5, -tau_max * 2.0]))
+    assert out[0] == pytest.approx(a_pos + b_pos * tau_max, abs=1e-13)
+    assert out[1] == pytest.approx(a_neg - b_neg * tau_max, abs=1e-13)
+
+
+def test_tabulated_propagator_hits_nodes_and_keeps_the_jump():
+    # grid nodes exactly representable (T and tau_max powers of two): node values
+    # come back exactly; tau = 0 takes the tau >= 0 table (G(0+)), tau < 0 the other
+    T, tau_max = 64, 8.0
+    rng = np.random.default_rng(12)
+    tab = rng.normal(size=(2, T + 1))
+    m = np.arange(T + 1)
+    assert np.array_equal(oracle.tabulated_propagator(tab, tau_max, m * (tau_max / T)), tab[0])
+    assert np.array_equal(oracle.tabulated_propagator(tab, tau_max, -tau_max + m[:-1] * (tau_max / T)), tab[1][:-1])
+    assert oracle.tabulated_propagator(tab, tau_max, 0.0)[0] == tab[0][0]
+    assert oracle.tabulated_propagator(tab, tau_max, -1e-300)[0] == pytest.approx(tab[1][-1], abs=1e-12)
+
+
+@pytest.mark.parametrize("eps", [-1.7, 0.0, 0.9])
+def test_tabulated_free_propagator_within_interpolation_bound(eps):
+    # tables sampled from the free-fermion G: linear interpolation is within
+    # h^2/8 * max|G''| of it, and G'' = eps^2 G with |G| <= 1 (antiperiodic halves)
+    beta, T = 10.0, 400
+    h = beta / T
+    xs = np.arange(T + 1) * h
+    tab = np.stack([oracle.propagator(eps, beta, xs), oracle.propagator(eps, beta, xs - beta + 0.0)])
+    tab[1][-1] = oracle.propagator(eps, beta, -1e-12)[0]   # G(0-) as the limit from below
+    tau = np.random.default_rng(13).uniform(-beta, beta, 5000)
+    tau = tau[np.abs(tau) > 1e-9]
+    err = np.abs(oracle.tabulated_propagator(tab, beta, tau) - oracle.propagator(eps, beta, tau))
+    bound = h * h / 8.0 * eps * eps * 1.0 + 1e-12
+    assert err.max() <= bound
+
+
+def test_tabulated_dp_against_brute_force():
+    g, eps, t = _random_graph(41, [1, 3, 5, 5, 2, 1], fmax=3)
+    rng = np.random.default_rng(14)
+    tables = rng.normal(size=(g.num_kinds, 2, 9))
+    mask = rng.random(g.num_edges) < 0.3
+    gs = _with_signs(g, mask)
+    R, A = oracle.evaluate_tabulated(gs, tables, 10.0, t)
+    paths = oracle.brute_force_paths(gs)
+    for s in range(t.shape[0]):
+        w = oracle.tabulated_edge_weights(gs, tables, 10.0, t[s])
+        r, a = oracle.brute_force_sum(paths, w)
+        assert abs(R[s] - r) <= 1e-13 * a and abs(A[s] - a) <= 1e-13 * a
+
+
+def test_tabulated_sign_flags_on_one_level_negate_every_path():
+    g, _, t = _random_graph(43, [1, 4, 6, 6, 3, 1], fmax=3)
+    tables = np.random.default_rng(15).normal(size=(g.num_kinds, 2, 6))
+    lvl = np.repeat(np.arange(g.num_levels), g.edge_counts)
+    R0, A0 = oracle.evaluate_tabulated(g, tables, 10.0, t)
+    R1, A1 = oracle.evaluate_tabulated(_with_signs(g, lvl == 3), tables, 10.0, t)
+    np.testing.assert_array_equal(R1, -R0)
+    np.testing.assert_array_equal(A1, A0)
