@@ -165,6 +165,25 @@ int cos_evaluate(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean
 int cos_get_result(cos_graph_t g, double* mean_out, void* stream);
 
 /*
+ * User-tabulated propagators (Fig. 1 caption: the edge factor is a general
+ * Green's function G; Sec. II.C "Numerical stability": each edge loads the
+ * relevant one).  Replaces the free-fermion formula of every kind k of g by
+ * numbers: table is host memory [K][2][T+1] doubles (copied; the caller keeps
+ * ownership); half 0 holds G_k at tau = m*h, m = 0..T, h = tau_max/T, and is used
+ * for tau = t_i - t_j >= 0; half 1 holds G_k at tau = -tau_max + m*h and is used
+ * for tau < 0 (two halves keep the jump at tau = 0).  Between grid nodes the value
+ * is the linear interpolation of its neighbours, computed in double and rounded
+ * once to the mode's propagator type; outside [-tau_max, tau_max] the end value.
+ * The fermion-loop sign (kind bit 30) still applies.  T = 0 (table and tau_max
+ * ignored) returns to the formula.  1 <= T <= 2^24, tau_max finite and > 0,
+ * every entry finite, else COS_ERR_INVALID and nothing changes.  The tables
+ * belong to the handle: cos_graph_share copies them into the new handle.
+ * Cost: about 7 FP64 operations per propagator slot and sample instead of one
+ * multiplication (no exponentials).
+ */
+int cos_set_propagator_table(cos_graph_t g, int32_t T, const double* table, double tau_max);
+
+/*
  * Graph facts, written to info[0..n) in this order (n <= 10):
  *   0 L, 1 N, 2 E, 3 number of propagator slots P, 4 widest level W_max,
  *   5 path count mod 2^64 (from ingest), 6 path-count overflow flag,

@@ -87,6 +87,7 @@ def load_library(build_if_missing: bool = False):
         lib.cos_get_trace.argtypes = [vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
         lib.cos_evaluate_static.argtypes = [vp, i32, i64, vp, i64, vp, f64, vp, vp, vp]
         lib.cos_graph_share.argtypes = [vp, ctypes.POINTER(vp)]
+        lib.cos_set_propagator_table.argtypes = [vp, i32, vp, f64]
         lib.cos_batch_create.argtypes = [i32, vp, i32, vp, ctypes.POINTER(vp)]
         lib.cos_batch_reset.argtypes = [vp, i32, vp, vp]
         lib.cos_batch_set_tuning.argtypes = [vp, ctypes.POINTER(CosTuning)]
@@ -211,6 +212,20 @@ class Graph:
         t = CosTuning(samples_per_lane, tile_samples, rows_per_warp, blocks_per_sm, timeout_ms, layout, schedule,
                       window_chunks)
         _check(load_library().cos_set_tuning(self._h, ctypes.byref(t)))
+
+    def set_propagator_table(self, tables, tau_max: float = 0.0):
+        """tables: [K, 2, T+1] float64 (half 0: tau >= 0 on m*tau_max/T, half 1: tau < 0
+        on -tau_max + m*tau_max/T); None returns to the free-fermion formula."""
+        lib = load_library()
+        if tables is None:
+            _check(lib.cos_set_propagator_table(self._h, 0, None, ctypes.c_double(0.0)))
+            return
+        tab = np.ascontiguousarray(tables, dtype=np.float64)
+        if tab.ndim != 3 or tab.shape[1] != 2 or tab.shape[2] < 2:
+            raise ValueError("tables must be [K, 2, T+1] with T >= 1")
+        _check(lib.cos_set_propagator_table(self._h, int(tab.shape[2] - 1),
+                                            tab.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            ctypes.c_double(float(tau_max))))
 
     def get_tuning(self, mode: int) -> dict:
         t = CosTuning()

@@ -141,6 +141,9 @@ struct cos_graph {
     int32_t trace_cap = 0;
     int last_mode = 0;
     cos_batch_t wave = nullptr;     // one-graph batch of the windowed schedule (created on first use)
+    double* d_ptab = nullptr;       // user-tabulated propagators [K][2][ptab_T+1], or none
+    int32_t ptab_T = 0;
+    double ptab_tau_max = 0.0;
     int last_wave = 0;              // the last evaluate ran the windowed schedule
 };
 
@@ -398,6 +401,15 @@ int cos_graph_share(cos_graph_t src, cos_graph_t* out) {
     DeviceGuard dg(g->device);
     cudaError_t e = cudaMalloc(&g->d_ctrl, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMemset(g->d_ctrl, 0, sizeof(Ctrl));
+    if (e == cudaSuccess && src->d_ptab) {   // the propagator tables are copied, not shared
+        const size_t bytes = sizeof(double) * 2 * 2 * (size_t)src->ptab_T * (size_t)src->K;
+        e = cudaMalloc(&g->d_ptab, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_ptab, src->d_ptab, bytes, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) {
+            g->ptab_T = src->ptab_T;
+            g->ptab_tau_max = src->ptab_tau_max;
+        }
+    }
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "cudaMalloc ctrl");
         cos_destroy(g);
@@ -413,6 +425,7 @@ int cos_destroy(cos_graph_t g) {
         DeviceGuard dg(g->device);
         if (g->wave) cos_batch_destroy(g->wave);
         g->wave = nullptr;
+        dfree(g->d_ptab);
         if (g->arrays) {
             g->arrays.reset();   // frees the structure arrays with the last handle sharing them
         } else {
@@ -727,6 +740,43 @@ int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, doub
     return rc == COS_OK ? COS_OK : fail(rc, "exp self-test launch failed");
 }
 
+int cos_set_propagator_table(cos_graph_t g, int32_t T, const double* table, double tau_max) {
+    if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
+    if (T < 0 || T > (1 << 24)) return fail(COS_ERR_INVALID, "T must be in [0, 2^24]");
+    DeviceGuard dg(g->device);
+    if (T == 0) {   // back to the free-fermion formula
+        dfree(g->d_ptab);
+        g->ptab_T = 0;
+        g->ptab_tau_max = 0.0;
+        return COS_OK;
+    }
+    if (!table) return fail(COS_ERR_INVALID, "table is NULL");
+    if (!(tau_max > 0.0) || !std::isfinite(tau_max)) return fail(COS_ERR_INVALID, "tau_max must be finite and > 0");
+    const size_t n = 2 * (size_t)(T + 1) * (size_t)g->K;
+    for (size_t q = 0; q < n; ++q)
+        if (!std::isfinite(table[q])) return fail(COS_ERR_INVALID, "table entry %zu is not finite", q);
+    // device form: per kind and half, T intervals as (value at the left node, slope)
+    std::vector<double> pairs(2 * 2 * (size_t)T * (size_t)g->K);
+    for (size_t h = 0; h < 2 * (size_t)g->K; ++h)
+        for (int32_t m = 0; m < T; ++m) {
+            const double a = table[h * (T + 1) + m], b = table[h * (T + 1) + m + 1];
+            pairs[2 * (h * T + m)] = a;
+            pairs[2 * (h * T + m) + 1] = b - a;
+        }
+    double* d = nullptr;
+    COS_CUDA(cudaMalloc(&d, sizeof(double) * pairs.size()), "cudaMalloc propagator table");
+    cudaError_t e = cudaMemcpy(d, pairs.data(), sizeof(double) * pairs.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "copy propagator table");
+    }
+    dfree(g->d_ptab);
+    g->d_ptab = d;
+    g->ptab_T = T;
+    g->ptab_tau_max = tau_max;
+    return COS_OK;
+}
+
 int cos_get_result(cos_graph_t g, double* mean_out, void* stream) {
     if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
     DeviceGuard dg(g->device);
@@ -754,6 +804,9 @@ int graph_view(cos_graph_t g, GraphView* out) {
     out->count_overflow = g->count_overflow ? 1 : 0;
     out->widths_host = g->widths.data();
     out->S = g->has_samples ? g->S : -1;
+    out->ptab = g->d_ptab;
+    out->ptab_T = g->ptab_T;
+    out->ptab_tau_max = g->ptab_tau_max;
     return COS_OK;
 }
 
@@ -808,6 +861,10 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
     p.tile = tile;
     p.rows_per_warp = tn.rows_per_warp;
     p.wmax = (int32_t)g->Wmax;
+    p.ptab = g->d_ptab;
+    p.ptab_T = g->ptab_T;
+    p.ptab_tau_max = g->ptab_tau_max;
+    p.ptab_inv_h = g->d_ptab ? (double)g->ptab_T / g->ptab_tau_max : 0.0;
     p.timeout_ns = (long long)tn.timeout_ms * 1000000LL;
     if (tn_out) *tn_out = tn;
     return COS_OK;

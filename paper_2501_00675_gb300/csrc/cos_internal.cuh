@@ -66,6 +66,14 @@ struct WalkParams {
     int32_t trace_cap;
     int32_t wmax;                // widest level: node-value slabs are [chunk][wmax rows][chunk samples]
     double* mean_out;            // optional second destination of the mean (batched launches)
+    // user-tabulated propagators (nullptr: the free-fermion formula): [K][2][ptab_T] pairs
+    // (G at node m, G at node m+1 minus G at node m); half 0 on tau = m*h (tau >= 0),
+    // half 1 on tau = -tau_max + m*h (tau < 0), h = tau_max/T
+    const double* ptab;
+    double ptab_tau_max;
+    double ptab_inv_h;           // T / tau_max
+    int32_t ptab_T;
+    int32_t pad3;
 };
 
 constexpr int kThreads = 256;           // 8 warps per CTA
@@ -87,6 +95,9 @@ struct GraphView {
     const double* exp_tab;
     const int64_t* widths_host;   // [L], host copy of the level widths
     int64_t S;                    // attached samples (-1: none)
+    const double* ptab;           // tabulated propagators (see WalkParams), or nullptr
+    double ptab_tau_max;
+    int32_t ptab_T;
 };
 int graph_view(cos_graph_t g, GraphView* out);
 // Resolve the launch tuning of `mode` (fields of `force` > 0 override the graph's own

@@ -441,6 +441,45 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
         const int64_t s0 = tc.base + (int64_t)c * CHV;
         const int q0 = __ldg(p.kind_slot + k), q1 = __ldg(p.kind_slot + k + 1);
         Prop* gt = static_cast<Prop*>(p.gtab) + (int64_t)c * p.P * CHV;
+        if (p.ptab) {
+            // user-tabulated G_k: linear interpolation on the half of the table that
+            // the sign of tau selects (tau = 0 takes the tau >= 0 half), in double,
+            // rounded once to the propagator type; end values outside the grid
+            double* st = sm;   // [D][CHV] times
+            for (int x = threadIdx.x; x < CHV * D; x += blockDim.x) {
+                const int i = x / CHV, s = x - i * CHV;
+                st[x] = p.t[(int64_t)i * p.t_ld + s0 + s];
+            }
+            __syncthreads();
+            const int T = p.ptab_T;
+            const double2* tk = reinterpret_cast<const double2*>(p.ptab) + (int64_t)k * 2 * T;   // (a_m, slope_m)
+            for (int q = q0 + warp; q < q1; q += kWarps) {
+                const int i = __ldg(p.slot_kij + 3 * q + 1), jw = __ldg(p.slot_kij + 3 * q + 2);
+                const int j = jw & 0x3fffffff;
+                const long long smask = (jw & 0x40000000) ? (long long)0x8000000000000000ULL : 0LL;
+#pragma unroll
+                for (int v = 0; v < CHV / 32; ++v) {
+                    const double tau = st[i * CHV + v * 32 + lane] - st[j * CHV + v * 32 + lane];
+                    const bool pos = tau >= 0.0;
+                    // grid coordinate: tau/h on the tau >= 0 half, (tau + tau_max)/h = tau/h + T below
+                    const double u = fma(tau, p.ptab_inv_h, pos ? 0.0 : (double)T);
+                    int m = (int)u;
+                    double f = u - (double)m;
+                    if (u < 0.0) {   // before the grid: the first node's value
+                        m = 0;
+                        f = 0.0;
+                    } else if (m >= T) {   // at or past the last node: its value
+                        m = T - 1;
+                        f = 1.0;
+                    }
+                    const double2 as = __ldg(tk + (pos ? 0 : T) + m);
+                    const double g = __longlong_as_double(__double_as_longlong(fma(f, as.y, as.x)) ^ smask);
+                    __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
+                }
+            }
+            __syncthreads();   // the next item reuses the shared memory
+            return;
+        }
         // FP32 mode with every factor and its low half inside the normal float range
         // (|eps| beta <= 30, so factors lie within e^{+-60}): exponentials,
         // prefactors and products in float-float FP32 arithmetic (about 1e-10 relative

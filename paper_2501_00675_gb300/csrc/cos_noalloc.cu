@@ -128,6 +128,10 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     p.tile = tile;
     p.rows_per_warp = 1;
     p.wmax = (int32_t)gv.Wmax;
+    p.ptab = gv.ptab;
+    p.ptab_T = gv.ptab_T;
+    p.ptab_tau_max = gv.ptab_tau_max;
+    p.ptab_inv_h = gv.ptab ? (double)gv.ptab_T / gv.ptab_tau_max : 0.0;
     p.timeout_ns = 10000LL * 1000000LL;
 
     int per_sm = 0, sms = 0;

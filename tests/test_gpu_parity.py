@@ -435,3 +435,65 @@ def test_device_counter_times_match_and_evaluate(cg, first):
     R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, t_host)
     check_fp(out.cpu().numpy(), m, R, A, 0)
     gr.close()
+
+
+# ------------------------------------------------------------------ tabulated propagators
+
+def _tables(rng, K, T):
+    # smooth random tables per kind and half, |G| <= 1 like a physical propagator
+    xs = np.linspace(0.0, 1.0, T + 1)
+    a, b, c = rng.uniform(-1, 1, (3, K, 2, 1))
+    return 0.5 * np.tanh(a + b * xs + c * np.sin(7 * xs))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tabulated_propagator_parity(cg, mode):
+    w = medium(num_samples=700)
+    rng = np.random.default_rng(21)
+    tables = _tables(rng, w.graph.num_kinds, 50)
+    tau_max = 9.0      # part of tau in (-10, 10) falls outside: end values
+    R, A = oracle.evaluate_tabulated(w.graph, tables, tau_max, w.samples.t)
+    for tuning in ({"schedule": 1}, {"schedule": 2, "rows_per_warp": 7}):
+        gr = cg.Graph.from_workload_graph(w.graph)
+        gr.set_tuning(**tuning)
+        gr.set_propagator_table(tables, tau_max)
+        gr.set_samples(torch.from_numpy(w.samples.t).cuda(), w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+        out = torch.empty(700, dtype=torch.float64, device="cuda")
+        m = gr.evaluate(mode, out=out)
+        check_fp(out.cpu().numpy(), m, R, A, mode)
+        gr.close()
+
+
+def test_tabulated_propagator_signs_share_reset_and_errors(cg):
+    rng = np.random.default_rng(22)
+    g = complete_layered_graph([1, 3, 6, 6, 2, 1], num_kinds=3, num_times=4, rng=rng)
+    e = g.edges.copy()
+    e[rng.random(len(e)) < 0.4, 2] |= oracle.SIGN_BIT
+    from workloads import Graph
+    g = Graph(g.widths, g.edge_counts, e, 3, 4)
+    t = rng.uniform(0, 10, (300, 4))
+    t[:, 1] = t[:, 2]                                  # tau == 0 on (1,2) and (2,1) slots
+    eps = rng.uniform(-2, 2, 3)
+    tables = _tables(rng, 3, 13)
+    R, A = oracle.evaluate_tabulated(g, tables, 10.0, t)
+    gr = cg.Graph.from_workload_graph(g)
+    gr.set_samples(torch.from_numpy(t).cuda(), eps, 10.0, cg.COS_T_SAMPLE_MAJOR)
+    analytic = torch.empty(300, dtype=torch.float64, device="cuda")
+    gr.evaluate(0, out=analytic)
+    gr.set_propagator_table(tables, 10.0)
+    out = torch.empty_like(analytic)
+    m = gr.evaluate(0, out=out)
+    check_fp(out.cpu().numpy(), m, R, A, 0)
+    twin = gr.share()                                  # the tables travel with a shared handle
+    twin.set_samples(torch.from_numpy(t).cuda(), eps, 10.0, cg.COS_T_SAMPLE_MAJOR)
+    out2 = torch.empty_like(out)
+    twin.evaluate(0, out=out2)
+    np.testing.assert_array_equal(out2.cpu().numpy(), out.cpu().numpy())
+    twin.close()
+    for bad in ((np.full((3, 2, 5), np.nan), 10.0), (tables, 0.0), (tables, -1.0)):
+        with pytest.raises(cg.CosError):
+            gr.set_propagator_table(*bad)
+    gr.set_propagator_table(None)                      # back to the formula
+    gr.evaluate(0, out=out)
+    np.testing.assert_array_equal(out.cpu().numpy(), analytic.cpu().numpy())
+    gr.close()
