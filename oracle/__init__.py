@@ -13,6 +13,8 @@ Contents
   * ``tabulated_propagator`` / ``evaluate_tabulated``: a user-tabulated G(tau) per
     kind (linear interpolation on a uniform grid, one table per sign of tau), and
     the DP with those factors.
+  * ``metropolis``: Metropolis walkers over the vertex times (weight |R|,
+    single-time proposals from counter-based random numbers).
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (closed forms, brute force, library matrix products, propagator identities).
