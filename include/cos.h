@@ -184,6 +184,37 @@ int cos_get_result(cos_graph_t g, double* mean_out, void* stream);
 int cos_set_propagator_table(cos_graph_t g, int32_t T, const double* table, double tau_max);
 
 /*
+ * Metropolis walkers over the vertex times (Sec. II.B: the sum over diagrams is
+ * integrated over the times by Monte Carlo sampling; Sec. II.C "Distributing the
+ * task": many Markov-chain walkers on one GPU; Sec. III: proposal and acceptance
+ * in device code).  Every sample attached to g is a walker and its times are the
+ * starting configuration; the walkers' state IS the graph's time buffer (with
+ * COS_T_BORROW, the caller's buffer), read back with cos_copy_times.
+ *   cos_mc_create  mode 0 (FP64) or 1 (FP32 mixed); evaluates R at the start
+ *                  (COS_ERR_STATE without samples, COS_ERR_INVALID for count mode)
+ *   cos_mc_run     num_steps steps, all on `stream`: walker s at step n draws
+ *                  Philox-4x32-10 words w0..w3 (counter (s mod 2^32, s >> 32,
+ *                  n mod 2^32, 2^31 | n >> 32), key (seed mod 2^32, seed >> 32)),
+ *                  replaces time i = (w0*D) >> 32 by beta*(((w2<<32|w1)>>11)*2^-53),
+ *                  evaluates every walker (cos_evaluate, the graph's tuning), keeps
+ *                  the move iff (w3 + 1/2)*2^-32 * |R| < |R'|, and tallies the sign
+ *                  of its current R
+ *   cos_mc_stats   out[4] = steps, accepted moves, positive and negative tallies
+ *                  (64-bit, exact); synchronizes `stream` and returns the status of
+ *                  the last evaluation.  (pos - neg)/(pos + neg) estimates the ratio
+ *                  of the integrals of R and |R| over [0, beta)^D.
+ *   cos_mc_values  copies the walkers' current R (double [S], host or device)
+ * The walkers must not outlive g, and g's samples must not be replaced while they
+ * run (COS_ERR_STATE).  The paper has the scheme, not this interface.
+ */
+typedef struct cos_mc* cos_mc_t;
+int cos_mc_create(cos_graph_t g, int32_t mode, uint64_t seed, void* stream, cos_mc_t* out);
+int cos_mc_run(cos_mc_t m, int32_t num_steps, void* stream);
+int cos_mc_stats(cos_mc_t m, int64_t* out, void* stream);
+int cos_mc_values(cos_mc_t m, double* per_walker_out, void* stream);
+int cos_mc_destroy(cos_mc_t m);
+
+/*
  * Graph facts, written to info[0..n) in this order (n <= 10):
  *   0 L, 1 N, 2 E, 3 number of propagator slots P, 4 widest level W_max,
  *   5 path count mod 2^64 (from ingest), 6 path-count overflow flag,

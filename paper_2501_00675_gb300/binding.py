@@ -88,6 +88,11 @@ def load_library(build_if_missing: bool = False):
         lib.cos_evaluate_static.argtypes = [vp, i32, i64, vp, i64, vp, f64, vp, vp, vp]
         lib.cos_graph_share.argtypes = [vp, ctypes.POINTER(vp)]
         lib.cos_set_propagator_table.argtypes = [vp, i32, vp, f64]
+        lib.cos_mc_create.argtypes = [vp, i32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+        lib.cos_mc_run.argtypes = [vp, i32, vp]
+        lib.cos_mc_stats.argtypes = [vp, vp, vp]
+        lib.cos_mc_values.argtypes = [vp, vp, vp]
+        lib.cos_mc_destroy.argtypes = [vp]
         lib.cos_batch_create.argtypes = [i32, vp, i32, vp, ctypes.POINTER(vp)]
         lib.cos_batch_reset.argtypes = [vp, i32, vp, vp]
         lib.cos_batch_set_tuning.argtypes = [vp, ctypes.POINTER(CosTuning)]
@@ -329,6 +334,43 @@ class Batch:
         if getattr(self, "_h", None) is not None and self._h.value:
             load_library().cos_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Metropolis:
+    """Metropolis walkers over a graph's attached times (cos_mc_*): every sample is
+    a walker; the graph's time buffer is the walkers' state."""
+
+    def __init__(self, graph: "Graph", mode: int, seed: int, stream=None):
+        self.graph = graph
+        h = ctypes.c_void_p()
+        _check(load_library().cos_mc_create(graph._h, int(mode), ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                            _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, num_steps: int, stream=None):
+        _check(load_library().cos_mc_run(self._h, int(num_steps), _stream_handle(stream)))
+
+    def stats(self, stream=None) -> dict:
+        out = np.zeros(4, dtype=np.int64)
+        _check(load_library().cos_mc_stats(self._h, _ptr(out), _stream_handle(stream)))
+        steps, acc, pos, neg = (int(x) for x in out)
+        return {"steps": steps, "accepted": acc, "n_pos": pos, "n_neg": neg}
+
+    def values(self, out, stream=None):
+        """Copy the walkers' current R into `out` (float64 tensor or array of S)."""
+        _check(load_library().cos_mc_values(self._h, _ptr(out), _stream_handle(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().cos_mc_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

@@ -807,6 +807,9 @@ int graph_view(cos_graph_t g, GraphView* out) {
     out->ptab = g->d_ptab;
     out->ptab_T = g->ptab_T;
     out->ptab_tau_max = g->ptab_tau_max;
+    out->t = g->t_borrowed ? const_cast<double*>(g->t_borrowed) : g->d_t;
+    out->t_ld = g->t_ld;
+    out->beta = g->beta;
     return COS_OK;
 }
 

@@ -98,6 +98,9 @@ struct GraphView {
     const double* ptab;           // tabulated propagators (see WalkParams), or nullptr
     double ptab_tau_max;
     int32_t ptab_T;
+    double* t;                    // attached times [D][t_ld] (the handle's or the caller's borrowed buffer)
+    int64_t t_ld;
+    double beta;
 };
 int graph_view(cos_graph_t g, GraphView* out);
 // Resolve the launch tuning of `mode` (fields of `force` > 0 override the graph's own

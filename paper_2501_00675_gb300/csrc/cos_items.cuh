@@ -49,6 +49,23 @@ __device__ __forceinline__ unsigned ld_acquire_gpu_u32(const unsigned* p) {
     return v;
 }
 
+// Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): counter (c0..c3),
+// key (k0, k1); each round multiplies c0 and c2 by the round constants and mixes the
+// high halves with c1, c3 and the key, which advances by the Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
 // ---------------------------------------------------------------- vector access
 
 template <typename T, int V>
