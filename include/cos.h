@@ -247,12 +247,18 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *                     1..L-1, continuing into the same window of the next tile) and
  *                     the chains are issued in wavefront order, so about L windows
  *                     are in flight.  Results are bitwise the same either way.
- *                     Automatic: 2 in FP64 mode or when the widest level has at
- *                     least 65536 nodes, else 1.  Batched launches always use the
+ *                     Automatic: 2 in FP64 mode with at least 1e9 edge x samples
+ *                     or when the widest level has at least 65536 nodes, else 1.
+ *                     Batched launches always use the
  *                     work queue, with windows when window_chunks > 0.
  *   window_chunks     chunks (of 32*samples_per_lane samples, 32 in the grouped
  *                     layout) per window of the work-queue schedule; automatic: one
  *                     window per tile
+ *   prefetch          wide layout: 1 = off; 2 = on levels whose parent slice per
+ *                     chunk (previous level's width x chunk samples x value size)
+ *                     exceeds 32 MB, i.e. does not stay in L2 (automatic); 3 = on
+ *                     every level.  When on, each warp issues an L2 prefetch of the
+ *                     next 4 edges' parent runs while it loads the current 4.
  */
 typedef struct cos_tuning {
     int32_t samples_per_lane;
@@ -263,6 +269,7 @@ typedef struct cos_tuning {
     int32_t layout;
     int32_t schedule;
     int32_t window_chunks;
+    int32_t prefetch;
 } cos_tuning;
 
 int cos_set_tuning(cos_graph_t g, const cos_tuning* tuning);

@@ -53,7 +53,7 @@ class CosTuning(ctypes.Structure):
     _fields_ = [("samples_per_lane", ctypes.c_int32), ("tile_samples", ctypes.c_int32),
                 ("rows_per_warp", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int32), ("layout", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("window_chunks", ctypes.c_int32)]
+                ("window_chunks", ctypes.c_int32), ("prefetch", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -213,9 +213,9 @@ class Graph:
         return mean.value
 
     def set_tuning(self, samples_per_lane=0, tile_samples=0, rows_per_warp=0, blocks_per_sm=0, timeout_ms=0,
-                   layout=0, schedule=0, window_chunks=0):
+                   layout=0, schedule=0, window_chunks=0, prefetch=0):
         t = CosTuning(samples_per_lane, tile_samples, rows_per_warp, blocks_per_sm, timeout_ms, layout, schedule,
-                      window_chunks)
+                      window_chunks, prefetch)
         _check(load_library().cos_set_tuning(self._h, ctypes.byref(t)))
 
     def set_propagator_table(self, tables, tau_max: float = 0.0):
@@ -306,9 +306,9 @@ class Batch:
         self.n = n
 
     def set_tuning(self, samples_per_lane=0, tile_samples=0, rows_per_warp=0, blocks_per_sm=0, timeout_ms=0,
-                   layout=0, schedule=0, window_chunks=0):
+                   layout=0, schedule=0, window_chunks=0, prefetch=0):
         t = CosTuning(samples_per_lane, tile_samples, rows_per_warp, blocks_per_sm, timeout_ms, layout, schedule,
-                      window_chunks)
+                      window_chunks, prefetch)
         _check(load_library().cos_batch_set_tuning(self._h, ctypes.byref(t)))
 
     def get_tuning(self) -> dict:

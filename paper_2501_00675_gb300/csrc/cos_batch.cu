@@ -428,6 +428,7 @@ int plan(cos_batch* b) {
     b->resolved.layout = force.layout;
     b->resolved.schedule = force.window_chunks > 0 ? 2 : 1;
     b->resolved.window_chunks = force.window_chunks;
+    b->resolved.prefetch = first.prefetch;
     const void* k = select_batch_kernel(mode, b->resolved.samples_per_lane, b->resolved.layout);
     if (!k) return set_error(COS_ERR_INVALID, "no batch kernel for samples_per_lane %d", b->resolved.samples_per_lane);
     int dmax = 1;
@@ -578,6 +579,7 @@ int cos_batch_set_tuning(cos_batch_t b, const cos_tuning* t) {
     if (t->rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
     if (t->layout < 0 || t->layout > 3) return set_error(COS_ERR_INVALID, "layout must be 0, 1, 2 or 3");
     if (t->window_chunks < 0) return set_error(COS_ERR_INVALID, "window_chunks must be >= 0");
+    if (t->prefetch < 0 || t->prefetch > 3) return set_error(COS_ERR_INVALID, "prefetch must be 0..3");
     b->tuning = *t;
     b->planned = false;
     return COS_OK;

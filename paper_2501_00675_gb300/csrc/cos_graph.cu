@@ -470,6 +470,8 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
     if (t->schedule < 0 || t->schedule > 2)
         return fail(COS_ERR_INVALID, "schedule must be 0 (auto), 1 (level-synchronous) or 2 (windowed)");
     if (t->window_chunks < 0) return fail(COS_ERR_INVALID, "window_chunks must be >= 0");
+    if (t->prefetch < 0 || t->prefetch > 3)
+        return fail(COS_ERR_INVALID, "prefetch must be 0 (auto), 1 (off), 2 (large parent slices) or 3 (always)");
     g->tuning = *t;
     return COS_OK;
 }
@@ -478,9 +480,11 @@ static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* til
     cos_tuning t = g->tuning;
     if (t.samples_per_lane <= 0) t.samples_per_lane = default_vec(mode);
     // Measured on GB300: the work queue (dynamic item assignment, dependency counters)
-    // is ahead in FP64 and on graphs with very wide levels; the cooperative kernel on
-    // the smaller FP32 and count walks.
-    if (t.schedule <= 0) t.schedule = (mode == COS_MODE_FP64 || g->Wmax >= 65536) ? 2 : 1;
+    // is ahead on large FP64 walks and on graphs with very wide levels; the cooperative
+    // kernel on the FP32 and count walks of smaller graphs and on small evaluations,
+    // where the work queue's per-call planning and upload are not amortised.
+    if (t.schedule <= 0)
+        t.schedule = ((mode == COS_MODE_FP64 && (double)g->E * (double)g->S >= 1e9) || g->Wmax >= 65536) ? 2 : 1;
     if (t.rows_per_warp <= 0) t.rows_per_warp = t.schedule == 2 ? 31 : (mode == COS_MODE_FP64 ? 4 : 16);
     if (t.layout <= 0) t.layout = 1;
     if (t.timeout_ms <= 0) {
@@ -512,6 +516,7 @@ static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* til
     t.tile_samples = (int32_t)tile;
     // one window per tile unless asked: smaller windows (kept in L2) measured slower
     if (t.window_chunks <= 0) t.window_chunks = (int32_t)(tile / ch);
+    if (t.prefetch <= 0) t.prefetch = 2;
     *out = t;
     *tile_out = tile;
     return COS_OK;
@@ -826,6 +831,7 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
         if (force->blocks_per_sm > 0) g->tuning.blocks_per_sm = force->blocks_per_sm;
         if (force->timeout_ms > 0) g->tuning.timeout_ms = force->timeout_ms;
         if (force->layout > 0) g->tuning.layout = force->layout;
+        if (force->prefetch > 0) g->tuning.prefetch = force->prefetch;
     }
     cos_tuning tn;
     int64_t tile;
@@ -864,6 +870,7 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
     p.tile = tile;
     p.rows_per_warp = tn.rows_per_warp;
     p.wmax = (int32_t)g->Wmax;
+    p.pf_slice_bytes = tn.prefetch == 1 ? INT64_MAX : tn.prefetch == 3 ? 0 : ((int64_t)32 << 20);
     p.ptab = g->d_ptab;
     p.ptab_T = g->ptab_T;
     p.ptab_tau_max = g->ptab_tau_max;

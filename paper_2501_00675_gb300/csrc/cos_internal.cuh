@@ -74,6 +74,7 @@ struct WalkParams {
     double ptab_inv_h;           // T / tau_max
     int32_t ptab_T;
     int32_t pad3;
+    int64_t pf_slice_bytes;      // wide layout: L2-prefetch parents on levels whose parent slice per chunk exceeds this
 };
 
 constexpr int kThreads = 256;           // 8 warps per CTA

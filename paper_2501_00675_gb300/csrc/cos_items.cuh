@@ -657,6 +657,8 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
     const Val* pc = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * p.wmax * CHV + off;
     Val* child = static_cast<Val*>(p.slab[l & 1]);
     const Prop* gc = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV + off;
+    // levels whose parent slice per chunk is too large for L2 to keep: prefetch ahead
+    const bool pf = (int64_t)ld.prev_width * (int64_t)(CHV * sizeof(Val)) > p.pf_slice_bytes;
     const int r0 = rb * rows_per_item + warp * rpw;
     if (r0 >= ld.width) return;
     const int nr = min(rpw, ld.width - r0);
@@ -690,6 +692,16 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
         const unsigned ends = __reduce_or_sync(
             0xffffffffu, (lane < nr && rp_next > rp && pos >= 0 && pos < 32) ? (1u << pos) : 0u);
         for (int q0 = 0; q0 < n; q0 += U) {
+            if (pf) {   // L2 prefetch of the next U edges' parent runs, one lane per 128-byte line
+                constexpr int LPL = (128 / (int)(sizeof(Val) * V)) - 1;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int qn = q0 + U + u;
+                    const int sn = __shfl_sync(0xffffffffu, meta.x, qn & 31);
+                    if (qn < n && (lane & LPL) == 0)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(pc + (int64_t)sn * CHV));
+                }
+            }
             VecT<Val, V> pv[U];
             VecT<Prop, V> gv[U];
 #pragma unroll

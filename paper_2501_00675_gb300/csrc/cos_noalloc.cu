@@ -14,6 +14,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cstdint>
+
 #include "cos_internal.cuh"
 
 namespace cosgpu {
@@ -128,6 +130,7 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     p.tile = tile;
     p.rows_per_warp = 1;
     p.wmax = (int32_t)gv.Wmax;
+    p.pf_slice_bytes = INT64_MAX;   // 32-sample chunks: every parent slice is small
     p.ptab = gv.ptab;
     p.ptab_T = gv.ptab_T;
     p.ptab_tau_max = gv.ptab_tau_max;
