@@ -429,6 +429,14 @@ __device__ __forceinline__ int prop_items(const WalkParams& p, const TileCtx& tc
     return tc.nch * p.K;
 }
 
+// Integer key of a time whose signed 64-bit order is the order of the doubles
+// (non-NaN; -0 taken as +0), so that the branch test t_i >= t_j of every slot and
+// sample runs on the integer pipes instead of GB300's slow FP64 pipe.
+__device__ __forceinline__ long long time_order_key(double t) {
+    const long long b = __double_as_longlong(t + 0.0);   // -0 + 0 = +0
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+
 // Shared memory of one propagator item: times and exponentials of the chunk's samples.
 __host__ __device__ constexpr int prop_smem_bytes(int D, int chv) { return 4 * 8 * D * chv; }
 
@@ -504,7 +512,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
         // GB300's slow FP64 pipe.
         bool use_ff = (MODE == COS_MODE_FP32_MIXED && fabs(eps) * p.beta <= 30.0);
         if (use_ff) {
-            double* st = sm;                                              // [D][CHV] times
+            long long* sk = reinterpret_cast<long long*>(sm);             // [D][CHV] time order keys
             float2* fp_ = reinterpret_cast<float2*>(sm + CHV * D);        // [D][CHV] coef+ e^{-eps t}
             float2* fn_ = fp_ + CHV * D;                                  // [D][CHV] coef- e^{-eps t}
             float2* fe_ = fn_ + CHV * D;                                  // [D][CHV] e^{+eps t}
@@ -521,7 +529,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                 }
                 float2 em, ep;
                 exp_pair_ff(arg, tff, em, ep);
-                st[x] = t;
+                sk[x] = time_order_key(t);
                 fp_[x] = mul_ff2(cp2, em);
                 fn_[x] = mul_ff2(cn2, em);
                 fe_[x] = ep;
@@ -535,7 +543,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
 #pragma unroll
                     for (int v = 0; v < CHV / 32; ++v) {
                         const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
-                        const float2 a = (st[xi] >= st[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
+                        const float2 a = (sk[xi] >= sk[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
                         __stcg(reinterpret_cast<float*>(gt) + (int64_t)q * CHV + v * 32 + lane,
                                __uint_as_float(__float_as_uint(mul_ff(a, fe_[xj])) ^ smask));
                     }
@@ -543,7 +551,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
             }
         }
         if (!use_ff) {
-            double* st = sm;                  // [D][CHV] times
+            long long* sk = reinterpret_cast<long long*>(sm);   // [D][CHV] time order keys
             double* sp = sm + CHV * D;        // [D][CHV] coef+ e^{-eps t}
             double* sn = sm + 2 * CHV * D;    // [D][CHV] coef- e^{-eps t}
             double* se = sm + 3 * CHV * D;    // [D][CHV] e^{+eps t}
@@ -552,7 +560,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                 const double t = p.t[(int64_t)i * p.t_ld + s0 + s];
                 double em, ep;
                 exp_pair(eps * t, p.exp_tab, em, ep);
-                st[x] = t;
+                sk[x] = time_order_key(t);
                 sp[x] = cpos * em;
                 sn[x] = cneg * em;
                 se[x] = ep;
@@ -566,7 +574,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
 #pragma unroll
                 for (int v = 0; v < CHV / 32; ++v) {
                     const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
-                    const double a = (st[xi] >= st[xj]) ? sp[xi] : sn[xi];   // tau = t_i - t_j >= 0 ?
+                    const double a = (sk[xi] >= sk[xj]) ? sp[xi] : sn[xi];   // tau = t_i - t_j >= 0 ?
                     const double g = __longlong_as_double(__double_as_longlong(a * se[xj]) ^ smask);
                     __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
                 }
