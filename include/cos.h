@@ -252,8 +252,8 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *                     Batched launches always use the
  *                     work queue, with windows when window_chunks > 0.
  *   window_chunks     chunks (of 32*samples_per_lane samples, 32 in the grouped
- *                     layout) per window of the work-queue schedule; automatic: one
- *                     window per tile
+ *                     layout) per window of the work-queue schedule; automatic: a
+ *                     quarter of a tile's chunks (four windows per tile)
  *   prefetch          wide layout: 1 = off; 2 = on levels whose parent slice per
  *                     chunk (previous level's width x chunk samples x value size)
  *                     exceeds 32 MB, i.e. does not stay in L2 (automatic); 3 = on
