@@ -77,6 +77,13 @@ __global__ void mc_accept_kernel(double* __restrict__ t, long long t_ld, long lo
     }
 }
 
+// A step whose evaluation could not be launched: every walker takes its old time back.
+__global__ void mc_restore_kernel(double* __restrict__ t, long long t_ld, long long S,
+                                  const double* __restrict__ old_val, const int* __restrict__ old_i) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (long long)gridDim.x * blockDim.x)
+        t[(long long)old_i[s] * t_ld + s] = old_val[s];
+}
+
 int grid_for(long long S) {
     const long long b = (S + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
@@ -178,7 +185,10 @@ int cos_mc_run(cos_mc_t m, int32_t num_steps, void* stream) {
             break;
         }
         rc = cos_evaluate(m->g, m->mode, m->Rp, nullptr, stream);
-        if (rc != COS_OK) break;
+        if (rc != COS_OK) {   // leave the walkers where they were
+            mc_restore_kernel<<<grid, 256, 0, st>>>(gv.t, gv.t_ld, m->S, m->old_val, m->old_i);
+            break;
+        }
         mc_accept_kernel<<<grid, 256, 0, st>>>(gv.t, gv.t_ld, m->S, m->seed, m->step, m->Rp, m->R, m->old_val,
                                                 m->old_i, m->tallies);
         e = cudaGetLastError();
