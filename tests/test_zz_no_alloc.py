@@ -94,3 +94,19 @@ def test_static_rejects_graphs_beyond_the_scratch_limit(cg):
     assert rc == cg.COS_ERR_INVALID
     assert b"static scratch" in cg.load_library().cos_last_error()
     gr.close()
+
+
+def test_static_uses_the_handles_propagator_tables(cg):
+    # tables set on the handle (cos_set_propagator_table) apply to the static entry too
+    wl = tiny(num_samples=600)
+    g, s = wl.graph, wl.samples
+    rng = np.random.default_rng(31)
+    tables = 0.5 * np.tanh(rng.normal(size=(g.num_kinds, 2, 17)))
+    R, A = oracle.evaluate_tabulated(g, tables, 9.0, s.t)
+    gr = cg.Graph.from_workload_graph(g)
+    gr.set_propagator_table(tables, 9.0)
+    for mode in (0, 1):
+        rc, r_static, _ = _static(cg, gr, mode, s.t, s.eps, s.beta)
+        assert rc == cg.COS_OK, cg.load_library().cos_last_error()
+        assert np.all(np.abs(r_static - R) <= TOL[mode] * A)
+    gr.close()
