@@ -123,19 +123,33 @@ def tabulated_propagator(table: np.ndarray, tau_max: float, tau) -> np.ndarray:
     the free propagator, decided by t_i >= t_j); table[1] holds the values at
     tau_m = -tau_max + m*h, used for tau < 0.  Between nodes the value is the
     linear interpolation of its two neighbours; outside [-tau_max, tau_max] the end
-    value.  Two halves keep the jump at tau = 0 (G(0+) - G(0-) = -1 for fermions)."""
+    value.  Two halves keep the jump at tau = 0 (G(0+) - G(0-) = -1 for fermions).
+
+    The arithmetic is fixed, each step rounded once in double: inv_h = T / tau_max,
+    u = tau * inv_h (plus T below zero), m = floor(u) (0 with f = 0 below the grid,
+    T - 1 with f = 1 at or past its end), f = u - m, G = a_m + f * (a_{m+1} - a_m);
+    near zero-crossings of G the position error of any other rounding order would
+    show up relative to G."""
     table = np.asarray(table, dtype=np.float64)
     if table.ndim != 2 or table.shape[0] != 2 or table.shape[1] < 2:
         raise ValueError("table must be [2, T+1] with T >= 1")
     T = table.shape[1] - 1
     tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
     pos = tau >= 0.0
-    out = np.empty_like(tau)
-    xs_pos = np.arange(T + 1) * (tau_max / T)
-    xs_neg = -tau_max + np.arange(T + 1) * (tau_max / T)
-    out[pos] = np.interp(tau[pos], xs_pos, table[0])
-    out[~pos] = np.interp(tau[~pos], xs_neg, table[1])
-    return out
+    inv_h = float(T) / float(tau_max)
+    u = tau * inv_h
+    u = np.where(pos, u, u + float(T))
+    below = u < 0.0
+    m = np.floor(np.where(below, 0.0, u)).astype(np.int64)
+    f = u - m
+    past = (~below) & (m >= T)
+    m = np.where(below, 0, np.where(past, T - 1, m))
+    f = np.where(below, 0.0, np.where(past, 1.0, f))
+    half = np.where(pos[:, None], table[0][None, :], table[1][None, :])
+    rows = np.arange(tau.size)
+    a = half[rows, m]
+    slope = half[rows, m + 1] - a
+    return a + f * slope
 
 
 def tabulated_edge_weights(graph, tables: np.ndarray, tau_max: float, t_sample: np.ndarray) -> np.ndarray:

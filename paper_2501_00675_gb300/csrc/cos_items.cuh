@@ -486,10 +486,12 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                 for (int v = 0; v < CHV / 32; ++v) {
                     const double tau = st[i * CHV + v * 32 + lane] - st[j * CHV + v * 32 + lane];
                     const bool pos = tau >= 0.0;
-                    // grid coordinate: tau/h on the tau >= 0 half, (tau + tau_max)/h = tau/h + T below
-                    const double u = fma(tau, p.ptab_inv_h, pos ? 0.0 : (double)T);
+                    // grid coordinate: tau/h on the tau >= 0 half, (tau + tau_max)/h = tau/h + T
+                    // below; every step rounded once (no contraction), so that the position in
+                    // the interval is the same on every implementation of the definition
+                    const double u = __dadd_rn(__dmul_rn(tau, p.ptab_inv_h), pos ? 0.0 : (double)T);
                     int m = (int)u;
-                    double f = u - (double)m;
+                    double f = __dsub_rn(u, (double)m);
                     if (u < 0.0) {   // before the grid: the first node's value
                         m = 0;
                         f = 0.0;
@@ -498,7 +500,8 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                         f = 1.0;
                     }
                     const double2 as = __ldg(tk + (pos ? 0 : T) + m);
-                    const double g = __longlong_as_double(__double_as_longlong(fma(f, as.y, as.x)) ^ smask);
+                    const double g =
+                        __longlong_as_double(__double_as_longlong(__dadd_rn(as.x, __dmul_rn(f, as.y))) ^ smask);
                     __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
                 }
             }

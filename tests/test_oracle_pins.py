@@ -344,3 +344,18 @@ def test_tabulated_sign_flags_on_one_level_negate_every_path():
     R1, A1 = oracle.evaluate_tabulated(_with_signs(g, lvl == 3), tables, 10.0, t)
     np.testing.assert_array_equal(R1, -R0)
     np.testing.assert_array_equal(A1, A0)
+
+
+def test_tabulated_formula_agrees_with_library_interpolation():
+    # the fixed arithmetic of the definition against numpy's linear interpolation:
+    # they differ only by the rounding of the position in the interval
+    rng = np.random.default_rng(16)
+    T, tau_max = 23, 9.0
+    tab = rng.normal(size=(2, T + 1))
+    tau = rng.uniform(-11.0, 11.0, 20000)
+    got = oracle.tabulated_propagator(tab, tau_max, tau)
+    xs = np.arange(T + 1) * (tau_max / T)
+    pos = tau >= 0
+    want = np.where(pos, np.interp(tau, xs, tab[0]), np.interp(tau, xs - tau_max, tab[1]))
+    slope = np.max(np.abs(np.diff(tab, axis=1))) * T / tau_max
+    assert np.max(np.abs(got - want)) <= 8 * np.finfo(float).eps * (11.0 * slope + np.max(np.abs(tab)))
