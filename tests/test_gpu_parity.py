@@ -498,3 +498,20 @@ def test_tabulated_propagator_signs_share_reset_and_errors(cg):
     gr.evaluate(0, out=out)
     np.testing.assert_array_equal(out.cpu().numpy(), analytic.cpu().numpy())
     gr.close()
+
+
+def test_renumbered_wide_levels_match_the_oracle(cg):
+    # levels after a parent level of >= 65536 nodes are renumbered at ingest by their
+    # smallest parent; the renumbering must not show in any result
+    rng = np.random.default_rng(33)
+    g = make_graph([1, 200, 70000, 70000, 300, 1], FaninSpec("uniform", 3), 4, 5, rng)
+    t = rng.uniform(0, 10, (96, 5))
+    eps = rng.uniform(-2, 2, 4)
+    R, A = oracle.evaluate(g, eps, 10.0, t)
+    for mode in (0, 1):
+        for tuning in ({"schedule": 1}, {"schedule": 2}):
+            Rg, mg = run_gpu(cg, g, eps, 10.0, t, mode, tuning)
+            check_fp(Rg, mg, R, A, mode)
+    cnt, _ = oracle.count_paths(g)
+    Rg, _ = run_gpu(cg, g, eps, 10.0, t, 2)
+    assert np.all(Rg == cnt)
