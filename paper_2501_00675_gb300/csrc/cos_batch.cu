@@ -126,7 +126,11 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V>()) batch_k
             case TK_COEF: item_coef(p); break;
             case TK_PROP: item_props<MODE, CHV>(p, tc, item, smem); break;
             case TK_LEVEL:
-                if (!item_level<MODE, V, LAYOUT>(p, tk.level, tc, item, reinterpret_cast<unsigned char*>(smem)) &&
+                // FP64 items are long and bound by the FP64 pipe: balance their warps' edges
+                // (medium 6.56 -> 6.47 ms); the short memory-bound items of the other modes
+                // lose more to the row-pointer search than they gain (large mixed +7 %)
+                if (!item_level<MODE, V, LAYOUT, MODE == COS_MODE_FP64>(p, tk.level, tc, item,
+                                                                       reinterpret_cast<unsigned char*>(smem)) &&
                     (threadIdx.x & 31) == 0) {   // a bounded wait gave up: report it for the whole launch
                     const int code = *(volatile int*)&p.ctrl->err;
                     if (atomicCAS(&a.ctrl->err, 0, code ? code : KERR_BARRIER_TIMEOUT) == 0)

@@ -648,7 +648,7 @@ __device__ __forceinline__ void sink_row_mixed(const WalkParams& p, const float*
 // propagator loads in flight, and closes a row (store, reset) at its last in-edge.
 // Every row is the sum of its in-edges in CSR order, one multiply-add per edge per
 // sample.
-template <int MODE, int V>
+template <int MODE, int V, bool BALANCE = false>
 __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, const TileCtx& tc, int item) {
     using Tr = Traits<MODE>;
     using Val = typename Tr::Val;
@@ -670,81 +670,107 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
     const Prop* gc = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV + off;
     // levels whose parent slice per chunk is too large for L2 to keep: prefetch ahead
     const bool pf = (int64_t)ld.prev_width * (int64_t)(CHV * sizeof(Val)) > p.pf_slice_bytes;
-    const int r0 = rb * rows_per_item + warp * rpw;
-    if (r0 >= ld.width) return;
-    const int nr = min(rpw, ld.width - r0);
-    if constexpr (MODE == COS_MODE_FP32_MIXED) {
-        if (sink) {
-            for (int r = r0; r < r0 + nr; ++r) {
-                const int node = ld.row_begin + r;
-                sink_row_mixed<V, CHV>(p, pc, gc, __ldg(p.row_ptr + node), __ldg(p.row_ptr + node + 1), c, tc, off);
+    // rows [r0, r0 + nr) of the item, nr <= 31, summed by this warp in CSR order
+    auto do_rows = [&](const int r0, const int nr) {
+        if constexpr (MODE == COS_MODE_FP32_MIXED) {
+            if (sink) {
+                for (int r = r0; r < r0 + nr; ++r) {
+                    const int node = ld.row_begin + r;
+                    sink_row_mixed<V, CHV>(p, pc, gc, __ldg(p.row_ptr + node), __ldg(p.row_ptr + node + 1), c, tc, off);
+                }
+                return;
             }
-            return;
         }
-    }
-    // lane j <= nr holds rp_j = row_ptr of row r0 + j
-    const int rp = (lane <= nr) ? __ldg(p.row_ptr + ld.row_begin + r0 + lane) : 0;
-    const int rp_next = __shfl_down_sync(0xffffffffu, rp, 1);
-    const int beg = __shfl_sync(0xffffffffu, rp, 0);
-    const int end = __shfl_sync(0xffffffffu, rp, nr);
-    const unsigned nonempty = __ballot_sync(0xffffffffu, lane < nr && rp_next > rp);
-    const unsigned empty = __ballot_sync(0xffffffffu, lane < nr && rp_next == rp);
-    Val acc[V];
+        // lane j <= nr holds rp_j = row_ptr of row r0 + j
+        const int rp = (lane <= nr) ? __ldg(p.row_ptr + ld.row_begin + r0 + lane) : 0;
+        const int rp_next = __shfl_down_sync(0xffffffffu, rp, 1);
+        const int beg = __shfl_sync(0xffffffffu, rp, 0);
+        const int end = __shfl_sync(0xffffffffu, rp, nr);
+        const unsigned nonempty = __ballot_sync(0xffffffffu, lane < nr && rp_next > rp);
+        const unsigned empty = __ballot_sync(0xffffffffu, lane < nr && rp_next == rp);
+        Val acc[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = (Val)0;
-    for (unsigned m = empty; m; m &= m - 1)   // rows without in-edges hold 0
-        store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(m) - 1, tc, off, acc);
-    unsigned rows_left = nonempty;
-    for (int w0 = beg; w0 < end; w0 += 32) {
-        const int n = min(32, end - w0);
-        const int2 meta = (lane < n) ? __ldg(p.edges + w0 + lane) : make_int2(0, 0);
-        // bit q set <=> edge w0+q is the last in-edge of its row
-        const int pos = rp_next - 1 - w0;
-        const unsigned ends = __reduce_or_sync(
-            0xffffffffu, (lane < nr && rp_next > rp && pos >= 0 && pos < 32) ? (1u << pos) : 0u);
-        for (int q0 = 0; q0 < n; q0 += U) {
-            if (pf) {   // L2 prefetch of the next U edges' parent runs, one lane per 128-byte line
-                constexpr int LPL = (128 / (int)(sizeof(Val) * V)) - 1;
+        for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+        for (unsigned m = empty; m; m &= m - 1)   // rows without in-edges hold 0
+            store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(m) - 1, tc, off, acc);
+        unsigned rows_left = nonempty;
+        for (int w0 = beg; w0 < end; w0 += 32) {
+            const int n = min(32, end - w0);
+            const int2 meta = (lane < n) ? __ldg(p.edges + w0 + lane) : make_int2(0, 0);
+            // bit q set <=> edge w0+q is the last in-edge of its row
+            const int pos = rp_next - 1 - w0;
+            const unsigned ends = __reduce_or_sync(
+                0xffffffffu, (lane < nr && rp_next > rp && pos >= 0 && pos < 32) ? (1u << pos) : 0u);
+            for (int q0 = 0; q0 < n; q0 += U) {
+                if (pf) {   // L2 prefetch of the next U edges' parent runs, one lane per 128-byte line
+                    constexpr int LPL = (128 / (int)(sizeof(Val) * V)) - 1;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int qn = q0 + U + u;
+                        const int sn = __shfl_sync(0xffffffffu, meta.x, qn & 31);
+                        if (qn < n && (lane & LPL) == 0)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(pc + (int64_t)sn * CHV));
+                    }
+                }
+                VecT<Val, V> pv[U];
+                VecT<Prop, V> gv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int qn = q0 + U + u;
-                    const int sn = __shfl_sync(0xffffffffu, meta.x, qn & 31);
-                    if (qn < n && (lane & LPL) == 0)
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(pc + (int64_t)sn * CHV));
-                }
-            }
-            VecT<Val, V> pv[U];
-            VecT<Prop, V> gv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int q = q0 + u;
-                const int src = __shfl_sync(0xffffffffu, meta.x, q & 31);
-                pv[u] = load_cg<Val, V>(pc + (int64_t)(q < n ? src : 0) * CHV);
-                if constexpr (!Tr::kCount) {
-                    const int slot = __shfl_sync(0xffffffffu, meta.y, q & 31);
-                    gv[u] = load_ca<Prop, V>(gc + (int64_t)(q < n ? slot : 0) * CHV);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int q = q0 + u;
-                if (q < n) {
-                    if constexpr (Tr::kCount) {
-#pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v] += pv[u].v[v];
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v] = madd(pv[u].v[v], gv[u].v[v], acc[v]);
+                    const int q = q0 + u;
+                    const int src = __shfl_sync(0xffffffffu, meta.x, q & 31);
+                    pv[u] = load_cg<Val, V>(pc + (int64_t)(q < n ? src : 0) * CHV);
+                    if constexpr (!Tr::kCount) {
+                        const int slot = __shfl_sync(0xffffffffu, meta.y, q & 31);
+                        gv[u] = load_ca<Prop, V>(gc + (int64_t)(q < n ? slot : 0) * CHV);
                     }
-                    if ((ends >> q) & 1u) {
-                        store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(rows_left) - 1, tc, off, acc);
-                        rows_left &= rows_left - 1;
+                }
 #pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+                for (int u = 0; u < U; ++u) {
+                    const int q = q0 + u;
+                    if (q < n) {
+                        if constexpr (Tr::kCount) {
+#pragma unroll
+                            for (int v = 0; v < V; ++v) acc[v] += pv[u].v[v];
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < V; ++v) acc[v] = madd(pv[u].v[v], gv[u].v[v], acc[v]);
+                        }
+                        if ((ends >> q) & 1u) {
+                            store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(rows_left) - 1, tc, off, acc);
+                            rows_left &= rows_left - 1;
+#pragma unroll
+                            for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+                        }
                     }
                 }
             }
         }
+    };
+    if constexpr (BALANCE) {
+        // work-queue items end at a block barrier: split the item's rows into one
+        // contiguous range per warp with about the same number of in-edges (rows stay
+        // whole), found by binary search on the row pointers
+        const int ir0 = rb * rows_per_item, ir1 = min(ir0 + rows_per_item, ld.width);
+        const int32_t* rp_item = p.row_ptr + ld.row_begin;
+        const int e0 = __ldg(rp_item + ir0), e1 = __ldg(rp_item + ir1);
+        auto bound = [&](const int w) {   // first row whose CSR start reaches warp w's share
+            if (w <= 0) return ir0;
+            if (w >= kWarps) return ir1;
+            const int target = e0 + (int)((long long)w * (e1 - e0) / kWarps);
+            int lo = ir0, hi = ir1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(rp_item + mid) < target) lo = mid + 1;
+                else hi = mid;
+            }
+            return lo;
+        };
+        const int ra = bound(warp), rz = bound(warp + 1);
+        for (int r0 = ra; r0 < rz; r0 += 31) do_rows(r0, min(31, rz - r0));
+    } else {
+        const int r0 = rb * rows_per_item + warp * rpw;
+        if (r0 >= ld.width) return;
+        do_rows(r0, min(rpw, ld.width - r0));
     }
 }
 
@@ -1014,11 +1040,11 @@ __device__ __forceinline__ bool item_level_bulk(const WalkParams& p, int l, cons
     return true;
 }
 
-template <int MODE, int V, int LAYOUT>
+template <int MODE, int V, int LAYOUT, bool BALANCE = false>
 __device__ __forceinline__ bool item_level(const WalkParams& p, int l, const TileCtx& tc, int item,
                                            unsigned char* smem) {
     if constexpr (LAYOUT == LAYOUT_BULK) return item_level_bulk<MODE, V>(p, l, tc, item, smem);
-    if constexpr (LAYOUT == LAYOUT_WIDE) item_level_wide<MODE, V>(p, l, tc, item);
+    if constexpr (LAYOUT == LAYOUT_WIDE) item_level_wide<MODE, V, BALANCE>(p, l, tc, item);
     else item_level_grouped<MODE, V>(p, l, tc, item);
     return true;
 }
