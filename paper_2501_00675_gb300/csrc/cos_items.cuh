@@ -749,23 +749,26 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
     if constexpr (BALANCE) {
         // work-queue items end at a block barrier: split the item's rows into one
         // contiguous range per warp with about the same number of in-edges (rows stay
-        // whole), found by binary search on the row pointers
+        // whole).  Warp w's range starts at the first row whose CSR start reaches
+        // e0 + w (e1 - e0) / 8; the warp finds both of its ends in two rounds of
+        // loads: every 8th row of the item (at most 31 x 8 rows), then the 8 rows of
+        // the block the first round points at.
         const int ir0 = rb * rows_per_item, ir1 = min(ir0 + rows_per_item, ld.width);
         const int32_t* rp_item = p.row_ptr + ld.row_begin;
         const int e0 = __ldg(rp_item + ir0), e1 = __ldg(rp_item + ir1);
-        auto bound = [&](const int w) {   // first row whose CSR start reaches warp w's share
-            if (w <= 0) return ir0;
-            if (w >= kWarps) return ir1;
-            const int target = e0 + (int)((long long)w * (e1 - e0) / kWarps);
-            int lo = ir0, hi = ir1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (__ldg(rp_item + mid) < target) lo = mid + 1;
-                else hi = mid;
-            }
-            return lo;
-        };
-        const int ra = bound(warp), rz = bound(warp + 1);
+        const int ta = e0 + (int)((long long)warp * (e1 - e0) / kWarps);
+        const int tz = e0 + (int)((long long)(warp + 1) * (e1 - e0) / kWarps);
+        const int v1 = __ldg(rp_item + min(ir0 + 8 * lane, ir1));       // rp is non-decreasing; rp[ir1] = e1
+        const int fa = __ffs(__ballot_sync(0xffffffffu, v1 >= ta)) - 1;  // first block start at or past ta
+        const int fz = __ffs(__ballot_sync(0xffffffffu, v1 >= tz)) - 1;
+        const int ba = ir0 + 8 * (fa - 1), bz = ir0 + 8 * (fz - 1);      // the end lies in (b, b + 8]
+        const int q = lane & 7;
+        // (an end decided by the first round, f = 0, leaves b = ir0 - 8: keep the load inside the item)
+        const int v2 = __ldg(rp_item + min(max((lane < 8 ? ba : bz) + 1 + q, ir0), ir1));
+        const unsigned ma = __ballot_sync(0xffffffffu, lane < 8 && v2 >= ta) & 0xffu;
+        const unsigned mz = (__ballot_sync(0xffffffffu, lane >= 8 && lane < 16 && v2 >= tz) >> 8) & 0xffu;
+        const int ra = warp == 0 ? ir0 : (fa == 0 ? ir0 : min(ba + __ffs(ma), ir1));
+        const int rz = warp == kWarps - 1 ? ir1 : (fz == 0 ? ir0 : min(bz + __ffs(mz), ir1));
         for (int r0 = ra; r0 < rz; r0 += 31) do_rows(r0, min(31, rz - r0));
     } else {
         const int r0 = rb * rows_per_item + warp * rpw;
