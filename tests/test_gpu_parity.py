@@ -253,6 +253,13 @@ def test_wide_fanin_duplicates_dead_and_orphan_nodes(cg):
             assert np.all(Rg == cnt)
         else:
             check_fp(Rg, mg, R, A, mode)
+    for mode in (0, 1, 2):                          # the work queue: FP64 items split their warps by edges
+        for rpw in (31, 5):
+            Rg, mg = run_gpu(cg, g2, eps, 10.0, t, mode, {"schedule": 2, "rows_per_warp": rpw})
+            if mode == 2:
+                assert np.all(Rg == cnt)
+            else:
+                check_fp(Rg, mg, R, A, mode)
 
 
 def test_count_overflow_reports_and_wraps(cg):
