@@ -275,6 +275,15 @@ typedef struct cos_tuning {
 int cos_set_tuning(cos_graph_t g, const cos_tuning* tuning);
 /* Tuning cos_evaluate will use for `mode` with the current samples (automatic fields resolved). */
 int cos_get_tuning(cos_graph_t g, int32_t mode, cos_tuning* tuning);
+/*
+ * Time launch shapes for `mode` on g's attached samples (both schedules, 8/16/31
+ * rows per warp, two vector widths; fields already set > 0 stay fixed), keep the
+ * fastest as g's tuning and, if best is non-NULL, store its resolved form there.
+ * Runs 36 evaluations at most on `stream` (writing per_sample_out, which may be
+ * NULL) and synchronizes; results are bitwise the same for every candidate.
+ * The paper has no counterpart; cos_batch_autotune does the same for batches.
+ */
+int cos_autotune(cos_graph_t g, int32_t mode, void* per_sample_out, void* stream, cos_tuning* best);
 
 /*
  * Batched evaluation of many graphs of uneven size and sample count in ONE

@@ -88,6 +88,7 @@ def load_library(build_if_missing: bool = False):
         lib.cos_evaluate_static.argtypes = [vp, i32, i64, vp, i64, vp, f64, vp, vp, vp]
         lib.cos_graph_share.argtypes = [vp, ctypes.POINTER(vp)]
         lib.cos_set_propagator_table.argtypes = [vp, i32, vp, f64]
+        lib.cos_autotune.argtypes = [vp, i32, vp, vp, ctypes.POINTER(CosTuning)]
         lib.cos_mc_create.argtypes = [vp, i32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
         lib.cos_mc_run.argtypes = [vp, i32, vp]
         lib.cos_mc_stats.argtypes = [vp, vp, vp]
@@ -231,6 +232,12 @@ class Graph:
         _check(lib.cos_set_propagator_table(self._h, int(tab.shape[2] - 1),
                                             tab.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                             ctypes.c_double(float(tau_max))))
+
+    def autotune(self, mode: int, out=None, stream=None) -> dict:
+        """cos_autotune: time launch shapes on the attached samples, keep the fastest."""
+        t = CosTuning()
+        _check(load_library().cos_autotune(self._h, int(mode), _ptr(out), _stream_handle(stream), ctypes.byref(t)))
+        return t.as_dict()
 
     def get_tuning(self, mode: int) -> dict:
         t = CosTuning()

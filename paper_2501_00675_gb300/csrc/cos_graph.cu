@@ -555,6 +555,64 @@ int cos_get_tuning(cos_graph_t g, int32_t mode, cos_tuning* tuning) {
     return resolve_tuning(g, mode, tuning, &tile);
 }
 
+int cos_autotune(cos_graph_t g, int32_t mode, void* per_sample_out, void* stream, cos_tuning* best_out) {
+    if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
+    if (mode < 0 || mode > 2) return fail(COS_ERR_INVALID, "bad mode %d", mode);
+    if (!g->has_samples) return fail(COS_ERR_STATE, "cos_set_samples has not been called");
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const cos_tuning base = g->tuning;
+    // candidates: both schedules, 8/16/31 rows per warp, the mode's two useful widths;
+    // fields the caller set (> 0) stay fixed
+    const int scheds[] = {1, 2};
+    const int rpws[] = {8, 16, 31};
+    const int vecs_fp64[] = {2, 1}, vecs_mixed[] = {4, 2}, vecs_count[] = {2, 4};
+    const int* vecs = mode == COS_MODE_FP64 ? vecs_fp64 : mode == COS_MODE_FP32_MIXED ? vecs_mixed : vecs_count;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(COS_ERR_CUDA, "cannot create timing events");
+    float best_ms = 1e30f;
+    cos_tuning best = base;
+    int rc = COS_OK;
+    for (int sc : scheds)
+        for (int r : rpws)
+            for (int vi = 0; vi < 2 && rc == COS_OK; ++vi) {
+                cos_tuning t = base;
+                if (base.schedule <= 0) t.schedule = sc;
+                else if (sc != scheds[0]) continue;
+                if (base.rows_per_warp <= 0) t.rows_per_warp = r;
+                else if (r != rpws[0]) continue;
+                if (base.samples_per_lane <= 0) t.samples_per_lane = vecs[vi];
+                else if (vi > 0) continue;
+                g->tuning = t;
+                float ms_best = 1e30f;
+                for (int rep = 0; rep < 3 && rc == COS_OK; ++rep) {   // the first run warms up
+                    cudaEventRecord(e0, st);
+                    rc = cos_evaluate(g, mode, per_sample_out, nullptr, stream);
+                    cudaEventRecord(e1, st);
+                    if (rc != COS_OK) break;
+                    rc = cos_get_result(g, nullptr, stream);
+                    if (rc == COS_ERR_OVERFLOW) rc = COS_OK;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) ms_best = std::min(ms_best, ms);
+                }
+                if (rc == COS_OK && ms_best < best_ms) {
+                    best_ms = ms_best;
+                    best = t;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->tuning = rc == COS_OK ? best : base;
+    if (rc != COS_OK) return rc;
+    if (best_out) {
+        int64_t tile;
+        return resolve_tuning(g, mode, best_out, &tile);
+    }
+    return COS_OK;
+}
+
 int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t t_flags, const double* eps,
                     double beta, void* stream) {
     if (!g) return fail(COS_ERR_INVALID, "graph is NULL");

@@ -522,3 +522,25 @@ def test_renumbered_wide_levels_match_the_oracle(cg):
     cnt, _ = oracle.count_paths(g)
     Rg, _ = run_gpu(cg, g, eps, 10.0, t, 2)
     assert np.all(Rg == cnt)
+
+
+def test_single_graph_autotune_keeps_results(cg):
+    w = medium(num_samples=3000)
+    gr = cg.Graph.from_workload_graph(w.graph)
+    gr.set_samples(torch.from_numpy(w.samples.t).cuda(), w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+    for mode in (0, 1, 2):
+        dt = torch.int64 if mode == 2 else torch.float64
+        ref = torch.empty(3000, dtype=dt, device="cuda")
+        m_ref = gr.evaluate(mode, out=ref, allow_overflow=True)
+        scratch = torch.empty_like(ref)
+        best = gr.autotune(mode, out=scratch)
+        assert best["schedule"] in (1, 2) and 1 <= best["rows_per_warp"] <= 31 and best["samples_per_lane"] in (1, 2, 4)
+        assert gr.get_tuning(mode)["rows_per_warp"] == best["rows_per_warp"]
+        out = torch.empty_like(ref)
+        m = gr.evaluate(mode, out=out, allow_overflow=True)
+        np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
+        assert m == m_ref
+        gr.set_tuning()                                # back to automatic for the next mode
+    gr.set_tuning(rows_per_warp=5)                     # fixed fields stay fixed
+    assert gr.autotune(1)["rows_per_warp"] == 5
+    gr.close()
