@@ -99,6 +99,18 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def combine_means(local_sum: float, local_count: int, world: int, device=None) -> float:
+    """The one exchange of the sample-sharded path: every rank's sample sum and count
+    summed over ranks (FP64 all-reduce), giving the mean over all ranks' samples."""
+    if world <= 1:
+        return local_sum / max(local_count, 1)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_sum, float(local_count)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t[0].item()) / max(float(t[1].item()), 1.0)
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -261,6 +273,7 @@ def run_ours(args, rank, world, local):
     barrier(world)
     clk = clocks.stop()
     mean = gr.get_result(stream) if mode != 2 else float("nan")
+    mean_all = combine_means(mean * S, S, world, dev) if mode != 2 else float("nan")   # untimed
     step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
     walk_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
     total_s = sum(step_ms) / 1e3
@@ -349,7 +362,7 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed between timed steps (512 MB write); working set larger than L2",
                    "tuning": tuning},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
-        "clocks": clk, "walk_ms_per_launch": statistics.mean(walk_ms), "mean_R": mean, "error_vs_oracle": err,
+        "clocks": clk, "walk_ms_per_launch": statistics.mean(walk_ms), "mean_R": mean, "mean_R_all_ranks": mean_all, "error_vs_oracle": err,
     }
     if other is not None:
         line["roofline_secondary"] = other

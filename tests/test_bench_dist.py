@@ -1,6 +1,6 @@
 """Host-side logic of the multi-GPU benchmark path, run as two gloo ranks on CPU:
-weak scaling gives every rank its own samples of the same graph, and the timed
-region is the maximum over ranks."""
+weak scaling gives every rank its own samples of the same graph, the timed region
+is the maximum over ranks, and the means combine over all ranks' samples."""
 import os
 import socket
 
@@ -25,8 +25,9 @@ def _worker(rank, world, port, q):
     r, w, _ = bench.dist_env()
     m = bench.max_over_ranks(float(10 * (rank + 1)), w)
     wl = tiny(seed=bench.rank_seed(0, r), num_samples=8)
+    mean = bench.combine_means([3.0, 5.0][r], [2, 6][r], w)   # (3 + 5) / (2 + 6)
     bench.barrier(w)
-    q.put((r, m, wl.samples.t.sum(), wl.graph.edges.sum()))
+    q.put((r, m, wl.samples.t.sum(), wl.graph.edges.sum(), mean))
     dist.destroy_process_group()
 
 
@@ -42,6 +43,7 @@ def test_two_rank_max_and_sample_sharding():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert [r[1] for r in res] == [20.0, 20.0]          # max over ranks seen by both
+    assert [r[4] for r in res] == [1.0, 1.0]            # mean over both ranks' samples
     assert res[0][2] != res[1][2]                        # rank samples differ (own seeds)
     assert bench.rank_seed(1, 0) == 1                    # rank 0 keeps the workload's own samples
 
