@@ -21,7 +21,8 @@
  *   - Edge factor for sample s: +-G_kind(t_{s,i} - t_{s,j}) with the free-fermion
  *     propagator G_k(tau) = -exp(-eps_k tau)/(1+exp(-beta eps_k)) for tau >= 0
  *     and G_k(tau) = -G_k(tau+beta) for tau < 0 (tau = 0 takes the first branch;
- *     the comparison is made on the double-precision times).
+ *     the comparison is made on the double-precision times), unless
+ *     cos_set_propagator_table gave the handle tables of G_k instead.
  *   - Device memory: every buffer the library allocates belongs to the graph
  *     handle and is freed by cos_destroy.  Output buffers passed in are owned by
  *     the caller.  All device work runs on the CUDA device that was current when
@@ -47,7 +48,8 @@ enum cos_status {
     COS_ERR_INVALID = -1,   /* bad argument or malformed graph; nothing was created or changed */
     COS_ERR_OOM = -2,       /* a device or host allocation failed */
     COS_ERR_CUDA = -3,      /* a CUDA runtime call failed (message in cos_last_error) */
-    COS_ERR_TIMEOUT = -4,   /* a grid barrier inside a kernel gave up waiting; results are invalid */
+    COS_ERR_TIMEOUT = -4,   /* a bounded wait inside a kernel (grid barrier, work-queue dependency,
+                               bulk-copy barrier) gave up; results are invalid, the context is usable */
     COS_ERR_OVERFLOW = -5,  /* count mode: the exact path count exceeds 2^63-1 (results wrap mod 2^64) */
     COS_ERR_STATE = -6      /* call out of order, e.g. cos_evaluate before cos_set_samples */
 };
@@ -106,10 +108,13 @@ int cos_graph_share(cos_graph_t src, cos_graph_t* out);
  *   eps[K]   host doubles, the per-kind energies
  *   beta     inverse temperature (> 0)
  *   stream   cudaStream_t (as void*) on which the copy is enqueued
- * Grows the graph's device workspace if needed (the only call besides
- * cos_create_graph that allocates); a tile_samples tuning fixes the workspace
- * to that many samples (set it before the first cos_set_samples).  The copy is asynchronous: a host t must
- * stay valid until the stream reaches this point.
+ * Grows the graph's device workspace if needed; a tile_samples tuning fixes the
+ * workspace to that many samples (set it before the first cos_set_samples).
+ * (Device memory is otherwise allocated by cos_create_graph, cos_graph_share,
+ * cos_set_propagator_table, cos_mc_create, and on first use of the work-queue
+ * schedule or of an internal result buffer; cos_evaluate_static never allocates.)
+ * The copy is asynchronous: a host t must stay valid until the stream reaches
+ * this point.
  * Errors: COS_ERR_INVALID, COS_ERR_OOM, COS_ERR_CUDA.
  */
 int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t t_flags,
@@ -138,12 +143,15 @@ int cos_copy_times(cos_graph_t g, double* dst, void* stream);
 
 /*
  * Evaluate the path sum of every attached sample (Fig. 1; Sec. II.C): one
- * persistent cooperative kernel computes, tile of samples by tile, the propagator
- * table, walks the levels in order with a grid-wide barrier between levels,
- * writes the sink value per sample, and finally reduces the samples.  Allocates
- * nothing when per_sample_out is given (without it, the first evaluation of a
- * larger sample set allocates an internal result buffer); may be captured in a
- * CUDA graph when mean_out is NULL and per_sample_out is given.
+ * persistent kernel computes, tile of samples by tile, the propagator table,
+ * walks the levels in order, writes the sink value per sample, and finally
+ * reduces the samples -- either level-synchronous (cooperative launch, a
+ * grid-wide barrier between levels) or from a work queue (see cos_tuning.schedule).
+ * The level-synchronous schedule allocates nothing when per_sample_out is given
+ * (without it, the first evaluation of a larger sample set allocates an internal
+ * result buffer) and may then be captured in a CUDA graph when mean_out is NULL;
+ * the work-queue schedule plans and uploads its task list on every call (and
+ * allocates its buffers on first use), so it is not meant for capture.
  *   mode            cos_mode
  *   per_sample_out  device pointer or NULL: double[S] (FP64, FP32_MIXED) or
  *                   int64[S] (COUNT_I64), index = sample index
@@ -166,8 +174,8 @@ int cos_get_result(cos_graph_t g, double* mean_out, void* stream);
 
 /*
  * User-tabulated propagators (Fig. 1 caption: the edge factor is a general
- * Green's function G; Sec. II.C "Numerical stability": each edge loads the
- * relevant one).  Replaces the free-fermion formula of every kind k of g by
+ * Green's function G; Sec. II.C "Numerical stability": every edge applies its
+ * own propagator).  Replaces the free-fermion formula of every kind k of g by
  * numbers: table is host memory [K][2][T+1] doubles (copied; the caller keeps
  * ownership); half 0 holds G_k at tau = m*h, m = 0..T, h = tau_max/T, and is used
  * for tau = t_i - t_j >= 0; half 1 holds G_k at tau = -tau_max + m*h and is used
@@ -229,7 +237,8 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *   rows_per_warp     consecutive destination rows one warp takes per work item (<= 31);
  *                     automatic: 31 with the work queue, else 4 (FP64) or 16
  *   blocks_per_sm     persistent CTAs per SM (capped by occupancy)
- *   timeout_ms        grid-barrier wait limit
+ *   timeout_ms        limit of every bounded wait in the kernels (grid barrier,
+ *                     work-queue dependency, bulk-copy barrier); default 10 s
  *   layout            1 = wide (a warp owns one row; chunks of 32*samples_per_lane
  *                     samples), 2 = grouped (a warp owns samples_per_lane rows, each
  *                     served by 32/samples_per_lane lanes; chunks of 32 samples),
@@ -293,7 +302,8 @@ int cos_autotune(cos_graph_t g, int32_t mode, void* per_sample_out, void* stream
  * work is cut into CTA-sized items (propagator factors and table per tile of
  * samples, each level per tile, the sample reduction); the per-graph phase chains
  * are interleaved into one task list that a persistent grid drains through a
- * ticket counter, each item waiting only for the previous phase of its own graph.
+ * ticket counter, each item waiting only for the previous phase of its own graph
+ * (of its own window of sample chunks when window_chunks > 0).
  * The launch (counter reset + kernel) is captured into a CUDA graph on first use
  * and replayed by every later cos_batch_launch.
  *
@@ -305,11 +315,13 @@ int cos_autotune(cos_graph_t g, int32_t mode, void* per_sample_out, void* stream
  *                     workspace layout).
  *   cos_batch_reset   replace the members (same rules as create) keeping the device
  *                     buffers; the previous launch must have been collected.
- *   cos_batch_set_tuning  batch-wide overrides (fields > 0): samples_per_lane (one
- *                     value for the launch), rows_per_warp, tile_samples,
- *                     blocks_per_sm, timeout_ms; other fields come from each graph.
- *   cos_batch_autotune  times every (samples_per_lane, rows_per_warp) candidate on
- *                     the batch itself, keeps the fastest and returns it in *best.
+ *   cos_batch_set_tuning  batch-wide overrides (fields > 0): samples_per_lane and
+ *                     layout (one value for the launch), rows_per_warp,
+ *                     tile_samples, blocks_per_sm, timeout_ms, window_chunks,
+ *                     prefetch; other fields come from each graph.
+ *   cos_batch_autotune  times every (samples_per_lane, rows_per_warp, layout)
+ *                     candidate on the batch itself, keeps the fastest and returns
+ *                     it in *best.
  *   cos_batch_launch  enqueue one evaluation of all graphs on `stream`.  The first
  *                     launch of a plan uploads it (stream-ordered) and runs the
  *                     kernel directly; the second captures counter reset + kernel
