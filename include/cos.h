@@ -167,6 +167,15 @@ int cos_copy_times(cos_graph_t g, double* dst, void* stream);
 int cos_evaluate(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean_out, void* stream);
 
 /*
+ * As cos_evaluate, with every edge factor replaced by its absolute value (the
+ * fermion-loop sign ignored): per_sample_out receives A(s), the sum over paths of
+ * |path value| -- the scale against which the accuracy of R(s) is stated (a
+ * result has relative error eps when |R_computed - R_exact| <= eps * A) -- and
+ * mean_out its mean.  Modes 0 and 1 only (COS_ERR_INVALID otherwise).
+ */
+int cos_evaluate_abs(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean_out, void* stream);
+
+/*
  * Wait for the last cos_evaluate on this graph (stream = the one it ran on) and
  * return its status; if mean_out is non-NULL store its mean there.
  */

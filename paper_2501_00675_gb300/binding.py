@@ -89,6 +89,7 @@ def load_library(build_if_missing: bool = False):
         lib.cos_graph_share.argtypes = [vp, ctypes.POINTER(vp)]
         lib.cos_set_propagator_table.argtypes = [vp, i32, vp, f64]
         lib.cos_autotune.argtypes = [vp, i32, vp, vp, ctypes.POINTER(CosTuning)]
+        lib.cos_evaluate_abs.argtypes = [vp, i32, vp, vp, vp]
         lib.cos_mc_create.argtypes = [vp, i32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
         lib.cos_mc_run.argtypes = [vp, i32, vp]
         lib.cos_mc_stats.argtypes = [vp, vp, vp]
@@ -206,6 +207,13 @@ class Graph:
         rc = load_library().cos_evaluate(self._h, int(mode), _ptr(out), ctypes.addressof(mean) if want_mean else None,
                                          _stream_handle(stream))
         _check(rc, allow=(COS_ERR_OVERFLOW,) if allow_overflow else ())
+        return mean.value if want_mean else None
+
+    def evaluate_abs(self, mode: int, out=None, want_mean: bool = True, stream=None):
+        """cos_evaluate_abs: A(s) = sum of |path| values per sample; returns its mean."""
+        mean = ctypes.c_double(0.0)
+        _check(load_library().cos_evaluate_abs(self._h, int(mode), _ptr(out),
+                                               ctypes.addressof(mean) if want_mean else None, _stream_handle(stream)))
         return mean.value if want_mean else None
 
     def get_result(self, stream=None) -> float:

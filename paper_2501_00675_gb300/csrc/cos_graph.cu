@@ -141,6 +141,7 @@ struct cos_graph {
     int32_t trace_cap = 0;
     int last_mode = 0;
     cos_batch_t wave = nullptr;     // one-graph batch of the windowed schedule (created on first use)
+    int abs_next = 0;               // the next walk uses |factor| (cos_evaluate_abs)
     double* d_ptab = nullptr;       // user-tabulated propagators [K][2][ptab_T+1], or none
     int32_t ptab_T = 0;
     double ptab_tau_max = 0.0;
@@ -866,6 +867,16 @@ int cos_set_propagator_table(cos_graph_t g, int32_t T, const double* table, doub
     return COS_OK;
 }
 
+int cos_evaluate_abs(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean_out, void* stream) {
+    if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
+    if (mode != COS_MODE_FP64 && mode != COS_MODE_FP32_MIXED)
+        return fail(COS_ERR_INVALID, "the sum of |path| values needs a floating-point mode (0 or 1)");
+    g->abs_next = 1;
+    const int rc = cos_evaluate(g, mode, per_sample_out, mean_out, stream);
+    g->abs_next = 0;
+    return rc;
+}
+
 int cos_get_result(cos_graph_t g, double* mean_out, void* stream) {
     if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
     DeviceGuard dg(g->device);
@@ -959,6 +970,7 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
     p.ptab_T = g->ptab_T;
     p.ptab_tau_max = g->ptab_tau_max;
     p.ptab_inv_h = g->d_ptab ? (double)g->ptab_T / g->ptab_tau_max : 0.0;
+    p.abs_weights = g->abs_next;
     p.timeout_ns = (long long)tn.timeout_ms * 1000000LL;
     if (tn_out) *tn_out = tn;
     return COS_OK;

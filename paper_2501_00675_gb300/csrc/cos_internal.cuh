@@ -73,7 +73,7 @@ struct WalkParams {
     double ptab_tau_max;
     double ptab_inv_h;           // T / tau_max
     int32_t ptab_T;
-    int32_t pad3;
+    int32_t abs_weights;         // 1: every factor replaced by its absolute value (A(s) = sum of |path|)
     int64_t pf_slice_bytes;      // wide layout: L2-prefetch parents on levels whose parent slice per chunk exceeds this
 };
 

@@ -482,6 +482,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                 const int i = __ldg(p.slot_kij + 3 * q + 1), jw = __ldg(p.slot_kij + 3 * q + 2);
                 const int j = jw & 0x3fffffff;
                 const long long smask = (jw & 0x40000000) ? (long long)0x8000000000000000ULL : 0LL;
+                const long long amask = p.abs_weights ? 0x7FFFFFFFFFFFFFFFLL : -1LL;
 #pragma unroll
                 for (int v = 0; v < CHV / 32; ++v) {
                     const double tau = st[i * CHV + v * 32 + lane] - st[j * CHV + v * 32 + lane];
@@ -501,7 +502,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                     }
                     const double2 as = __ldg(tk + (pos ? 0 : T) + m);
                     const double g =
-                        __longlong_as_double(__double_as_longlong(__dadd_rn(as.x, __dmul_rn(f, as.y))) ^ smask);
+                        __longlong_as_double((__double_as_longlong(__dadd_rn(as.x, __dmul_rn(f, as.y))) ^ smask) & amask);
                     __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
                 }
             }
@@ -543,12 +544,13 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                     const int i = __ldg(p.slot_kij + 3 * q + 1), jw = __ldg(p.slot_kij + 3 * q + 2);
                     const int j = jw & 0x3fffffff;
                     const unsigned smask = (jw & 0x40000000) ? 0x80000000u : 0u;   // closes a fermion loop
+                    const unsigned amask = p.abs_weights ? 0x7FFFFFFFu : 0xFFFFFFFFu;   // |G| for A(s)
 #pragma unroll
                     for (int v = 0; v < CHV / 32; ++v) {
                         const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
                         const float2 a = (sk[xi] >= sk[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
                         __stcg(reinterpret_cast<float*>(gt) + (int64_t)q * CHV + v * 32 + lane,
-                               __uint_as_float(__float_as_uint(mul_ff(a, fe_[xj])) ^ smask));
+                               __uint_as_float((__float_as_uint(mul_ff(a, fe_[xj])) ^ smask) & amask));
                     }
                 }
             }
@@ -574,11 +576,12 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                 const int j = jw & 0x3fffffff;
                 // closes a fermion loop: flip the sign bit (no extra FP64 operation)
                 const long long smask = (jw & 0x40000000) ? (long long)0x8000000000000000ULL : 0LL;
+                const long long amask = p.abs_weights ? 0x7FFFFFFFFFFFFFFFLL : -1LL;   // |G| for A(s)
 #pragma unroll
                 for (int v = 0; v < CHV / 32; ++v) {
                     const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
                     const double a = (sk[xi] >= sk[xj]) ? sp[xi] : sn[xi];   // tau = t_i - t_j >= 0 ?
-                    const double g = __longlong_as_double(__double_as_longlong(a * se[xj]) ^ smask);
+                    const double g = __longlong_as_double((__double_as_longlong(a * se[xj]) ^ smask) & amask);
                     __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
                 }
             }

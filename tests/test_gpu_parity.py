@@ -544,3 +544,32 @@ def test_single_graph_autotune_keeps_results(cg):
     gr.set_tuning(rows_per_warp=5)                     # fixed fields stay fixed
     assert gr.autotune(1)["rows_per_warp"] == 5
     gr.close()
+
+
+def test_sum_of_abs_paths_matches_the_oracle(cg):
+    # cos_evaluate_abs: A(s) = sum over paths of |path value|, the accuracy scale of R(s)
+    w = medium(num_samples=900)
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    gr = cg.Graph.from_workload_graph(w.graph)
+    gr.set_samples(torch.from_numpy(w.samples.t).cuda(), w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+    for mode in (0, 1):
+        for schedule in (1, 2):
+            gr.set_tuning(schedule=schedule)
+            out = torch.empty(900, dtype=torch.float64, device="cuda")
+            ma = gr.evaluate_abs(mode, out=out)
+            a = out.cpu().numpy()
+            assert np.all(np.abs(a - A) <= TOL[mode] * A)
+            assert abs(ma - float(np.mean(A))) <= TOL[mode] * float(np.mean(A))
+            r = torch.empty_like(out)
+            gr.evaluate(mode, out=r)                      # the ordinary walk is unchanged afterwards
+            assert np.all(np.abs(r.cpu().numpy()) <= a * (1 + 1e-6))
+    rng = np.random.default_rng(41)                        # with tabulated propagators: |table|
+    tables = 0.5 * np.tanh(rng.normal(size=(w.graph.num_kinds, 2, 9))) + 0.3
+    Rt, At = oracle.evaluate_tabulated(w.graph, tables, 9.0, w.samples.t)
+    gr.set_propagator_table(tables, 9.0)
+    out = torch.empty(900, dtype=torch.float64, device="cuda")
+    gr.evaluate_abs(0, out=out)
+    assert np.all(np.abs(out.cpu().numpy() - At) <= 1e-12 * At)
+    with pytest.raises(cg.CosError):
+        gr.evaluate_abs(2)
+    gr.close()
