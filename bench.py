@@ -341,7 +341,11 @@ def run_ours(args, rank, world, local):
             err = {"bit_exact": bool(np.all(got == cnt)), "samples_checked": int(idx.size)}
         else:
             rel = np.abs(got - R_or) / A_or
+            R_ld = oracle.evaluate_tight(g, s.eps, s.beta, s.t[idx])   # long-double reference
+            rel_ld = np.abs(got - R_ld) / A_or
             err = {"max_err_over_abs_path_sum": float(rel.max()), "median_err_over_abs_path_sum": float(np.median(rel)),
+                   "max_err_vs_long_double": float(rel_ld.max()),
+                   "oracle_max_err_vs_long_double": float((np.abs(R_or - R_ld) / A_or).max()),
                    "tolerance": 1e-12 if mode == 0 else 1e-5, "samples_checked": int(idx.size)}
 
     cpu = None

@@ -7,7 +7,8 @@ package never imports the GPU library.
 Contents
   * ``cos_oracle.c`` (built here with gcc): the level-wise dynamic program of
     Sec. II.B / Fig. 1 in IEEE double, per-sample propagators, unit-weight path
-    counts with 128-bit overflow detection, Neumaier summation.
+    counts with 128-bit overflow detection, Neumaier summation; and the same DP in
+    long double (``evaluate_tight``) as a tighter reference.
   * ``brute_force_paths`` / ``brute_force_sum``: pure-Python enumeration of all
     root-to-sink paths (one path = one diagram, Sec. II.B) for tiny graphs.
   * ``tabulated_propagator`` / ``evaluate_tabulated``: a user-tabulated G(tau) per
@@ -70,6 +71,9 @@ def _load():
             lib.cos_oracle_eval.argtypes = [ctypes.c_int32, _i64p, _i64p, _i32p, ctypes.c_int32, ctypes.c_int32,
                                             _f64p, ctypes.c_double, ctypes.c_int64, _f64p, _f64p, _f64p,
                                             ctypes.c_int32]
+            lib.cos_oracle_eval_ld.restype = ctypes.c_int
+            lib.cos_oracle_eval_ld.argtypes = [ctypes.c_int32, _i64p, _i64p, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                               _f64p, ctypes.c_double, ctypes.c_int64, _f64p, _f64p, ctypes.c_int32]
             lib.cos_oracle_count.restype = ctypes.c_int
             lib.cos_oracle_count.argtypes = [ctypes.c_int32, _i64p, _i64p, _i32p, _i64p, _i32p]
             lib.cos_oracle_neumaier_sum.restype = ctypes.c_double
@@ -212,6 +216,22 @@ def evaluate(graph, eps: np.ndarray, beta: float, t: np.ndarray, with_abs: bool 
     if rc:
         raise ValueError(f"oracle evaluation failed ({rc})")
     return R, A
+
+
+def evaluate_tight(graph, eps: np.ndarray, beta: float, t: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """Per-sample sink values computed in long double (expl), rounded once to double:
+    a tighter reference than ``evaluate`` for measuring double-precision results."""
+    lib = _load()
+    wd, c, e = _graph_arrays(graph)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    S, D = t.shape
+    R = np.empty(S)
+    rc = lib.cos_oracle_eval_ld(len(wd), _p(wd, _i64p), _p(c, _i64p), _p(e, _i32p), graph.num_kinds, D,
+                                _p(eps, _f64p), float(beta), S, _p(t, _f64p), _p(R, _f64p), int(nthreads))
+    if rc:
+        raise ValueError(f"oracle evaluation failed ({rc})")
+    return R
 
 
 def count_paths(graph) -> Tuple[int, bool]:

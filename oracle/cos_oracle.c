@@ -134,6 +134,56 @@ int cos_oracle_eval(int32_t L, const int64_t* widths, const int64_t* counts, con
     return status;
 }
 
+/* The same evaluation carried in long double (the host's extended format: 64-bit
+ * significand on x86-64, IEEE binary128 on AArch64) with expl: a reference whose
+ * rounding error is far below double's, against which the double results (here
+ * and on the GPU) can be measured.  tau = t_i - t_j is formed in long double from
+ * the double times; the branch is still decided by t_i >= t_j on the doubles.
+ * R[s] is the long double sink value rounded once to double. */
+static long double propagator_ld(long double eps, long double beta, double ti, double tj) {
+    const long double tau = (long double)ti - (long double)tj;
+    if (ti >= tj) return -expl(-eps * tau) / (1.0L + expl(-beta * eps));
+    return expl(-eps * (tau + beta)) / (1.0L + expl(-beta * eps));
+}
+
+int cos_oracle_eval_ld(int32_t L, const int64_t* widths, const int64_t* counts, const int32_t* edges,
+                       int32_t K, int32_t D, const double* eps, double beta,
+                       int64_t S, const double* t, double* R, int32_t nthreads) {
+    int64_t N, E;
+    if (check_graph(L, widths, counts, edges, K, D, &N, &E)) return -1;
+    int status = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        long double* v = (long double*)malloc(sizeof(long double) * (size_t)N);
+        if (!v) {
+#pragma omp atomic write
+            status = -2;
+        } else {
+#pragma omp for schedule(dynamic, 4)
+            for (int64_t s = 0; s < S; ++s) {
+                const double* ts = t + s * D;
+                for (int64_t n = 0; n < N; ++n) v[n] = 0.0L;
+                v[0] = 1.0L;
+                for (int64_t e = 0; e < E; ++e) {
+                    const int32_t* r = edges + 5 * e;
+                    long double w = propagator_ld((long double)eps[r[2] & COS_ORACLE_KIND_MASK], (long double)beta,
+                                                  ts[r[3]], ts[r[4]]);
+                    if (r[2] & COS_ORACLE_SIGN_BIT) w = -w;
+                    v[r[1]] += v[r[0]] * w;
+                }
+                R[s] = (double)v[N - 1];
+            }
+        }
+        free(v);
+    }
+    return status;
+}
+
 /* Unit-weight path count.  *count_wrapped = count mod 2^64 (as int64);
  * *overflow = 1 if the exact count exceeds 2^63-1. */
 int cos_oracle_count(int32_t L, const int64_t* widths, const int64_t* counts, const int32_t* edges,

@@ -573,3 +573,16 @@ def test_sum_of_abs_paths_matches_the_oracle(cg):
     with pytest.raises(cg.CosError):
         gr.evaluate_abs(2)
     gr.close()
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_fp64_error_against_the_long_double_reference(cg, schedule):
+    # the GPU's FP64 results measured against the oracle's long-double evaluation:
+    # within the double DP's own rounding bound (as the double oracle is), far inside 1e-12
+    w = medium(num_samples=300)
+    Rt = oracle.evaluate_tight(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    _, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    Rg, _ = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, 0, {"schedule": schedule})
+    rel = np.abs(Rg - Rt) / A
+    print(f"FP64 GPU vs long double, schedule {schedule}: max {rel.max():.2e} median {np.median(rel):.2e}")
+    assert rel.max() <= 4 * (w.graph.num_levels + 4) * 2.0 ** -53

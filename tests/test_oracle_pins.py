@@ -359,3 +359,40 @@ def test_tabulated_formula_agrees_with_library_interpolation():
     want = np.where(pos, np.interp(tau, xs, tab[0]), np.interp(tau, xs - tau_max, tab[1]))
     slope = np.max(np.abs(np.diff(tab, axis=1))) * T / tau_max
     assert np.max(np.abs(got - want)) <= 8 * np.finfo(float).eps * (11.0 * slope + np.max(np.abs(tab)))
+
+
+# ------------------------------------------------------------------ long-double reference
+
+def test_tight_oracle_chain_closed_form():
+    # the chain of rational factors (-0.4, 0.4, -0.4, 0.4, -0.8) of the double closed-form pin
+    g = chain_graph([0, 0, 0, 0, 0], [0, 1, 0, 1, 0], [1, 0, 1, 0, 0], 1, 2)
+    Rt = oracle.evaluate_tight(g, np.array([math.log(2.0)]), 2.0, np.array([[1.5, 0.5]]))
+    expected = (-0.4) * 0.4 * (-0.4) * 0.4 * (-0.8)
+    assert abs(Rt[0] - expected) <= 2 * np.spacing(abs(expected))
+
+
+def test_tight_oracle_zero_energy_sign_count_is_exact():
+    # eps = 0: factors are exactly -1/2 or +1/2, so every path value and their sum are
+    # exact in any binary format; the long-double result must equal the brute-force sum
+    g, _, t = _random_graph(6, [1, 4, 6, 6, 3, 1], fmax=3, K=2, D=5)
+    t[:, 1] = t[:, 2]
+    g = _with_signs(g, np.random.default_rng(7).random(g.num_edges) < 0.3)   # fermion-loop flags too
+    Rt = oracle.evaluate_tight(g, np.zeros(2), 10.0, t)
+    paths = oracle.brute_force_paths(g)
+    e = g.edges
+    flip = np.where((e[:, 2] & oracle.SIGN_BIT) != 0, -1.0, 1.0)
+    for s in range(t.shape[0]):
+        w = np.where(t[s, e[:, 3]] >= t[s, e[:, 4]], -0.5, 0.5) * flip
+        assert Rt[s] == oracle.brute_force_sum(paths, w)[0]
+
+
+def test_double_oracle_within_its_rounding_bound_of_the_tight_one():
+    # the double DP's error is at most about (path length + fan-in) roundings of the
+    # largest paths: |R - R_tight| <= c (L + F) u A with u = 2^-53
+    from workloads import medium
+    w = medium(num_samples=120)
+    R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    Rt = oracle.evaluate_tight(w.graph, w.samples.eps, w.samples.beta, w.samples.t)
+    u = 2.0 ** -53
+    assert np.all(np.abs(R - Rt) <= 4 * (w.graph.num_levels + 4) * u * A)
+    assert np.max(np.abs(R - Rt) / A) > 0      # the references differ: double rounding is visible
