@@ -150,8 +150,9 @@ int cos_copy_times(cos_graph_t g, double* dst, void* stream);
  * The level-synchronous schedule allocates nothing when per_sample_out is given
  * (without it, the first evaluation of a larger sample set allocates an internal
  * result buffer) and may then be captured in a CUDA graph when mean_out is NULL;
- * the work-queue schedule plans and uploads its task list on every call (and
- * allocates its buffers on first use), so it is not meant for capture.
+ * the work-queue schedule plans its task list on every call and uploads it when it
+ * changed (a host wait for the previous upload's copy to run precedes a new
+ * upload; buffers are allocated on first use), so it is not meant for capture.
  *   mode            cos_mode
  *   per_sample_out  device pointer or NULL: double[S] (FP64, FP32_MIXED) or
  *                   int64[S] (COUNT_I64), index = sample index

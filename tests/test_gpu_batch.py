@@ -150,3 +150,30 @@ def test_batch_rejects_duplicates_and_reports_overflow(cg):
     b.close()
     g1.close()
     big.close()
+
+
+def test_queue_plans_enqueued_behind_busy_stream(cg):
+    """Work-queue evaluations whose plans differ only in the output pointer, enqueued
+    one after another without a host wait behind ~0.1 s of other work on the stream:
+    each launch must use its own plan, so every buffer receives the sink values
+    (the host-side plan staging may not be overwritten before its copy has run)."""
+    from workloads import medium
+    w = medium(num_samples=1024)
+    g, s = w.graph, w.samples
+    R, A = oracle.evaluate(g, s.eps, s.beta, s.t)
+    gr = cg.Graph.from_workload_graph(g)
+    gr.set_samples(torch.from_numpy(s.t).cuda(), s.eps, s.beta, cg.COS_T_SAMPLE_MAJOR)
+    gr.set_tuning(schedule=2)
+    st = torch.cuda.current_stream()
+    outs = [torch.full((s.num_samples,), -9.0, dtype=torch.float64, device="cuda") for _ in range(3)]
+    torch.cuda._sleep(200_000_000)
+    for o in outs[:2]:
+        gr.evaluate(0, out=o, want_mean=False, stream=st)
+    outs[0].fill_(-9.0)
+    gr.evaluate(0, out=outs[0], want_mean=False, stream=st)     # back to the first plan
+    gr.evaluate(0, out=outs[2], want_mean=False, stream=st)
+    torch.cuda.synchronize()
+    for o in outs:
+        r = o.cpu().numpy()
+        assert np.all(np.abs(r - R) <= 1e-12 * A)
+    gr.close()
