@@ -51,7 +51,9 @@ enum cos_status {
     COS_ERR_TIMEOUT = -4,   /* a bounded wait inside a kernel (grid barrier, work-queue dependency,
                                bulk-copy barrier) gave up; results are invalid, the context is usable */
     COS_ERR_OVERFLOW = -5,  /* count mode: the exact path count exceeds 2^63-1 (results wrap mod 2^64) */
-    COS_ERR_STATE = -6      /* call out of order, e.g. cos_evaluate before cos_set_samples */
+    COS_ERR_STATE = -6,     /* call out of order, e.g. cos_evaluate before cos_set_samples */
+    COS_ERR_BUSY = -7       /* resident server: the request is still running (poll), or no request
+                               slot or queue space is free right now (submit; retry later) */
 };
 
 enum cos_mode {
@@ -425,6 +427,78 @@ int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samples, const 
  * 15 (1989)).  g supplies the device and the 2^{j/64} table.  Asynchronous on stream.
  */
 int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, double* ep, void* stream);
+
+/*
+ * Resident server (continuous batching at work-item granularity).  One persistent
+ * kernel keeps running while requests arrive; a request is one evaluation of a
+ * graph handle (Fig. 1; Sec. II.C) over counter-based uniform sample times drawn
+ * on the device (the generator of cos_set_samples_uniform), cut into the same
+ * work items as a batched launch.  Submitting appends the request's items to a
+ * task queue in device memory through host-to-device copies on a stream of the
+ * server's own, so a request admitted while the kernel runs starts as soon as the
+ * items queued before it are handed out -- no launch boundary, and no kernel has
+ * to run to admit it.  Items are handed out in submission order.  CTAs that find
+ * no work for idle_ms leave; the next submit, poll or wait relaunches the kernel
+ * when work is pending.  Completion is reported through host-mapped records that
+ * poll and wait read without synchronising a stream.
+ *
+ *   cos_server_create  mode (one per server); max_times = the largest D of the
+ *                      graphs to be served (sizes shared memory); tuning (NULL or
+ *                      fields > 0): samples_per_lane, rows_per_warp (default 31),
+ *                      tile_samples, blocks_per_sm, timeout_ms (dependency waits,
+ *                      default 10000), window_chunks, prefetch; layout must be 0 or
+ *                      1 (wide).  max_requests (default 256) request slots;
+ *                      queue_tasks (default 65536, rounded up to a power of two)
+ *                      task entries; idle_ms (default 50).  Allocates everything
+ *                      it will use (nothing is allocated while serving).  The
+ *                      server belongs to the device current at creation.
+ *   cos_server_submit  evaluate handle g over num_samples samples numbered
+ *                      first_sample.. of generator key `seed`; per-sample values go
+ *                      to per_sample_out (device, max(num_samples,1) doubles, or
+ *                      int64 in count mode; required).  g must have had a sample
+ *                      set of at least num_samples attached in its own buffer
+ *                      (cos_set_samples_uniform, or cos_set_samples without
+ *                      COS_T_BORROW) so that eps, beta and the buffers exist; the
+ *                      request overwrites the handle's times and sample count.  A
+ *                      handle serves one request at a time (COS_ERR_STATE while
+ *                      busy: use cos_graph_share for concurrent requests on one
+ *                      graph).  *request_id receives the request number.
+ *                      COS_ERR_BUSY: no free request slot or queue space (nothing
+ *                      changed; collect results and retry).
+ *   cos_server_poll    COS_OK with *mean_out (may be NULL) once the request is
+ *                      complete (the request is then collected and its id becomes
+ *                      invalid), COS_ERR_BUSY while it runs, or its error
+ *                      (COS_ERR_TIMEOUT if a dependency wait gave up; then every
+ *                      pending request fails and the server must be destroyed;
+ *                      COS_ERR_OVERFLOW in count mode as cos_evaluate).
+ *   cos_server_wait    poll until not busy or timeout_ms (< 0: no limit) passed
+ *                      (then COS_ERR_TIMEOUT; the request stays pending).
+ *   cos_server_stats   counters (below).
+ *   cos_server_destroy let the kernel finish the queued work, then free everything.
+ * One host thread per server.  Sample times of a request live in the handle's own
+ * buffer until its next request; per_sample_out is written before completion is
+ * reported.
+ */
+typedef struct cos_server* cos_server_t;
+typedef struct cos_server_info {
+    int64_t launches;         /* kernel launches so far (1 + relaunches after idle exits) */
+    int64_t completed;        /* requests completed */
+    int64_t in_flight;        /* requests submitted and not complete */
+    int64_t queued_tasks;     /* task entries held by requests not yet retired */
+    int64_t published_tasks;  /* tasks published since creation */
+    int32_t running;          /* 1 while the kernel has CTAs resident */
+    int32_t grid;             /* CTAs per launch */
+    int32_t samples_per_lane;
+    int32_t failed;           /* 0, or the cos_status every pending request fails with */
+} cos_server_info;
+int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning, int32_t max_requests,
+                      int64_t queue_tasks, int32_t idle_ms, cos_server_t* out);
+int cos_server_submit(cos_server_t s, cos_graph_t g, int64_t num_samples, uint64_t seed, int64_t first_sample,
+                      void* per_sample_out, int64_t* request_id);
+int cos_server_poll(cos_server_t s, int64_t request_id, double* mean_out);
+int cos_server_wait(cos_server_t s, int64_t request_id, int32_t timeout_ms, double* mean_out);
+int cos_server_stats(cos_server_t s, cos_server_info* info);
+int cos_server_destroy(cos_server_t s);
 
 /* Free every device and host resource of the handle (NULL is accepted). */
 int cos_destroy(cos_graph_t g);

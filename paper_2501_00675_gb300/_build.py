@@ -16,8 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcosgpu.so")
-SOURCES = ["cos_graph.cu", "cos_walk.cu", "cos_batch.cu", "cos_noalloc.cu", "cos_mc.cu"]
-HEADERS = ["cos_internal.cuh", "cos_items.cuh"]
+SOURCES = ["cos_graph.cu", "cos_walk.cu", "cos_batch.cu", "cos_noalloc.cu", "cos_mc.cu", "cos_serve.cu"]
+HEADERS = ["cos_internal.cuh", "cos_items.cuh", "cos_tasks.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -23,6 +23,7 @@ COS_ERR_CUDA = -3
 COS_ERR_TIMEOUT = -4
 COS_ERR_OVERFLOW = -5
 COS_ERR_STATE = -6
+COS_ERR_BUSY = -7
 
 COS_MODE_FP64 = 0
 COS_MODE_FP32_MIXED = 1
@@ -37,7 +38,9 @@ EXPORTED = ["cos_create_graph", "cos_set_samples", "cos_evaluate", "cos_get_resu
             "cos_set_tuning", "cos_get_tuning", "cos_set_trace", "cos_get_trace", "cos_evaluate_static",
             "cos_graph_share", "cos_batch_create", "cos_batch_reset", "cos_batch_set_tuning", "cos_batch_get_tuning", "cos_batch_autotune",
             "cos_batch_launch", "cos_batch_results", "cos_batch_destroy", "cos_evaluate_batch",
-            "cos_selftest_exp", "cos_set_samples_uniform", "cos_copy_times", "cos_destroy", "cos_last_error"]
+            "cos_selftest_exp", "cos_set_samples_uniform", "cos_copy_times", "cos_server_create",
+            "cos_server_submit", "cos_server_poll", "cos_server_wait", "cos_server_stats", "cos_server_destroy",
+            "cos_destroy", "cos_last_error"]
 
 _lock = threading.Lock()
 _lib = None
@@ -47,6 +50,12 @@ class CosError(RuntimeError):
     def __init__(self, code: int, message: str):
         super().__init__(f"[{code}] {message}")
         self.code = code
+
+
+class CosServerInfo(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("completed", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("queued_tasks", ctypes.c_int64), ("published_tasks", ctypes.c_int64), ("running", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("samples_per_lane", ctypes.c_int32), ("failed", ctypes.c_int32)]
 
 
 class CosTuning(ctypes.Structure):
@@ -107,6 +116,12 @@ def load_library(build_if_missing: bool = False):
         lib.cos_selftest_exp.argtypes = [vp, i64, vp, vp, vp, vp]
         lib.cos_set_samples_uniform.argtypes = [vp, i64, ctypes.c_uint64, i64, vp, f64, vp]
         lib.cos_copy_times.argtypes = [vp, vp, vp]
+        lib.cos_server_create.argtypes = [i32, i32, ctypes.POINTER(CosTuning), i32, i64, i32, ctypes.POINTER(vp)]
+        lib.cos_server_submit.argtypes = [vp, vp, i64, ctypes.c_uint64, i64, vp, ctypes.POINTER(i64)]
+        lib.cos_server_poll.argtypes = [vp, i64, ctypes.POINTER(f64)]
+        lib.cos_server_wait.argtypes = [vp, i64, i32, ctypes.POINTER(f64)]
+        lib.cos_server_stats.argtypes = [vp, ctypes.POINTER(CosServerInfo)]
+        lib.cos_server_destroy.argtypes = [vp]
         lib.cos_destroy.argtypes = [vp]
         lib.cos_last_error.restype = ctypes.c_char_p
         lib.cos_last_error.argtypes = []
@@ -386,6 +401,58 @@ class Metropolis:
         if getattr(self, "_h", None):
             load_library().cos_mc_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ResidentServer:
+    """Resident server (cos_server_*): one persistent kernel that keeps running while
+    requests arrive; each request evaluates a graph handle over counter-based uniform
+    times drawn on the device.  See include/cos.h for the semantics."""
+
+    def __init__(self, mode: int, max_times: int, max_requests: int = 256, queue_tasks: int = 65536,
+                 idle_ms: int = 50, **tuning):
+        t = CosTuning(**{k: int(v) for k, v in tuning.items()})
+        h = ctypes.c_void_p()
+        _check(load_library().cos_server_create(int(mode), int(max_times), ctypes.byref(t), int(max_requests),
+                                                int(queue_tasks), int(idle_ms), ctypes.byref(h)))
+        self._h = h
+        self.mode = int(mode)
+
+    def submit(self, graph: "Graph", num_samples: int, seed: int, out, first_sample: int = 0) -> Optional[int]:
+        """Request id, or None when no slot or queue space is free (COS_ERR_BUSY)."""
+        rid = ctypes.c_int64(0)
+        rc = _check(load_library().cos_server_submit(self._h, graph._h, int(num_samples),
+                                                     ctypes.c_uint64(int(seed) & (2**64 - 1)), int(first_sample),
+                                                     _ptr(out), ctypes.byref(rid)), allow=(COS_ERR_BUSY,))
+        return None if rc == COS_ERR_BUSY else int(rid.value)
+
+    def poll(self, request_id: int, allow_overflow: bool = False):
+        """The request's mean once complete (the request is then collected), else None."""
+        m = ctypes.c_double(0.0)
+        rc = _check(load_library().cos_server_poll(self._h, int(request_id), ctypes.byref(m)),
+                    allow=(COS_ERR_BUSY, COS_ERR_OVERFLOW) if allow_overflow else (COS_ERR_BUSY,))
+        return None if rc == COS_ERR_BUSY else m.value
+
+    def wait(self, request_id: int, timeout_ms: int = -1, allow_overflow: bool = False) -> float:
+        m = ctypes.c_double(0.0)
+        _check(load_library().cos_server_wait(self._h, int(request_id), int(timeout_ms), ctypes.byref(m)),
+               allow=(COS_ERR_OVERFLOW,) if allow_overflow else ())
+        return m.value
+
+    def stats(self) -> dict:
+        info = CosServerInfo()
+        _check(load_library().cos_server_stats(self._h, ctypes.byref(info)))
+        return {f: int(getattr(info, f)) for f, _ in info._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            h, self._h = self._h, None
+            _check(load_library().cos_server_destroy(h))
 
     def __del__(self):
         try:

@@ -26,26 +26,10 @@
 #include <vector>
 
 #include "cos_items.cuh"
+#include "cos_tasks.cuh"
 
 namespace cosgpu {
 namespace {
-
-// TK_STALL: a test-only task (COS_TEST_STALL_TASK) that is drawn but never counted
-// done, so that a dependency wait on it runs into its time limit.
-enum TaskKind : int32_t { TK_COEF = 0, TK_PROP = 1, TK_LEVEL = 3, TK_PARTIALS = 4, TK_FINAL = 5, TK_STALL = 6 };
-
-struct Task {
-    int32_t graph;      // index into the parameter array
-    int32_t kind;
-    int32_t level;
-    int32_t dep;        // task that must be complete first (-1: none)
-    int64_t tix;        // tile index
-    int64_t first;      // first ticket of this task
-    int32_t items;
-    int32_t c0;         // first chunk of the task's window within the tile
-    int32_t join_off;   // further tasks that must be complete: joins[join_off .. +join_cnt)
-    int32_t join_cnt;
-};
 
 struct BatchCtrl {
     unsigned long long ticket;
@@ -176,8 +160,6 @@ const void* select_batch_kernel(int mode, int vec, int layout) {
     if (layout == 1) return select_batch_layout<LAYOUT_WIDE>(mode, vec);
     return nullptr;
 }
-
-int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 }  // namespace cosgpu
@@ -356,74 +338,9 @@ int plan(cos_batch* b) {
         GraphView gv;
         graph_view(b->graphs[(size_t)g], &gv);
         b->counts_overflow[(size_t)g] = gv.count_overflow;
-        const WalkParams& p = b->params[(size_t)g];
-        std::vector<Task>& out = lists[(size_t)g];
-        std::vector<std::vector<int32_t>>& joins = local_joins[(size_t)g];
-        auto make = [&](int32_t kind, int32_t level, int64_t tix, int64_t items, int32_t c0) {
-            Task t;
-            memset(&t, 0, sizeof(t));
-            t.graph = g;
-            t.kind = kind;
-            t.level = level;
-            t.tix = tix;
-            t.items = (int32_t)items;
-            t.c0 = c0;
-            t.dep = -1;
-            return t;
-        };
-        auto emit = [&](const Task& t, std::vector<int32_t> js) {
-            out.push_back(t);
-            joins.push_back(std::move(js));
-            return (int32_t)out.size() - 1;
-        };
-        int32_t coef = -1;
-        if (mode != COS_MODE_COUNT_I64) coef = emit(make(TK_COEF, 0, 0, 1, 0), {});
-        // window chains: chunks [w*wch, (w+1)*wch) of every tile
-        const int64_t ntiles = p.S > 0 ? (p.S + p.tile - 1) / p.tile : 0;
-        const int nch_max = p.S > 0 ? div_up(std::min<int64_t>(p.tile, p.S), chv) : 0;
-        const int wch = force.window_chunks > 0 ? std::min(force.window_chunks, std::max(nch_max, 1)) : std::max(nch_max, 1);
-        const int nw = nch_max > 0 ? div_up(nch_max, wch) : 0;
-        const int rows_per_item = kWarps * p.rows_per_warp;
-        std::vector<std::vector<Task>> chains((size_t)nw);
-        for (int64_t tix = 0; tix < ntiles; ++tix) {
-            const int64_t nsamp = std::min(p.tile, p.S - tix * p.tile);
-            const int nch = div_up(nsamp, chv);
-            for (int w = 0; w < nw; ++w) {
-                const int c0 = w * wch;
-                if (c0 >= nch) break;
-                const int n_w = std::min(wch, nch - c0);
-                chains[(size_t)w].push_back(
-                    make(TK_PROP, 0, tix, mode == COS_MODE_COUNT_I64 ? n_w : (int64_t)n_w * p.K, c0));
-                for (int l = 1; l < p.L; ++l)
-                    chains[(size_t)w].push_back(
-                        make(TK_LEVEL, l, tix, (int64_t)n_w * div_up(gv.widths_host[l], rows_per_item), c0));
-            }
-        }
-        // wavefront: step d issues phase d - w of window w, oldest window first
-        std::vector<int32_t> last((size_t)nw, coef);
-        size_t maxlen = 0;
-        for (auto& ch : chains) maxlen = std::max(maxlen, ch.size());
-        for (size_t d = 0; d + 1 < maxlen + (size_t)nw; ++d)
-            for (int w = 0; w < nw; ++w) {
-                if ((size_t)w > d) break;
-                const size_t ph = d - (size_t)w;
-                if (ph >= chains[(size_t)w].size()) continue;
-                Task t = chains[(size_t)w][ph];
-                t.dep = last[(size_t)w];
-                last[(size_t)w] = emit(t, {});
-            }
-        // the sample reduction waits for every window; the final mean for the reduction
-        Task part = make(TK_PARTIALS, 0, 0, div_up(div_up(p.S, kReduceBlock), kWarps), 0);
-        part.dep = coef;
-        std::vector<int32_t> js;
-        for (int w = 0; w < nw; ++w)
-            if (last[(size_t)w] != coef) js.push_back(last[(size_t)w]);
-        const int32_t ip = emit(part, std::move(js));
-        Task fin = make(TK_FINAL, 0, 0, 1, 0);
-        fin.dep = ip;
-        std::vector<int32_t> stall;
-        if (g == 0 && getenv("COS_TEST_STALL_TASK")) stall.push_back(emit(make(TK_STALL, 0, 0, 1, 0), {}));
-        emit(fin, std::move(stall));
+        graph_task_chain(b->params[(size_t)g], gv.widths_host, mode, chv, force.window_chunks, g, false,
+                         g == 0 && getenv("COS_TEST_STALL_TASK") != nullptr, lists[(size_t)g],
+                         local_joins[(size_t)g]);
     }
     // Round-robin interleave of the graphs' lists (each list keeps its order).
     b->tasks.clear();

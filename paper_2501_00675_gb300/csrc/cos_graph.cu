@@ -976,6 +976,33 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
     return COS_OK;
 }
 
+int attach_own_samples(cos_graph_t g, int64_t num_samples, SampleState* undo) {
+    if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
+    if (!g->has_samples) return fail(COS_ERR_STATE, "attach samples once (cos_set_samples*) to set eps, beta and buffers");
+    if (num_samples < 0) return fail(COS_ERR_INVALID, "num_samples must be >= 0");
+    const int64_t t_ld = std::max<int64_t>(round_up(num_samples, 128), 128);
+    if (!g->d_t || t_ld * g->D > g->t_cap)
+        return fail(COS_ERR_STATE, "the handle's time buffer holds %lld samples; attach a sample set of %lld once first",
+                    (long long)(g->D > 0 ? g->t_cap / g->D : 0), (long long)num_samples);
+    if (std::max<int64_t>((num_samples + kReduceBlock - 1) / kReduceBlock, 1) > g->partial_cap)
+        return fail(COS_ERR_STATE, "partial-sum buffer too small for %lld samples", (long long)num_samples);
+    if (undo) {
+        undo->S = g->S;
+        undo->t_ld = g->t_ld;
+        undo->t_borrowed = g->t_borrowed;
+    }
+    g->S = num_samples;
+    g->t_ld = t_ld;
+    g->t_borrowed = nullptr;
+    return COS_OK;
+}
+
+void restore_samples(cos_graph_t g, const SampleState& s) {
+    g->S = s.S;
+    g->t_ld = s.t_ld;
+    g->t_borrowed = s.t_borrowed;
+}
+
 int set_error(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;

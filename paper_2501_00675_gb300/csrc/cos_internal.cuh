@@ -108,6 +108,17 @@ int graph_view(cos_graph_t g, GraphView* out);
 // tuning) and fill the walker parameters for the graph's current samples.
 int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sample_out, WalkParams* out,
                  cos_tuning* tn_out);
+// Host-side sample state of a handle (what attach_own_samples changes).
+struct SampleState {
+    int64_t S, t_ld;
+    const double* t_borrowed;
+};
+// Point the handle at num_samples samples of its own time buffer [D][t_ld] without any
+// CUDA call (the caller fills the buffer on the device).  The handle must have had a
+// sample set of at least that size attached before (which also set eps and beta);
+// *undo (may be NULL) receives the previous state for restore_samples.
+int attach_own_samples(cos_graph_t g, int64_t num_samples, SampleState* undo);
+void restore_samples(cos_graph_t g, const SampleState& s);
 // Records a message for cos_last_error() and returns code.
 int set_error(int code, const char* fmt, ...);
 // Windowed schedule of one graph (cos_batch.cu): plan the graph alone as a batch of

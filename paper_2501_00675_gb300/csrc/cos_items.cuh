@@ -66,6 +66,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1
     return c;
 }
 
+// Times 2m and 2m+1 of sample number n, uniform in [0, beta): Philox counter
+// (n lo, n hi, m, 0) under the key `seed`; the top 53 bits of the word pairs
+// (w1:w0) and (w3:w2) scaled by 2^-53.
+__device__ __forceinline__ void uniform_time_pair(unsigned long long seed, unsigned long long n, int m, double beta,
+                                                  double& a, double& b) {
+    const uint4 w = philox4x32_10(make_uint4((unsigned)n, (unsigned)(n >> 32), (unsigned)m, 0u), (unsigned)seed,
+                                  (unsigned)(seed >> 32));
+    a = beta * ((double)((((unsigned long long)w.y << 32) | w.x) >> 11) * 0x1.0p-53);
+    b = beta * ((double)((((unsigned long long)w.w << 32) | w.z) >> 11) * 0x1.0p-53);
+}
+
 // ---------------------------------------------------------------- vector access
 
 template <typename T, int V>

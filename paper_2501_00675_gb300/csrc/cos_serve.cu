@@ -1,0 +1,802 @@
+// Resident evaluation server: one persistent kernel keeps running while requests
+// arrive, and a request admitted while it runs starts at the next free work item,
+// not at the next launch.
+//
+// Requests are graph evaluations (Fig. 1; Sec. II.C) over counter-based uniform
+// sample times drawn on the device.  The host turns each request into the same
+// task chain as a batched launch (times, coefficients, per window of sample chunks
+// propagators and levels 1..L-1, partial sums, final mean) and appends it to a task
+// ring in device memory; the ring entries, the request's walker parameters, the
+// per-slot claim words and finally the published-task counter are written by
+// host-to-device copies on one copy stream, so the counter is never seen before
+// what it publishes.  The kernel never waits for a copy and no kernel has to run
+// to admit a request.
+//
+// Claiming: a global cursor names the task whose items are handed out; a CTA reads
+// the cursor, checks that the task is published and that the slot's claim word
+// carries the task's tag (the low 32 bits of its absolute index), and takes the
+// next item by compare-and-swap on that word; a task whose items are all handed
+// out moves the cursor on.  Items are therefore handed out in task order, and a
+// CTA holds a claimed item only while it runs, so the lowest unfinished item can
+// always run (its dependencies are earlier tasks): no co-residency is required and
+// an idle CTA, which holds nothing, may leave at any time.  Completion counters
+// per ring slot are cumulative over the tasks the slot has held (a task is
+// complete once its slot's counter reaches the value the host assigned), so no
+// counter is ever reset while a late increment could still arrive.
+//
+// Every wait is bounded: dependency waits by the tuning's timeout (then the error
+// is recorded and every CTA leaves), the idle poll by the server's idle time (then
+// the CTA leaves; the host relaunches the kernel when work is pending and no CTA
+// is left).  Completion is reported through host-mapped records (the mean, then
+// the request number with a system-scope release), which the host polls.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <vector>
+
+#include "cos_items.cuh"
+#include "cos_tasks.cuh"
+
+namespace cosgpu {
+namespace {
+
+struct SvTask {
+    int64_t self;       // absolute task index; its ring slot is self & mask
+    int64_t seq;        // request number (key of the CTAs' parameter cache)
+    int64_t tix;        // tile index (TK_TIMES: number of the request's first sample)
+    int64_t dep;        // absolute index of the task that must be complete first, or -1
+    int64_t join_off;   // absolute index of the first join entry
+    uint64_t seed;      // TK_TIMES: generator key
+    int32_t req;        // request slot: walker parameters and completion record
+    int32_t kind;
+    int32_t level;
+    int32_t items;
+    int32_t c0;
+    int32_t join_cnt;
+    uint32_t need;      // value of done[self & mask] once this task is complete
+    int32_t pad;
+};
+static_assert(sizeof(SvTask) % 8 == 0, "descriptor is copied as 8-byte words");
+static_assert(sizeof(WalkParams) % 8 == 0, "parameters are copied as 8-byte words");
+
+struct SvPub {          // device memory, written only by host-to-device copies
+    long long tasks;    // tasks published so far
+    int shutdown;       // 1: leave as soon as no published work is left
+    int pad;
+};
+
+struct SvCtl {          // device memory
+    long long cursor;   // task whose items are being handed out
+    int err;
+    int pad;
+};
+
+struct SvComp {                 // host-mapped, one per request slot
+    unsigned long long seq;     // request number, stored last (release, system scope)
+    double mean;
+};
+
+struct SvStatus {               // host-mapped
+    int err;                    // first kernel-side error (KERR_*, or a level item's code)
+    int pad;
+    long long err_task;         // absolute index of the task that reported it
+};
+
+struct ServeArgs {
+    const SvTask* ring;
+    const long long* joins;
+    const WalkParams* params;
+    unsigned long long* claim;  // [cap]: (task tag << 32) | items handed out
+    unsigned* done;             // [cap]: items completed, cumulative over the slot's tasks
+    SvCtl* ctl;
+    const SvPub* pub;
+    SvComp* comp;               // device alias of the mapped completion records
+    SvStatus* status;           // device alias of the mapped status
+    long long mask;
+    long long jmask;
+    long long timeout_ns;
+    long long idle_ns;
+};
+
+__device__ __forceinline__ long long ld_volatile_s64(const long long* p) { return *(const volatile long long*)p; }
+__device__ __forceinline__ int ld_volatile_s32(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+
+__device__ __forceinline__ long long ld_acquire_gpu_s64(const long long* p) {
+    long long v;
+    asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Record the first error for the host and for the other CTAs.
+__device__ __forceinline__ void sv_fail(const ServeArgs& a, int code, long long task) {
+    if (atomicCAS(&a.ctl->err, 0, code) == 0) {
+        a.status->err_task = task;
+        a.status->err = code;
+        __threadfence_system();
+    }
+}
+
+// One attempt to claim an item (thread 0).  Returns 1 with (k, item), 0 when every
+// published item is handed out, 2 when items were left but the attempts lost races.
+__device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out, int& item_out) {
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        const long long k = ld_volatile_s64(&a.ctl->cursor);
+        if (k >= pub) {
+            pub = ld_acquire_gpu_s64(&a.pub->tasks);
+            if (k >= pub) return 0;
+        }
+        const long long s = k & a.mask;
+        const unsigned long long w = ld_volatile_u64(a.claim + s);
+        const int tag_age = (int)((unsigned)k - (unsigned)(w >> 32));
+        if (tag_age > 0) return 0;   // not yet initialised for k (cannot happen once k is published)
+        const int items = __ldcg(&a.ring[s].items);
+        if (tag_age == 0 && (unsigned)w < (unsigned)items) {
+            if (atomicCAS(a.claim + s, w, w + 1) == w) {
+                k_out = k;
+                item_out = (int)(unsigned)w;
+                return 1;
+            }
+            continue;
+        }
+        // task k is exhausted (or its slot already holds a later task): move the cursor on
+        atomicCAS(reinterpret_cast<unsigned long long*>(&a.ctl->cursor), (unsigned long long)k,
+                  (unsigned long long)(k + 1));
+    }
+    return 2;
+}
+
+// Claim an item, waiting (bounded by the idle time) for work to be published.
+// Returns 1 with (k, item), 0 to leave (shutdown, idle, or another CTA's error).
+__device__ int sv_claim(const ServeArgs& a, long long& pub, long long& k_out, int& item_out) {
+    unsigned long long t0 = global_timer_ns();
+    unsigned sleep_ns = 64;
+    for (unsigned long long spin = 0;; ++spin) {
+        const int r = sv_try_claim(a, pub, k_out, item_out);
+        if (r == 1) return 1;
+        if (ld_volatile_s32(&a.ctl->err) != 0) return 0;
+        if (r == 2) {   // work is there: not idle
+            t0 = global_timer_ns();
+            continue;
+        }
+        if (ld_volatile_s32(&a.pub->shutdown) != 0) return 0;
+        if ((long long)(global_timer_ns() - t0) > a.idle_ns || spin > (1ull << 32)) return 0;
+        __nanosleep(sleep_ns);
+        sleep_ns = min(sleep_ns * 2, 8192u);
+    }
+}
+
+// Request times: columns [item * kTimesPerItem, ...) of t[D][t_ld]; draws for the
+// samples s < S (sample number first + s), zeros in the padding.
+__device__ __forceinline__ void item_times(const WalkParams& p, unsigned long long seed, long long first, int item) {
+    const int pairs = (p.D + 1) / 2;
+    const long long s0 = (long long)item * kTimesPerItem;
+    const long long n = min((long long)kTimesPerItem, p.t_ld - s0);
+    double* t = const_cast<double*>(p.t);
+    for (long long q = threadIdx.x; q < n * pairs; q += blockDim.x) {
+        const int m = (int)(q / n);
+        const long long s = s0 + (q - (long long)m * n);
+        double x = 0.0, y = 0.0;
+        if (s < p.S) uniform_time_pair(seed, (unsigned long long)(first + s), m, p.beta, x, y);
+        t[(long long)(2 * m) * p.t_ld + s] = x;
+        if (2 * m + 1 < p.D) t[(long long)(2 * m + 1) * p.t_ld + s] = y;
+    }
+}
+
+template <int MODE, int V>
+__global__ void __launch_bounds__(kThreads, (MODE == COS_MODE_FP64 && V > 2) ? 2 : 3) serve_kernel(const ServeArgs a) {
+    constexpr int CHV = chunk_samples<V, LAYOUT_WIDE>();
+    extern __shared__ __align__(16) double smem[];
+    __shared__ WalkParams s_p;
+    __shared__ SvTask s_tk;
+    __shared__ long long s_k[2];
+    __shared__ int s_item[2];
+    __shared__ int s_ok;
+    long long pub = 0;            // thread 0: published tasks last seen
+    long long nk = -1;            // thread 0: claimed-ahead item
+    int nitem = 0;
+    if (threadIdx.x == 0) {
+        long long k = -1;
+        int item = 0;
+        if (!sv_claim(a, pub, k, item)) k = -1;
+        s_k[0] = k;
+        s_item[0] = item;
+    }
+    __syncthreads();
+    long long cur_k = -1, cur_seq = -1;
+    int buf = 0;
+    for (;;) {
+        const long long k = s_k[buf];
+        const int item = s_item[buf];
+        if (k < 0) return;
+        if (k != cur_k) {   // uniform: every thread sees the same k
+            const long long s = k & a.mask;
+            constexpr int TW = sizeof(SvTask) / 8;
+            if (threadIdx.x < TW)
+                reinterpret_cast<unsigned long long*>(&s_tk)[threadIdx.x] =
+                    __ldcg(reinterpret_cast<const unsigned long long*>(a.ring + s) + threadIdx.x);
+            __syncthreads();
+            if (s_tk.seq != cur_seq) {
+                constexpr int PW = sizeof(WalkParams) / 8;
+                const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.params + s_tk.req);
+                for (int w = threadIdx.x; w < PW; w += blockDim.x)
+                    reinterpret_cast<unsigned long long*>(&s_p)[w] = __ldcg(src + w);
+                cur_seq = s_tk.seq;
+            }
+            if (threadIdx.x == 0) {   // dependencies: the chain predecessor, then the joins
+                int ok = 1;
+                const unsigned long long t0 = global_timer_ns();
+                unsigned long long spin = 0;
+                for (int q = -1; ok && q < s_tk.join_cnt; ++q) {
+                    const long long dep = q < 0 ? s_tk.dep : __ldcg(a.joins + ((s_tk.join_off + q) & a.jmask));
+                    if (dep < 0) continue;
+                    const unsigned need = __ldcg(&a.ring[dep & a.mask].need);
+                    for (;; ++spin) {
+                        if ((int)(ld_acquire_gpu_u32(a.done + (dep & a.mask)) - need) >= 0) break;
+                        if (ld_volatile_s32(&a.ctl->err) != 0) { ok = 0; break; }
+                        if ((spin & 31) == 31 &&
+                            ((long long)(global_timer_ns() - t0) > a.timeout_ns || spin > (1ull << 32))) {
+                            sv_fail(a, KERR_BARRIER_TIMEOUT, k);
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) return;   // holds only an item that can no longer matter: the launch is failing
+            cur_k = k;
+        }
+        if (threadIdx.x == 0 && nk < 0) {   // claim the next item while this one runs
+            if (sv_try_claim(a, pub, nk, nitem) != 1) nk = -1;
+        }
+        const WalkParams& p = s_p;
+        TileCtx tc;
+        if (s_tk.kind == TK_PROP || s_tk.kind == TK_LEVEL) {
+            tc = tile_ctx<CHV>(p, s_tk.tix);
+            tc.c0 = s_tk.c0;
+        }
+        switch (s_tk.kind) {
+            case TK_TIMES: item_times(p, s_tk.seed, s_tk.tix, item); break;
+            case TK_COEF: item_coef(p); break;
+            case TK_PROP: item_props<MODE, CHV>(p, tc, item, smem); break;
+            case TK_LEVEL:
+                if (!item_level<MODE, V, LAYOUT_WIDE, MODE == COS_MODE_FP64>(p, s_tk.level, tc, item,
+                                                                            reinterpret_cast<unsigned char*>(smem)) &&
+                    (threadIdx.x & 31) == 0) {
+                    const int code = *(volatile int*)&p.ctrl->err;
+                    sv_fail(a, code ? code : KERR_BARRIER_TIMEOUT, k);
+                }
+                break;
+            case TK_PARTIALS: item_partials<MODE>(p, item); break;
+            case TK_FINAL: item_final(p); break;
+            default: break;   // TK_STALL
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_tk.kind != TK_STALL)   // release: the item's writes are visible first
+                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.done + (k & a.mask)) : "memory");
+            if (s_tk.kind == TK_FINAL) {   // the mean (written above by this thread), then the request number
+                SvComp* c = a.comp + s_tk.req;
+                asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(&c->seq), "l"((unsigned long long)s_tk.seq)
+                             : "memory");
+            }
+            if (nk < 0 && !sv_claim(a, pub, nk, nitem)) nk = -1;
+            s_k[buf ^ 1] = nk;
+            s_item[buf ^ 1] = nitem;
+            nk = -1;
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+}
+
+template <int MODE, int V>
+const void* sk() {
+    return reinterpret_cast<const void*>(&serve_kernel<MODE, V>);
+}
+
+const void* select_serve_kernel(int mode, int vec) {
+    switch (mode * 8 + vec) {
+        case COS_MODE_FP64 * 8 + 1: return sk<COS_MODE_FP64, 1>();
+        case COS_MODE_FP64 * 8 + 2: return sk<COS_MODE_FP64, 2>();
+        case COS_MODE_FP64 * 8 + 4: return sk<COS_MODE_FP64, 4>();
+        case COS_MODE_FP32_MIXED * 8 + 1: return sk<COS_MODE_FP32_MIXED, 1>();
+        case COS_MODE_FP32_MIXED * 8 + 2: return sk<COS_MODE_FP32_MIXED, 2>();
+        case COS_MODE_FP32_MIXED * 8 + 4: return sk<COS_MODE_FP32_MIXED, 4>();
+        case COS_MODE_COUNT_I64 * 8 + 1: return sk<COS_MODE_COUNT_I64, 1>();
+        case COS_MODE_COUNT_I64 * 8 + 2: return sk<COS_MODE_COUNT_I64, 2>();
+        case COS_MODE_COUNT_I64 * 8 + 4: return sk<COS_MODE_COUNT_I64, 4>();
+        default: return nullptr;
+    }
+}
+
+int64_t pow2_at_least(int64_t x) {
+    int64_t c = 1;
+    while (c < x) c <<= 1;
+    return c;
+}
+
+}  // namespace
+}  // namespace cosgpu
+
+using namespace cosgpu;
+
+struct cos_server {
+    int device = 0;
+    int32_t mode = 0;
+    int vec = 2;
+    int32_t max_D = 0;
+    cos_tuning force{};
+    int32_t max_req = 0;
+    int64_t cap = 0, jcap = 0;
+    int grid = 0, smem = 0;
+    const void* kernel = nullptr;
+    long long timeout_ns = 0, idle_ns = 0;
+    // device
+    SvTask* d_ring = nullptr;
+    long long* d_joins = nullptr;
+    WalkParams* d_params = nullptr;
+    unsigned long long* d_claim = nullptr;
+    unsigned* d_done = nullptr;
+    SvCtl* d_ctl = nullptr;
+    SvPub* d_pub = nullptr;
+    // pinned host mirrors (sources of the publishing copies)
+    SvTask* h_ring = nullptr;
+    long long* h_joins = nullptr;
+    WalkParams* h_params = nullptr;
+    unsigned long long* h_claim = nullptr;
+    long long* h_pubval = nullptr;   // [max_req]: the counter value each request publishes
+    int* h_one = nullptr;            // 1, the shutdown flag's source
+    // host-mapped records written by the kernel
+    SvComp* h_comp = nullptr;
+    SvComp* d_comp = nullptr;
+    SvStatus* h_status = nullptr;
+    SvStatus* d_status = nullptr;
+    cudaStream_t ks = nullptr, cs = nullptr;
+    cudaEvent_t kdone = nullptr, cev = nullptr;
+    bool running = false;
+    int failed = 0;                  // cos_status once the kernel has reported an error
+    int64_t next_task = 0, tail_task = 0, next_join = 0, tail_join = 0, next_seq = 1;
+    std::vector<uint32_t> slot_total;
+    struct Req {
+        int64_t seq = 0;
+        cos_graph_t g = nullptr;
+        bool active = false, done = false;
+        int overflow = 0;
+        int err = 0;
+        double mean = 0.0;
+    };
+    std::vector<Req> reqs;
+    struct Span {
+        int64_t seq;
+        int32_t slot;
+        int64_t t_end, j_end;
+    };
+    std::deque<Span> fifo;           // ring space in publication order
+    int64_t launches = 0, completed = 0;
+};
+
+namespace {
+
+using Srv = cos_server;
+
+int cuda_err(cudaError_t e, const char* what) {
+    return set_error(COS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void free_server(Srv* s) {
+    cudaFree(s->d_ring);
+    cudaFree(s->d_joins);
+    cudaFree(s->d_params);
+    cudaFree(s->d_claim);
+    cudaFree(s->d_done);
+    cudaFree(s->d_ctl);
+    cudaFree(s->d_pub);
+    cudaFreeHost(s->h_ring);
+    cudaFreeHost(s->h_joins);
+    cudaFreeHost(s->h_params);
+    cudaFreeHost(s->h_claim);
+    cudaFreeHost(s->h_pubval);
+    cudaFreeHost(s->h_one);
+    cudaFreeHost(s->h_comp);
+    cudaFreeHost(s->h_status);
+    if (s->kdone) cudaEventDestroy(s->kdone);
+    if (s->cev) cudaEventDestroy(s->cev);
+    if (s->ks) cudaStreamDestroy(s->ks);
+    if (s->cs) cudaStreamDestroy(s->cs);
+}
+
+int map_kernel_error(int err) {
+    return err == KERR_BARRIER_TIMEOUT ? COS_ERR_TIMEOUT : COS_ERR_CUDA;
+}
+
+// Has the kernel left?  Records a kernel-side error as the server's failure.
+void check_kernel(Srv* s) {
+    if (!s->running) return;
+    const cudaError_t q = cudaEventQuery(s->kdone);
+    if (q == cudaErrorNotReady) return;
+    s->running = false;
+    if (q != cudaSuccess) {
+        s->failed = COS_ERR_CUDA;
+        set_error(COS_ERR_CUDA, "resident kernel: %s", cudaGetErrorString(q));
+        return;
+    }
+    const int err = *(volatile int*)&s->h_status->err;
+    if (err != 0 && !s->failed) {
+        s->failed = map_kernel_error(err);
+        set_error(s->failed, "resident kernel reported error %d at task %lld", err,
+                  (long long)*(volatile long long*)&s->h_status->err_task);
+    }
+}
+
+// Completion records -> requests; ring space of finished requests, oldest first.
+void collect(Srv* s) {
+    for (int32_t r = 0; r < s->max_req; ++r) {
+        Srv::Req& q = s->reqs[(size_t)r];
+        if (!q.active || q.done) continue;
+        if (*(volatile unsigned long long*)&s->h_comp[r].seq == (unsigned long long)q.seq) {
+            __atomic_thread_fence(__ATOMIC_ACQUIRE);
+            q.mean = *(volatile double*)&s->h_comp[r].mean;
+            q.done = true;
+            s->completed++;
+        } else if (s->failed) {
+            q.err = s->failed;
+            q.done = true;
+        }
+    }
+    while (!s->fifo.empty()) {
+        const Srv::Span& f = s->fifo.front();
+        const Srv::Req& q = s->reqs[(size_t)f.slot];
+        if (q.seq == f.seq && !q.done) break;
+        s->tail_task = f.t_end;
+        s->tail_join = f.j_end;
+        s->fifo.pop_front();
+    }
+}
+
+int launch(Srv* s) {
+    ServeArgs a;
+    a.ring = s->d_ring;
+    a.joins = s->d_joins;
+    a.params = s->d_params;
+    a.claim = s->d_claim;
+    a.done = s->d_done;
+    a.ctl = s->d_ctl;
+    a.pub = s->d_pub;
+    a.comp = s->d_comp;
+    a.status = s->d_status;
+    a.mask = s->cap - 1;
+    a.jmask = s->jcap - 1;
+    a.timeout_ns = s->timeout_ns;
+    a.idle_ns = s->idle_ns;
+    cudaError_t e;
+    if ((e = cudaEventRecord(s->cev, s->cs)) != cudaSuccess) return cuda_err(e, "record publish event");
+    if ((e = cudaStreamWaitEvent(s->ks, s->cev, 0)) != cudaSuccess) return cuda_err(e, "order launch after publish");
+    void* args[] = {&a};
+    if ((e = cudaLaunchKernel(s->kernel, dim3((unsigned)s->grid), dim3(kThreads), args, (size_t)s->smem, s->ks)) !=
+        cudaSuccess)
+        return cuda_err(e, "launch resident kernel");
+    if ((e = cudaEventRecord(s->kdone, s->ks)) != cudaSuccess) return cuda_err(e, "record kernel event");
+    s->running = true;
+    s->launches++;
+    return COS_OK;
+}
+
+// Kernel exit, completions, and a relaunch when work is pending and no CTA is left.
+int pump(Srv* s) {
+    check_kernel(s);
+    collect(s);
+    if (s->failed || s->running) return COS_OK;
+    for (const Srv::Req& q : s->reqs)
+        if (q.active && !q.done) return launch(s);
+    return COS_OK;
+}
+
+// Copy entries [first, first + n) of a ring of `cap` entries (wrapping) to the device.
+template <typename T>
+cudaError_t copy_ring(T* dst, const T* src, int64_t cap, int64_t first, int64_t n, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    while (n > 0 && e == cudaSuccess) {
+        const int64_t at = first & (cap - 1);
+        const int64_t m = std::min(n, cap - at);
+        e = cudaMemcpyAsync(dst + at, src + at, sizeof(T) * (size_t)m, cudaMemcpyHostToDevice, st);
+        first += m;
+        n -= m;
+    }
+    return e;
+}
+
+int find_request(Srv* s, int64_t id) {
+    for (int32_t r = 0; r < s->max_req; ++r)
+        if (s->reqs[(size_t)r].active && s->reqs[(size_t)r].seq == id) return r;
+    return -1;
+}
+
+struct DevSel {
+    int prev = -1;
+    explicit DevSel(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevSel() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning, int32_t max_requests,
+                      int64_t queue_tasks, int32_t idle_ms, cos_server_t* out) {
+    if (!out) return set_error(COS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (mode < 0 || mode > 2) return set_error(COS_ERR_INVALID, "bad mode %d", mode);
+    if (max_times < 1) return set_error(COS_ERR_INVALID, "max_times must be >= 1");
+    if (max_requests < 0 || queue_tasks < 0 || idle_ms < 0)
+        return set_error(COS_ERR_INVALID, "max_requests, queue_tasks and idle_ms must be >= 0");
+    cos_tuning t{};
+    if (tuning) t = *tuning;
+    if (t.samples_per_lane > 0 && t.samples_per_lane != 1 && t.samples_per_lane != 2 && t.samples_per_lane != 4)
+        return set_error(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
+    if (t.layout > 1) return set_error(COS_ERR_INVALID, "the resident server runs the wide layout (layout 0 or 1)");
+    if (t.rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
+    if (t.window_chunks < 0 || t.prefetch < 0 || t.prefetch > 3)
+        return set_error(COS_ERR_INVALID, "window_chunks must be >= 0 and prefetch 0..3");
+    Srv* s = new (std::nothrow) Srv();
+    if (!s) return set_error(COS_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&s->device);
+    s->mode = mode;
+    s->vec = t.samples_per_lane > 0 ? t.samples_per_lane : (mode == COS_MODE_FP32_MIXED ? 4 : 2);
+    s->max_D = max_times;
+    s->force = t;
+    s->force.samples_per_lane = s->vec;
+    s->force.layout = 1;
+    if (s->force.rows_per_warp <= 0) s->force.rows_per_warp = 31;
+    s->max_req = max_requests > 0 ? max_requests : 256;
+    s->cap = pow2_at_least(std::max<int64_t>(queue_tasks > 0 ? queue_tasks : 65536, 64));
+    s->jcap = s->cap;
+    s->timeout_ns = (long long)(t.timeout_ms > 0 ? t.timeout_ms : 10000) * 1000000LL;
+    s->idle_ns = (long long)(idle_ms > 0 ? idle_ms : 50) * 1000000LL;
+    s->kernel = select_serve_kernel(mode, s->vec);
+    s->smem = walk_smem_bytes(mode, s->vec, 1, max_times);
+    int rc = COS_OK;
+    cudaError_t e = cudaSuccess;
+    int per_sm = 0, sms = 0;
+    if (!s->kernel) {
+        rc = set_error(COS_ERR_INVALID, "no resident kernel for samples_per_lane %d", s->vec);
+    } else if (prepare_kernel_attrs(s->kernel, s->smem) != COS_OK) {
+        rc = set_error(COS_ERR_INVALID, "shared memory for %d time variables exceeds the limit", max_times);
+    } else if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s->kernel, kThreads, s->smem)) !=
+                   cudaSuccess ||
+               per_sm <= 0) {
+        rc = set_error(COS_ERR_CUDA, "occupancy query failed");
+    }
+    if (rc == COS_OK) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+        const int bps = t.blocks_per_sm > 0 ? std::min(t.blocks_per_sm, per_sm) : per_sm;
+        s->force.blocks_per_sm = bps;
+        s->grid = sms * bps;
+        const size_t nr = (size_t)s->max_req;
+        const size_t cap = (size_t)s->cap, jcap = (size_t)s->jcap;
+        if ((e = cudaMalloc(&s->d_ring, sizeof(SvTask) * cap)) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_joins, sizeof(long long) * jcap)) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_params, sizeof(WalkParams) * nr)) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_claim, sizeof(unsigned long long) * cap)) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_done, sizeof(unsigned) * cap)) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_ctl, sizeof(SvCtl))) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_pub, sizeof(SvPub))) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_ring, sizeof(SvTask) * cap)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_joins, sizeof(long long) * jcap)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_params, sizeof(WalkParams) * nr)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_claim, sizeof(unsigned long long) * cap)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_pubval, sizeof(long long) * nr)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_one, sizeof(int))) != cudaSuccess ||
+            (e = cudaHostAlloc(&s->h_comp, sizeof(SvComp) * nr, cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostAlloc(&s->h_status, sizeof(SvStatus), cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_comp), s->h_comp, 0)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_status), s->h_status, 0)) != cudaSuccess)
+            rc = set_error(COS_ERR_OOM, "server buffers: %s", cudaGetErrorString(e));
+    }
+    if (rc == COS_OK) {
+        memset(s->h_comp, 0, sizeof(SvComp) * (size_t)s->max_req);
+        memset(s->h_status, 0, sizeof(SvStatus));
+        *s->h_one = 1;
+        if ((e = cudaMemset(s->d_claim, 0, sizeof(unsigned long long) * (size_t)s->cap)) != cudaSuccess ||
+            (e = cudaMemset(s->d_done, 0, sizeof(unsigned) * (size_t)s->cap)) != cudaSuccess ||
+            (e = cudaMemset(s->d_ctl, 0, sizeof(SvCtl))) != cudaSuccess ||
+            (e = cudaMemset(s->d_pub, 0, sizeof(SvPub))) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&s->ks, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&s->kdone, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&s->cev, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaDeviceSynchronize()) != cudaSuccess)
+            rc = cuda_err(e, "server set-up");
+    }
+    if (rc != COS_OK) {
+        free_server(s);
+        delete s;
+        return rc;
+    }
+    s->slot_total.assign((size_t)s->cap, 0u);
+    s->reqs.assign((size_t)s->max_req, Srv::Req{});
+    *out = s;
+    return COS_OK;
+}
+
+int cos_server_submit(cos_server_t s, cos_graph_t g, int64_t num_samples, uint64_t seed, int64_t first_sample,
+                      void* per_sample_out, int64_t* request_id) {
+    if (!s || !g || !request_id) return set_error(COS_ERR_INVALID, "bad arguments");
+    if (!per_sample_out) return set_error(COS_ERR_INVALID, "per_sample_out is required");
+    if (num_samples < 0 || first_sample < 0) return set_error(COS_ERR_INVALID, "num_samples and first_sample must be >= 0");
+    DevSel dev(s->device);
+    int rc = pump(s);
+    if (rc != COS_OK) return rc;
+    if (s->failed) return set_error(s->failed, "the server has failed; destroy it");
+    GraphView gv;
+    if ((rc = graph_view(g, &gv)) != COS_OK) return rc;
+    if (gv.device != s->device) return set_error(COS_ERR_INVALID, "graph and server are on different devices");
+    if (gv.D > s->max_D) return set_error(COS_ERR_INVALID, "graph has %d time variables; the server was made for %d", gv.D, s->max_D);
+    int32_t slot = -1;
+    for (int32_t r = 0; r < s->max_req; ++r) {
+        const Srv::Req& q = s->reqs[(size_t)r];
+        if (q.active && q.g == g) return set_error(COS_ERR_STATE, "the handle is in use by request %lld", (long long)q.seq);
+        if (!q.active && slot < 0) slot = r;
+    }
+    if (slot < 0) return set_error(COS_ERR_BUSY, "all %d request slots are in use", s->max_req);
+    SampleState undo;
+    if ((rc = attach_own_samples(g, num_samples, &undo)) != COS_OK) return rc;
+    WalkParams p;
+    cos_tuning tn;
+    rc = prepare_walk(g, s->mode, &s->force, per_sample_out, &p, &tn);
+    if (rc == COS_OK && (tn.samples_per_lane != s->vec || tn.layout != 1))
+        rc = set_error(COS_ERR_INVALID, "graph needs samples_per_lane %d; the server runs %d", tn.samples_per_lane, s->vec);
+    if (rc != COS_OK) {
+        restore_samples(g, undo);
+        return rc;
+    }
+    p.mean_out = &s->d_comp[slot].mean;
+    std::vector<Task> list;
+    std::vector<std::vector<int32_t>> js;
+    graph_task_chain(p, gv.widths_host, s->mode, 32 * s->vec, s->force.window_chunks > 0 ? s->force.window_chunks : tn.window_chunks,
+                     slot, s->mode != COS_MODE_COUNT_I64, getenv("COS_TEST_STALL_TASK") != nullptr, list, js);
+    const int64_t nt = (int64_t)list.size();
+    int64_t nj = 0;
+    for (auto& j : js) nj += (int64_t)j.size();
+    if (nt > s->cap - (s->next_task - s->tail_task) || nj > s->jcap - (s->next_join - s->tail_join)) {
+        restore_samples(g, undo);
+        if (nt > s->cap || nj > s->jcap)
+            return set_error(COS_ERR_INVALID, "request needs %lld tasks; the queue holds %lld", (long long)nt, (long long)s->cap);
+        return set_error(COS_ERR_BUSY, "task queue full (%lld of %lld in use)", (long long)(s->next_task - s->tail_task),
+                         (long long)s->cap);
+    }
+    const int64_t seq = s->next_seq;
+    int64_t joff = 0;
+    for (int64_t i = 0; i < nt; ++i) {
+        const Task& t = list[(size_t)i];
+        const int64_t self = s->next_task + i;
+        const int64_t at = self & (s->cap - 1);
+        SvTask& e = s->h_ring[at];
+        memset(&e, 0, sizeof(e));
+        e.self = self;
+        e.seq = seq;
+        e.tix = t.kind == TK_TIMES ? first_sample : t.tix;
+        e.dep = t.dep >= 0 ? s->next_task + t.dep : -1;
+        e.join_off = s->next_join + joff;
+        e.seed = seed;
+        e.req = slot;
+        e.kind = t.kind;
+        e.level = t.level;
+        e.items = t.items;
+        e.c0 = t.c0;
+        e.join_cnt = (int32_t)js[(size_t)i].size();
+        s->slot_total[(size_t)at] += (uint32_t)t.items;
+        e.need = s->slot_total[(size_t)at];
+        s->h_claim[at] = (unsigned long long)(uint32_t)self << 32;
+        for (int32_t d : js[(size_t)i]) s->h_joins[(s->next_join + joff++) & (s->jcap - 1)] = s->next_task + d;
+    }
+    s->h_params[slot] = p;
+    s->h_pubval[slot] = s->next_task + nt;
+    // publish: parameters, descriptors, claim words, joins, then the counter (one stream, in order)
+    cudaError_t e = cudaMemcpyAsync(s->d_params + slot, s->h_params + slot, sizeof(WalkParams), cudaMemcpyHostToDevice, s->cs);
+    if (e == cudaSuccess) e = copy_ring(s->d_ring, s->h_ring, s->cap, s->next_task, nt, s->cs);
+    if (e == cudaSuccess) e = copy_ring(s->d_claim, s->h_claim, s->cap, s->next_task, nt, s->cs);
+    if (e == cudaSuccess) e = copy_ring(s->d_joins, s->h_joins, s->jcap, s->next_join, nj, s->cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&s->d_pub->tasks, s->h_pubval + slot, sizeof(long long), cudaMemcpyHostToDevice, s->cs);
+    if (e != cudaSuccess) {   // the ring mirrors have moved on: the server cannot continue
+        s->failed = COS_ERR_CUDA;
+        return cuda_err(e, "publish request");
+    }
+    Srv::Req& q = s->reqs[(size_t)slot];
+    q = Srv::Req{};
+    q.seq = seq;
+    q.g = g;
+    q.active = true;
+    q.overflow = s->mode == COS_MODE_COUNT_I64 && gv.count_overflow;
+    s->fifo.push_back(Srv::Span{seq, slot, s->next_task + nt, s->next_join + nj});
+    s->next_task += nt;
+    s->next_join += nj;
+    s->next_seq++;
+    *request_id = seq;
+    return pump(s);
+}
+
+int cos_server_poll(cos_server_t s, int64_t request_id, double* mean_out) {
+    if (!s) return set_error(COS_ERR_INVALID, "server is NULL");
+    DevSel dev(s->device);
+    const int r = find_request(s, request_id);
+    if (r < 0) return set_error(COS_ERR_INVALID, "unknown or already collected request %lld", (long long)request_id);
+    int rc = pump(s);
+    if (rc != COS_OK) return rc;
+    Srv::Req& q = s->reqs[(size_t)r];
+    if (!q.done) return COS_ERR_BUSY;
+    q.active = false;
+    q.g = nullptr;
+    if (q.err) return set_error(q.err, "request %lld failed: %s", (long long)request_id, cos_last_error());
+    if (mean_out) *mean_out = q.mean;
+    if (q.overflow) return set_error(COS_ERR_OVERFLOW, "path count exceeds 2^63-1; results wrap modulo 2^64");
+    return COS_OK;
+}
+
+int cos_server_wait(cos_server_t s, int64_t request_id, int32_t timeout_ms, double* mean_out) {
+    if (!s) return set_error(COS_ERR_INVALID, "server is NULL");
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const int rc = cos_server_poll(s, request_id, mean_out);
+        if (rc != COS_ERR_BUSY) return rc;
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (timeout_ms >= 0 && ms > timeout_ms)
+            return set_error(COS_ERR_TIMEOUT, "request %lld not complete after %d ms", (long long)request_id, timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+int cos_server_stats(cos_server_t s, cos_server_info* info) {
+    if (!s || !info) return set_error(COS_ERR_INVALID, "bad arguments");
+    DevSel dev(s->device);
+    int rc = pump(s);
+    if (rc != COS_OK) return rc;
+    memset(info, 0, sizeof(*info));
+    info->launches = s->launches;
+    info->completed = s->completed;
+    for (const Srv::Req& q : s->reqs) info->in_flight += (q.active && !q.done) ? 1 : 0;
+    info->queued_tasks = s->next_task - s->tail_task;
+    info->published_tasks = s->next_task;
+    info->running = s->running ? 1 : 0;
+    info->grid = s->grid;
+    info->samples_per_lane = s->vec;
+    info->failed = s->failed;
+    return COS_OK;
+}
+
+int cos_server_destroy(cos_server_t s) {
+    if (!s) return COS_OK;
+    int rc = COS_OK;
+    {
+        DevSel dev(s->device);
+        if (s->running) {
+            // ask the CTAs to leave once the published work is done, then wait for them
+            cudaError_t e = cudaMemcpyAsync(&s->d_pub->shutdown, s->h_one, sizeof(int), cudaMemcpyHostToDevice, s->cs);
+            if (e == cudaSuccess) e = cudaEventSynchronize(s->kdone);
+            if (e != cudaSuccess) rc = cuda_err(e, "stop resident kernel");
+            s->running = false;
+        }
+        free_server(s);
+    }
+    delete s;
+    return rc;
+}
+
+}  // extern "C"

@@ -119,13 +119,10 @@ __global__ void uniform_times_kernel(unsigned long long seed, long long first, l
          q += (long long)gridDim.x * blockDim.x) {
         const int m = (int)(q / S);
         const long long s = q - (long long)m * S;
-        const unsigned long long n = (unsigned long long)(first + s);
-        const uint4 w = philox4x32_10(make_uint4((unsigned)n, (unsigned)(n >> 32), (unsigned)m, 0u), (unsigned)seed,
-                                      (unsigned)(seed >> 32));
-        const unsigned long long a = (((unsigned long long)w.y << 32) | w.x) >> 11;
-        const unsigned long long b = (((unsigned long long)w.w << 32) | w.z) >> 11;
-        t[(long long)(2 * m) * t_ld + s] = beta * ((double)a * 0x1.0p-53);
-        if (2 * m + 1 < D) t[(long long)(2 * m + 1) * t_ld + s] = beta * ((double)b * 0x1.0p-53);
+        double a, b;
+        uniform_time_pair(seed, (unsigned long long)(first + s), m, beta, a, b);
+        t[(long long)(2 * m) * t_ld + s] = a;
+        if (2 * m + 1 < D) t[(long long)(2 * m + 1) * t_ld + s] = b;
     }
 }
 
