@@ -474,7 +474,7 @@ def run_serving(args, rank, world, local):
     FP32/FP64-mixed mode next to one-request-at-a-time plain FP64."""
     import torch
     import paper_2501_00675_gb300 as cg
-    from paper_2501_00675_gb300.serve import RequestSpec, Server, latency_summary, poisson_run
+    from paper_2501_00675_gb300.serve import RequestSpec, ResidentScheduler, Server, latency_summary, poisson_run
     from workloads import serving_pool
 
     torch.cuda.set_device(local)
@@ -492,15 +492,22 @@ def run_serving(args, rank, world, local):
 
     def one(rate, duration):
         res = {}
-        for name, kw in (("batched_mixed", dict(mode=cg.COS_MODE_FP32_MIXED, max_batch=64, streams=2)),
+        for name, kw in (("resident_mixed", dict(mode=cg.COS_MODE_FP32_MIXED)),
+                         ("batched_mixed", dict(mode=cg.COS_MODE_FP32_MIXED, max_batch=64, streams=2)),
                          ("plain_fp64", dict(mode=cg.COS_MODE_FP64, single=True))):
-            srv = Server(pool, budget_bytes=budget, max_queue=args.max_queue, **kw)
+            if name.startswith("resident"):
+                srv = ResidentScheduler(pool, budget_bytes=budget, max_queue=args.max_queue, **kw)
+            else:
+                srv = Server(pool, budget_bytes=budget, max_queue=args.max_queue, **kw)
             reqs, wall = poisson_run(srv, specs, rate_per_s=rate, duration_s=duration, seed=rank)
             summ = latency_summary(reqs)
             summ.update({"offered": len(reqs), "shed": int(sum(r.status == "shed" for r in reqs)),
                          "failed": int(sum(r.status == "failed" for r in reqs)), "wall_s": wall,
                          "edge_sample_updates_per_s": srv.units_done / wall,
-                         "peak_admitted_gb": srv.ctrl.peak / (1 << 30)})
+                         "peak_admitted_gb": (srv.reserved if name.startswith("resident") else srv.ctrl.peak)
+                         / (1 << 30)})
+            if name.startswith("resident"):
+                summ["kernel_launches"] = srv.srv.stats()["launches"]
             res[name] = summ
             srv.close()
         return res

@@ -433,14 +433,16 @@ int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, doub
  * kernel keeps running while requests arrive; a request is one evaluation of a
  * graph handle (Fig. 1; Sec. II.C) over counter-based uniform sample times drawn
  * on the device (the generator of cos_set_samples_uniform), cut into the same
- * work items as a batched launch.  Submitting appends the request's items to a
- * task queue in device memory through host-to-device copies on a stream of the
- * server's own, so a request admitted while the kernel runs starts as soon as the
- * items queued before it are handed out -- no launch boundary, and no kernel has
- * to run to admit it.  Items are handed out in submission order.  CTAs that find
- * no work for idle_ms leave; the next submit, poll or wait relaunches the kernel
- * when work is pending.  Completion is reported through host-mapped records that
- * poll and wait read without synchronising a stream.
+ * work items as a batched launch.  The host feeds the tasks of all active requests
+ * into a task queue in device memory round-robin (one task per request per round,
+ * as the batched plan interleaves graphs), through host-to-device copies on a
+ * stream of the server's own, keeping a bounded backlog ahead of the kernel: a
+ * request admitted while the kernel runs joins the rotation within that backlog --
+ * no launch boundary, and no kernel has to run to admit it.  Feeding happens inside
+ * submit, poll, wait and stats, so a caller with requests in flight keeps calling
+ * poll or wait.  CTAs that find no work for idle_ms leave; the next call relaunches
+ * the kernel when work is pending.  Completion is reported through host-mapped
+ * records that poll and wait read without synchronising a stream.
  *
  *   cos_server_create  mode (one per server); max_times = the largest D of the
  *                      graphs to be served (sizes shared memory); tuning (NULL or
@@ -449,7 +451,8 @@ int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, doub
  *                      default 10000), window_chunks, prefetch; layout must be 0 or
  *                      1 (wide).  max_requests (default 256) request slots;
  *                      queue_tasks (default 65536, rounded up to a power of two)
- *                      task entries; idle_ms (default 50).  Allocates everything
+ *                      task entries (the backlog is min(queue_tasks/2, 16384));
+ *                      idle_ms (default 50).  Allocates everything
  *                      it will use (nothing is allocated while serving).  The
  *                      server belongs to the device current at creation.
  *   cos_server_submit  evaluate handle g over num_samples samples numbered
@@ -463,8 +466,8 @@ int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, doub
  *                      handle serves one request at a time (COS_ERR_STATE while
  *                      busy: use cos_graph_share for concurrent requests on one
  *                      graph).  *request_id receives the request number.
- *                      COS_ERR_BUSY: no free request slot or queue space (nothing
- *                      changed; collect results and retry).
+ *                      COS_ERR_BUSY: no free request slot (nothing changed;
+ *                      collect results and retry).
  *   cos_server_poll    COS_OK with *mean_out (may be NULL) once the request is
  *                      complete (the request is then collected and its id becomes
  *                      invalid), COS_ERR_BUSY while it runs, or its error
@@ -474,7 +477,8 @@ int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, doub
  *   cos_server_wait    poll until not busy or timeout_ms (< 0: no limit) passed
  *                      (then COS_ERR_TIMEOUT; the request stays pending).
  *   cos_server_stats   counters (below).
- *   cos_server_destroy let the kernel finish the queued work, then free everything.
+ *   cos_server_destroy finish every submitted request (unless the server failed),
+ *                      stop the kernel, free everything.
  * One host thread per server.  Sample times of a request live in the handle's own
  * buffer until its next request; per_sample_out is written before completion is
  * reported.
@@ -484,7 +488,7 @@ typedef struct cos_server_info {
     int64_t launches;         /* kernel launches so far (1 + relaunches after idle exits) */
     int64_t completed;        /* requests completed */
     int64_t in_flight;        /* requests submitted and not complete */
-    int64_t queued_tasks;     /* task entries held by requests not yet retired */
+    int64_t queued_tasks;     /* task entries published and not yet complete (in order) */
     int64_t published_tasks;  /* tasks published since creation */
     int32_t running;          /* 1 while the kernel has CTAs resident */
     int32_t grid;             /* CTAs per launch */

@@ -5,24 +5,33 @@
 // Requests are graph evaluations (Fig. 1; Sec. II.C) over counter-based uniform
 // sample times drawn on the device.  The host turns each request into the same
 // task chain as a batched launch (times, coefficients, per window of sample chunks
-// propagators and levels 1..L-1, partial sums, final mean) and appends it to a task
-// ring in device memory; the ring entries, the request's walker parameters, the
-// per-slot claim words and finally the published-task counter are written by
-// host-to-device copies on one copy stream, so the counter is never seen before
-// what it publishes.  The kernel never waits for a copy and no kernel has to run
-// to admit a request.
+// propagators and levels 1..L-1, partial sums, final mean) and feeds the chains of
+// all active requests into a task ring in device memory round-robin, one task per
+// request per round (consecutive tasks are then independent, as in the batched
+// plan), keeping a bounded backlog ahead of the kernel's cursor so that a new
+// request joins the rotation within that backlog.  Ring entries, claim words and
+// finally the published-task counter are written by host-to-device copies on one
+// copy stream, so the counter is never seen before what it publishes; no kernel has
+// to run to admit a request.  The host feeds from every submit, poll, wait and
+// stats call.
 //
 // Claiming: a global cursor names the task whose items are handed out; a CTA reads
-// the cursor, checks that the task is published and that the slot's claim word
-// carries the task's tag (the low 32 bits of its absolute index), and takes the
-// next item by compare-and-swap on that word; a task whose items are all handed
-// out moves the cursor on.  Items are therefore handed out in task order, and a
+// the cursor and, if that task is published, takes an item by one fetch-and-add on
+// the slot's claim word, (tag << 32) | (2^31 + items left): the tag is the low 32
+// bits of the task's absolute index, and counting down from the bias never borrows
+// into it.  The returned value names the item (or, if the slot already holds a
+// later task, an item of that task, which is as good a claim); a task whose items
+// are all handed out moves the cursor on.  No compare-and-swap retry is on the
+// path of an item.  Items are therefore handed out in task order, and a
 // CTA holds a claimed item only while it runs, so the lowest unfinished item can
 // always run (its dependencies are earlier tasks): no co-residency is required and
 // an idle CTA, which holds nothing, may leave at any time.  Completion counters
 // per ring slot are cumulative over the tasks the slot has held (a task is
-// complete once its slot's counter reaches the value the host assigned), so no
-// counter is ever reset while a late increment could still arrive.
+// complete once its slot's counter reaches the value the host assigned, which
+// every dependent carries in its own descriptor); the CTA that completes a task
+// flags it in host-mapped memory, and the host reuses ring entries in order once
+// they are flagged.  A published task never needs a later one, so the ring always
+// drains.
 //
 // Every wait is bounded: dependency waits by the tuning's timeout (then the error
 // is recorded and every CTA leaves), the idle poll by the server's idle time (then
@@ -45,10 +54,9 @@ namespace cosgpu {
 namespace {
 
 struct SvTask {
-    int64_t self;       // absolute task index; its ring slot is self & mask
+    int64_t self;       // absolute task index (publication order); its ring slot is self & mask
     int64_t seq;        // request number (key of the CTAs' parameter cache)
     int64_t tix;        // tile index (TK_TIMES: number of the request's first sample)
-    int64_t dep;        // absolute index of the task that must be complete first, or -1
     int64_t join_off;   // absolute index of the first join entry
     uint64_t seed;      // TK_TIMES: generator key
     int32_t req;        // request slot: walker parameters and completion record
@@ -57,6 +65,8 @@ struct SvTask {
     int32_t items;
     int32_t c0;
     int32_t join_cnt;
+    int32_t dep_slot;   // ring slot of the task that must be complete first, or -1 ...
+    uint32_t dep_need;  // ... and the value that slot's counter has reached then
     uint32_t need;      // value of done[self & mask] once this task is complete
     int32_t pad;
 };
@@ -88,14 +98,16 @@ struct SvStatus {               // host-mapped
 
 struct ServeArgs {
     const SvTask* ring;
-    const long long* joins;
+    const unsigned long long* joins;   // (ring slot << 32) | counter value, per join
     const WalkParams* params;
-    unsigned long long* claim;  // [cap]: (task tag << 32) | items handed out
+    unsigned long long* claim;  // [cap]: (task tag << 32) | (2^31 + items not yet handed out)
     unsigned* done;             // [cap]: items completed, cumulative over the slot's tasks
     SvCtl* ctl;
     const SvPub* pub;
     SvComp* comp;               // device alias of the mapped completion records
     SvStatus* status;           // device alias of the mapped status
+    unsigned* tdone;            // device alias of the mapped task-complete flags [cap] (task tag)
+    unsigned long long* cursor_out;   // device alias of the mapped cursor copy
     long long mask;
     long long jmask;
     long long timeout_ns;
@@ -124,7 +136,7 @@ __device__ __forceinline__ void sv_fail(const ServeArgs& a, int code, long long 
 }
 
 // One attempt to claim an item (thread 0).  Returns 1 with (k, item), 0 when every
-// published item is handed out, 2 when items were left but the attempts lost races.
+// published item is handed out, 2 when 64 tasks in a row turned out exhausted.
 __device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out, int& item_out) {
     for (int attempt = 0; attempt < 64; ++attempt) {
         const long long k = ld_volatile_s64(&a.ctl->cursor);
@@ -132,22 +144,20 @@ __device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out
             pub = ld_acquire_gpu_s64(&a.pub->tasks);
             if (k >= pub) return 0;
         }
-        const long long s = k & a.mask;
-        const unsigned long long w = ld_volatile_u64(a.claim + s);
-        const int tag_age = (int)((unsigned)k - (unsigned)(w >> 32));
-        if (tag_age > 0) return 0;   // not yet initialised for k (cannot happen once k is published)
-        const int items = __ldcg(&a.ring[s].items);
-        if (tag_age == 0 && (unsigned)w < (unsigned)items) {
-            if (atomicCAS(a.claim + s, w, w + 1) == w) {
-                k_out = k;
-                item_out = (int)(unsigned)w;
-                return 1;
-            }
-            continue;
+        const unsigned long long old = atomicAdd(a.claim + (k & a.mask), ~0ull);   // minus one
+        const int age = (int)((unsigned)(old >> 32) - (unsigned)k);   // > 0: the slot holds a later task
+        const unsigned left = (unsigned)old;
+        if (age < 0) return 0;   // not yet initialised for k (cannot happen once k is published)
+        if (left > 0x80000000u) {
+            k_out = k + age;
+            item_out = (int)(left - 0x80000001u);
+            return 1;
         }
-        // task k is exhausted (or its slot already holds a later task): move the cursor on
-        atomicCAS(reinterpret_cast<unsigned long long*>(&a.ctl->cursor), (unsigned long long)k,
-                  (unsigned long long)(k + 1));
+        // task k is exhausted: move the cursor on
+        if (atomicCAS(reinterpret_cast<unsigned long long*>(&a.ctl->cursor), (unsigned long long)k,
+                      (unsigned long long)(k + 1)) == (unsigned long long)k)   // for the host's feeder
+            asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(a.cursor_out), "l"((unsigned long long)(k + 1))
+                         : "memory");
     }
     return 2;
 }
@@ -234,11 +244,19 @@ __global__ void __launch_bounds__(kThreads, (MODE == COS_MODE_FP64 && V > 2) ? 2
                 const unsigned long long t0 = global_timer_ns();
                 unsigned long long spin = 0;
                 for (int q = -1; ok && q < s_tk.join_cnt; ++q) {
-                    const long long dep = q < 0 ? s_tk.dep : __ldcg(a.joins + ((s_tk.join_off + q) & a.jmask));
-                    if (dep < 0) continue;
-                    const unsigned need = __ldcg(&a.ring[dep & a.mask].need);
+                    int dslot;
+                    unsigned need;
+                    if (q < 0) {
+                        dslot = s_tk.dep_slot;
+                        need = s_tk.dep_need;
+                    } else {
+                        const unsigned long long j = __ldcg(a.joins + ((s_tk.join_off + q) & a.jmask));
+                        dslot = (int)(j >> 32);
+                        need = (unsigned)j;
+                    }
+                    if (dslot < 0) continue;
                     for (;; ++spin) {
-                        if ((int)(ld_acquire_gpu_u32(a.done + (dep & a.mask)) - need) >= 0) break;
+                        if ((int)(ld_acquire_gpu_u32(a.done + dslot) - need) >= 0) break;
                         if (ld_volatile_s32(&a.ctl->err) != 0) { ok = 0; break; }
                         if ((spin & 31) == 31 &&
                             ((long long)(global_timer_ns() - t0) > a.timeout_ns || spin > (1ull << 32))) {
@@ -282,8 +300,17 @@ __global__ void __launch_bounds__(kThreads, (MODE == COS_MODE_FP64 && V > 2) ? 2
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            if (s_tk.kind != TK_STALL)   // release: the item's writes are visible first
-                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.done + (k & a.mask)) : "memory");
+            if (s_tk.kind != TK_STALL) {   // release: the item's writes are visible first
+                unsigned old;
+                asm volatile("atom.release.gpu.global.add.u32 %0, [%1], 1;"
+                             : "=r"(old)
+                             : "l"(a.done + (k & a.mask))
+                             : "memory");
+                if (old + 1u == s_tk.need)   // the task's last item: its ring entry may be reused
+                    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.tdone + (k & a.mask)),
+                                 "r"((unsigned)s_tk.self)
+                                 : "memory");
+            }
             if (s_tk.kind == TK_FINAL) {   // the mean (written above by this thread), then the request number
                 SvComp* c = a.comp + s_tk.req;
                 asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(&c->seq), "l"((unsigned long long)s_tk.seq)
@@ -319,6 +346,11 @@ const void* select_serve_kernel(int mode, int vec) {
     }
 }
 
+// Sources of the published-counter copies: a ring of kPubRing values, reused in
+// blocks of kPubBlock once the copies of the block's previous use have run.
+constexpr int kPubRing = 4096;
+constexpr int kPubBlock = 64;
+
 int64_t pow2_at_least(int64_t x) {
     int64_t c = 1;
     while (c < x) c <<= 1;
@@ -338,12 +370,13 @@ struct cos_server {
     cos_tuning force{};
     int32_t max_req = 0;
     int64_t cap = 0, jcap = 0;
+    int64_t backlog = 0;             // tasks published ahead of the kernel's cursor at most
     int grid = 0, smem = 0;
     const void* kernel = nullptr;
     long long timeout_ns = 0, idle_ns = 0;
     // device
     SvTask* d_ring = nullptr;
-    long long* d_joins = nullptr;
+    unsigned long long* d_joins = nullptr;
     WalkParams* d_params = nullptr;
     unsigned long long* d_claim = nullptr;
     unsigned* d_done = nullptr;
@@ -351,22 +384,29 @@ struct cos_server {
     SvPub* d_pub = nullptr;
     // pinned host mirrors (sources of the publishing copies)
     SvTask* h_ring = nullptr;
-    long long* h_joins = nullptr;
+    unsigned long long* h_joins = nullptr;
     WalkParams* h_params = nullptr;
     unsigned long long* h_claim = nullptr;
-    long long* h_pubval = nullptr;   // [max_req]: the counter value each request publishes
+    long long* h_pubval = nullptr;   // [kPubRing]: sources of the counter copies
+    cudaEvent_t pub_ev[kPubRing / kPubBlock] = {};
+    int64_t n_pub = 0;
     int* h_one = nullptr;            // 1, the shutdown flag's source
     // host-mapped records written by the kernel
     SvComp* h_comp = nullptr;
     SvComp* d_comp = nullptr;
     SvStatus* h_status = nullptr;
     SvStatus* d_status = nullptr;
+    unsigned* h_tdone = nullptr;     // [cap]: tag of the last task completed in each ring slot
+    unsigned* d_tdone = nullptr;
+    unsigned long long* h_cursor = nullptr;
+    unsigned long long* d_cursor = nullptr;
     cudaStream_t ks = nullptr, cs = nullptr;
     cudaEvent_t kdone = nullptr, cev = nullptr;
     bool running = false;
     int failed = 0;                  // cos_status once the kernel has reported an error
     int64_t next_task = 0, tail_task = 0, next_join = 0, tail_join = 0, next_seq = 1;
-    std::vector<uint32_t> slot_total;
+    std::vector<uint32_t> slot_total;   // per ring slot: items of every task it has held
+    std::vector<int64_t> join_end;      // per ring slot: next_join after its task's joins
     struct Req {
         int64_t seq = 0;
         cos_graph_t g = nullptr;
@@ -374,14 +414,16 @@ struct cos_server {
         int overflow = 0;
         int err = 0;
         double mean = 0.0;
+        uint64_t seed = 0;
+        int64_t first_sample = 0;
+        std::vector<Task> tasks;                 // the request's chain (local dep indices)
+        std::vector<std::vector<int32_t>> joins;
+        size_t next = 0;                         // tasks published so far
+        std::vector<int32_t> slot_of;            // ring slot of each published task
+        std::vector<uint32_t> need_of;           // its completion value
     };
     std::vector<Req> reqs;
-    struct Span {
-        int64_t seq;
-        int32_t slot;
-        int64_t t_end, j_end;
-    };
-    std::deque<Span> fifo;           // ring space in publication order
+    std::deque<int32_t> feeding;     // request slots with tasks left to publish, oldest first
     int64_t launches = 0, completed = 0;
 };
 
@@ -409,6 +451,10 @@ void free_server(Srv* s) {
     cudaFreeHost(s->h_one);
     cudaFreeHost(s->h_comp);
     cudaFreeHost(s->h_status);
+    cudaFreeHost(s->h_tdone);
+    cudaFreeHost(s->h_cursor);
+    for (cudaEvent_t& e : s->pub_ev)
+        if (e) cudaEventDestroy(e);
     if (s->kdone) cudaEventDestroy(s->kdone);
     if (s->cev) cudaEventDestroy(s->cev);
     if (s->ks) cudaStreamDestroy(s->ks);
@@ -438,7 +484,7 @@ void check_kernel(Srv* s) {
     }
 }
 
-// Completion records -> requests; ring space of finished requests, oldest first.
+// Completion records -> requests; ring entries of completed tasks, in order.
 void collect(Srv* s) {
     for (int32_t r = 0; r < s->max_req; ++r) {
         Srv::Req& q = s->reqs[(size_t)r];
@@ -453,14 +499,114 @@ void collect(Srv* s) {
             q.done = true;
         }
     }
-    while (!s->fifo.empty()) {
-        const Srv::Span& f = s->fifo.front();
-        const Srv::Req& q = s->reqs[(size_t)f.slot];
-        if (q.seq == f.seq && !q.done) break;
-        s->tail_task = f.t_end;
-        s->tail_join = f.j_end;
-        s->fifo.pop_front();
+    while (s->tail_task < s->next_task) {
+        const int64_t at = s->tail_task & (s->cap - 1);
+        if (*(volatile unsigned*)&s->h_tdone[at] != (unsigned)s->tail_task) break;
+        s->tail_join = s->join_end[(size_t)at];
+        s->tail_task++;
     }
+    __atomic_thread_fence(__ATOMIC_ACQUIRE);
+}
+
+// Copy entries [first, first + n) of a ring of `cap` entries (wrapping) to the device.
+template <typename T>
+cudaError_t copy_ring(T* dst, const T* src, int64_t cap, int64_t first, int64_t n, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    while (n > 0 && e == cudaSuccess) {
+        const int64_t at = first & (cap - 1);
+        const int64_t m = std::min(n, cap - at);
+        e = cudaMemcpyAsync(dst + at, src + at, sizeof(T) * (size_t)m, cudaMemcpyHostToDevice, st);
+        first += m;
+        n -= m;
+    }
+    return e;
+}
+
+// Write one task of request slot r into the ring mirrors at position next_task.
+void stage_task(Srv* s, int32_t r) {
+    Srv::Req& q = s->reqs[(size_t)r];
+    const size_t li = q.next++;
+    const Task& t = q.tasks[li];
+    const int64_t self = s->next_task++;
+    const int64_t at = self & (s->cap - 1);
+    SvTask& e = s->h_ring[at];
+    memset(&e, 0, sizeof(e));
+    e.self = self;
+    e.seq = q.seq;
+    e.tix = t.kind == TK_TIMES ? q.first_sample : t.tix;
+    e.seed = q.seed;
+    e.req = r;
+    e.kind = t.kind;
+    e.level = t.level;
+    e.items = t.items;
+    e.c0 = t.c0;
+    e.dep_slot = t.dep >= 0 ? q.slot_of[(size_t)t.dep] : -1;
+    e.dep_need = t.dep >= 0 ? q.need_of[(size_t)t.dep] : 0u;
+    e.join_off = s->next_join;
+    e.join_cnt = (int32_t)q.joins[li].size();
+    for (int32_t d : q.joins[li])
+        s->h_joins[s->next_join++ & (s->jcap - 1)] =
+            ((unsigned long long)(uint32_t)q.slot_of[(size_t)d] << 32) | q.need_of[(size_t)d];
+    s->slot_total[(size_t)at] += (uint32_t)t.items;
+    e.need = s->slot_total[(size_t)at];
+    s->join_end[(size_t)at] = s->next_join;
+    s->h_claim[at] = ((unsigned long long)(uint32_t)self << 32) | (0x80000000ull + (uint32_t)t.items);
+    q.slot_of.push_back((int32_t)at);
+    q.need_of.push_back(e.need);
+    if (t.items == 0) *(volatile unsigned*)&s->h_tdone[at] = (unsigned)self;   // complete as soon as published
+}
+
+// Publish the counter value v: its source stays untouched until the copy has run.
+int publish_counter(Srv* s, long long v) {
+    const int64_t n = s->n_pub++;
+    const int i = (int)(n % kPubRing);
+    cudaError_t e = cudaSuccess;
+    if (n >= kPubRing && i % kPubBlock == 0) e = cudaEventSynchronize(s->pub_ev[i / kPubBlock]);
+    if (e == cudaSuccess) {
+        s->h_pubval[i] = v;
+        e = cudaMemcpyAsync(&s->d_pub->tasks, s->h_pubval + i, sizeof(long long), cudaMemcpyHostToDevice, s->cs);
+    }
+    if (e == cudaSuccess && i % kPubBlock == kPubBlock - 1) e = cudaEventRecord(s->pub_ev[i / kPubBlock], s->cs);
+    return e == cudaSuccess ? COS_OK : cuda_err(e, "publish counter");
+}
+
+// Feed the ring: one task per active request per round, oldest request first, while
+// the backlog ahead of the kernel's cursor and the free ring space allow.
+int feed(Srv* s) {
+    if (s->feeding.empty()) return COS_OK;
+    const int64_t cursor = (int64_t)*(volatile unsigned long long*)s->h_cursor;
+    int64_t room = std::min(s->backlog - (s->next_task - cursor), s->cap - (s->next_task - s->tail_task));
+    if (room <= 0) return COS_OK;
+    const int64_t t0 = s->next_task, j0 = s->next_join;
+    bool progress = true;
+    while (room > 0 && progress) {
+        progress = false;
+        for (int32_t r : s->feeding) {
+            if (room <= 0) break;
+            Srv::Req& q = s->reqs[(size_t)r];
+            if (q.next >= q.tasks.size()) continue;
+            if (s->next_join + (int64_t)q.joins[q.next].size() - s->tail_join > s->jcap) {
+                room = 0;
+                break;
+            }
+            stage_task(s, r);
+            --room;
+            progress = true;
+        }
+    }
+    for (auto it = s->feeding.begin(); it != s->feeding.end();) {
+        const Srv::Req& q = s->reqs[(size_t)*it];
+        it = q.next >= q.tasks.size() ? s->feeding.erase(it) : it + 1;
+    }
+    if (s->next_task == t0) return COS_OK;
+    // descriptors and joins, then the claim words (a CTA that finds a new tag may run the
+    // task at once), then the counter (one stream, in order)
+    cudaError_t e = copy_ring(s->d_ring, s->h_ring, s->cap, t0, s->next_task - t0, s->cs);
+    if (e == cudaSuccess) e = copy_ring(s->d_joins, s->h_joins, s->jcap, j0, s->next_join - j0, s->cs);
+    if (e == cudaSuccess) e = copy_ring(s->d_claim, s->h_claim, s->cap, t0, s->next_task - t0, s->cs);
+    int rc = e == cudaSuccess ? publish_counter(s, s->next_task) : cuda_err(e, "publish tasks");
+    if (rc != COS_OK) s->failed = COS_ERR_CUDA;   // the mirrors have moved on: the server cannot continue
+    return rc;
 }
 
 int launch(Srv* s) {
@@ -474,6 +620,8 @@ int launch(Srv* s) {
     a.pub = s->d_pub;
     a.comp = s->d_comp;
     a.status = s->d_status;
+    a.tdone = s->d_tdone;
+    a.cursor_out = s->d_cursor;
     a.mask = s->cap - 1;
     a.jmask = s->jcap - 1;
     a.timeout_ns = s->timeout_ns;
@@ -491,28 +639,19 @@ int launch(Srv* s) {
     return COS_OK;
 }
 
-// Kernel exit, completions, and a relaunch when work is pending and no CTA is left.
+// Kernel exit, completions, feeding, and a relaunch when work is pending and no CTA is left.
 int pump(Srv* s) {
     check_kernel(s);
     collect(s);
-    if (s->failed || s->running) return COS_OK;
+    if (s->failed) {
+        s->feeding.clear();
+        return COS_OK;
+    }
+    int rc = feed(s);
+    if (rc != COS_OK || s->running) return rc;
     for (const Srv::Req& q : s->reqs)
         if (q.active && !q.done) return launch(s);
     return COS_OK;
-}
-
-// Copy entries [first, first + n) of a ring of `cap` entries (wrapping) to the device.
-template <typename T>
-cudaError_t copy_ring(T* dst, const T* src, int64_t cap, int64_t first, int64_t n, cudaStream_t st) {
-    cudaError_t e = cudaSuccess;
-    while (n > 0 && e == cudaSuccess) {
-        const int64_t at = first & (cap - 1);
-        const int64_t m = std::min(n, cap - at);
-        e = cudaMemcpyAsync(dst + at, src + at, sizeof(T) * (size_t)m, cudaMemcpyHostToDevice, st);
-        first += m;
-        n -= m;
-    }
-    return e;
 }
 
 int find_request(Srv* s, int64_t id) {
@@ -567,6 +706,7 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
     s->max_req = max_requests > 0 ? max_requests : 256;
     s->cap = pow2_at_least(std::max<int64_t>(queue_tasks > 0 ? queue_tasks : 65536, 64));
     s->jcap = s->cap;
+    s->backlog = std::min<int64_t>(s->cap / 2, 16384);
     s->timeout_ns = (long long)(t.timeout_ms > 0 ? t.timeout_ms : 10000) * 1000000LL;
     s->idle_ns = (long long)(idle_ms > 0 ? idle_ms : 50) * 1000000LL;
     s->kernel = select_serve_kernel(mode, s->vec);
@@ -591,27 +731,33 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
         const size_t nr = (size_t)s->max_req;
         const size_t cap = (size_t)s->cap, jcap = (size_t)s->jcap;
         if ((e = cudaMalloc(&s->d_ring, sizeof(SvTask) * cap)) != cudaSuccess ||
-            (e = cudaMalloc(&s->d_joins, sizeof(long long) * jcap)) != cudaSuccess ||
+            (e = cudaMalloc(&s->d_joins, sizeof(unsigned long long) * jcap)) != cudaSuccess ||
             (e = cudaMalloc(&s->d_params, sizeof(WalkParams) * nr)) != cudaSuccess ||
             (e = cudaMalloc(&s->d_claim, sizeof(unsigned long long) * cap)) != cudaSuccess ||
             (e = cudaMalloc(&s->d_done, sizeof(unsigned) * cap)) != cudaSuccess ||
             (e = cudaMalloc(&s->d_ctl, sizeof(SvCtl))) != cudaSuccess ||
             (e = cudaMalloc(&s->d_pub, sizeof(SvPub))) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_ring, sizeof(SvTask) * cap)) != cudaSuccess ||
-            (e = cudaMallocHost(&s->h_joins, sizeof(long long) * jcap)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_joins, sizeof(unsigned long long) * jcap)) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_params, sizeof(WalkParams) * nr)) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_claim, sizeof(unsigned long long) * cap)) != cudaSuccess ||
-            (e = cudaMallocHost(&s->h_pubval, sizeof(long long) * nr)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_pubval, sizeof(long long) * kPubRing)) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_one, sizeof(int))) != cudaSuccess ||
             (e = cudaHostAlloc(&s->h_comp, sizeof(SvComp) * nr, cudaHostAllocMapped)) != cudaSuccess ||
             (e = cudaHostAlloc(&s->h_status, sizeof(SvStatus), cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostAlloc(&s->h_tdone, sizeof(unsigned) * cap, cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostAlloc(&s->h_cursor, sizeof(unsigned long long), cudaHostAllocMapped)) != cudaSuccess ||
             (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_comp), s->h_comp, 0)) != cudaSuccess ||
-            (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_status), s->h_status, 0)) != cudaSuccess)
+            (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_status), s->h_status, 0)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_tdone), s->h_tdone, 0)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_cursor), s->h_cursor, 0)) != cudaSuccess)
             rc = set_error(COS_ERR_OOM, "server buffers: %s", cudaGetErrorString(e));
     }
     if (rc == COS_OK) {
         memset(s->h_comp, 0, sizeof(SvComp) * (size_t)s->max_req);
         memset(s->h_status, 0, sizeof(SvStatus));
+        for (int64_t i = 0; i < s->cap; ++i) s->h_tdone[i] = (unsigned)(i - s->cap);   // no task's tag yet
+        *s->h_cursor = 0;
         *s->h_one = 1;
         if ((e = cudaMemset(s->d_claim, 0, sizeof(unsigned long long) * (size_t)s->cap)) != cudaSuccess ||
             (e = cudaMemset(s->d_done, 0, sizeof(unsigned) * (size_t)s->cap)) != cudaSuccess ||
@@ -620,9 +766,12 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
             (e = cudaStreamCreateWithFlags(&s->ks, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&s->kdone, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&s->cev, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaDeviceSynchronize()) != cudaSuccess)
+            (e = cudaEventCreateWithFlags(&s->cev, cudaEventDisableTiming)) != cudaSuccess)
             rc = cuda_err(e, "server set-up");
+        for (cudaEvent_t& ev : s->pub_ev)
+            if (rc == COS_OK && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                rc = cuda_err(e, "server set-up");
+        if (rc == COS_OK && (e = cudaDeviceSynchronize()) != cudaSuccess) rc = cuda_err(e, "server set-up");
     }
     if (rc != COS_OK) {
         free_server(s);
@@ -630,6 +779,7 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
         return rc;
     }
     s->slot_total.assign((size_t)s->cap, 0u);
+    s->join_end.assign((size_t)s->cap, 0);
     s->reqs.assign((size_t)s->max_req, Srv::Req{});
     *out = s;
     return COS_OK;
@@ -667,69 +817,29 @@ int cos_server_submit(cos_server_t s, cos_graph_t g, int64_t num_samples, uint64
         return rc;
     }
     p.mean_out = &s->d_comp[slot].mean;
-    std::vector<Task> list;
-    std::vector<std::vector<int32_t>> js;
-    graph_task_chain(p, gv.widths_host, s->mode, 32 * s->vec, s->force.window_chunks > 0 ? s->force.window_chunks : tn.window_chunks,
-                     slot, s->mode != COS_MODE_COUNT_I64, getenv("COS_TEST_STALL_TASK") != nullptr, list, js);
-    const int64_t nt = (int64_t)list.size();
-    int64_t nj = 0;
-    for (auto& j : js) nj += (int64_t)j.size();
-    if (nt > s->cap - (s->next_task - s->tail_task) || nj > s->jcap - (s->next_join - s->tail_join)) {
-        restore_samples(g, undo);
-        if (nt > s->cap || nj > s->jcap)
-            return set_error(COS_ERR_INVALID, "request needs %lld tasks; the queue holds %lld", (long long)nt, (long long)s->cap);
-        return set_error(COS_ERR_BUSY, "task queue full (%lld of %lld in use)", (long long)(s->next_task - s->tail_task),
-                         (long long)s->cap);
-    }
-    const int64_t seq = s->next_seq;
-    int64_t joff = 0;
-    for (int64_t i = 0; i < nt; ++i) {
-        const Task& t = list[(size_t)i];
-        const int64_t self = s->next_task + i;
-        const int64_t at = self & (s->cap - 1);
-        SvTask& e = s->h_ring[at];
-        memset(&e, 0, sizeof(e));
-        e.self = self;
-        e.seq = seq;
-        e.tix = t.kind == TK_TIMES ? first_sample : t.tix;
-        e.dep = t.dep >= 0 ? s->next_task + t.dep : -1;
-        e.join_off = s->next_join + joff;
-        e.seed = seed;
-        e.req = slot;
-        e.kind = t.kind;
-        e.level = t.level;
-        e.items = t.items;
-        e.c0 = t.c0;
-        e.join_cnt = (int32_t)js[(size_t)i].size();
-        s->slot_total[(size_t)at] += (uint32_t)t.items;
-        e.need = s->slot_total[(size_t)at];
-        s->h_claim[at] = (unsigned long long)(uint32_t)self << 32;
-        for (int32_t d : js[(size_t)i]) s->h_joins[(s->next_join + joff++) & (s->jcap - 1)] = s->next_task + d;
-    }
-    s->h_params[slot] = p;
-    s->h_pubval[slot] = s->next_task + nt;
-    // publish: parameters, descriptors, claim words, joins, then the counter (one stream, in order)
-    cudaError_t e = cudaMemcpyAsync(s->d_params + slot, s->h_params + slot, sizeof(WalkParams), cudaMemcpyHostToDevice, s->cs);
-    if (e == cudaSuccess) e = copy_ring(s->d_ring, s->h_ring, s->cap, s->next_task, nt, s->cs);
-    if (e == cudaSuccess) e = copy_ring(s->d_claim, s->h_claim, s->cap, s->next_task, nt, s->cs);
-    if (e == cudaSuccess) e = copy_ring(s->d_joins, s->h_joins, s->jcap, s->next_join, nj, s->cs);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&s->d_pub->tasks, s->h_pubval + slot, sizeof(long long), cudaMemcpyHostToDevice, s->cs);
-    if (e != cudaSuccess) {   // the ring mirrors have moved on: the server cannot continue
-        s->failed = COS_ERR_CUDA;
-        return cuda_err(e, "publish request");
-    }
     Srv::Req& q = s->reqs[(size_t)slot];
     q = Srv::Req{};
-    q.seq = seq;
+    graph_task_chain(p, gv.widths_host, s->mode, 32 * s->vec,
+                     s->force.window_chunks > 0 ? s->force.window_chunks : tn.window_chunks, slot,
+                     s->mode != COS_MODE_COUNT_I64, getenv("COS_TEST_STALL_TASK") != nullptr, q.tasks, q.joins);
+    s->h_params[slot] = p;
+    // the parameters go ahead of every counter copy that publishes one of the request's tasks
+    cudaError_t e = cudaMemcpyAsync(s->d_params + slot, s->h_params + slot, sizeof(WalkParams), cudaMemcpyHostToDevice, s->cs);
+    if (e != cudaSuccess) {
+        q = Srv::Req{};
+        restore_samples(g, undo);
+        return cuda_err(e, "copy request parameters");
+    }
+    q.seq = s->next_seq++;
     q.g = g;
     q.active = true;
+    q.seed = seed;
+    q.first_sample = first_sample;
     q.overflow = s->mode == COS_MODE_COUNT_I64 && gv.count_overflow;
-    s->fifo.push_back(Srv::Span{seq, slot, s->next_task + nt, s->next_join + nj});
-    s->next_task += nt;
-    s->next_join += nj;
-    s->next_seq++;
-    *request_id = seq;
+    q.slot_of.reserve(q.tasks.size());
+    q.need_of.reserve(q.tasks.size());
+    s->feeding.push_back(slot);
+    *request_id = q.seq;
     return pump(s);
 }
 
@@ -742,11 +852,12 @@ int cos_server_poll(cos_server_t s, int64_t request_id, double* mean_out) {
     if (rc != COS_OK) return rc;
     Srv::Req& q = s->reqs[(size_t)r];
     if (!q.done) return COS_ERR_BUSY;
-    q.active = false;
-    q.g = nullptr;
-    if (q.err) return set_error(q.err, "request %lld failed: %s", (long long)request_id, cos_last_error());
-    if (mean_out) *mean_out = q.mean;
-    if (q.overflow) return set_error(COS_ERR_OVERFLOW, "path count exceeds 2^63-1; results wrap modulo 2^64");
+    const int err = q.err, overflow = q.overflow;
+    const double mean = q.mean;
+    q = Srv::Req{};
+    if (err) return set_error(err, "request %lld failed: %s", (long long)request_id, cos_last_error());
+    if (mean_out) *mean_out = mean;
+    if (overflow) return set_error(COS_ERR_OVERFLOW, "path count exceeds 2^63-1; results wrap modulo 2^64");
     return COS_OK;
 }
 
@@ -786,6 +897,14 @@ int cos_server_destroy(cos_server_t s) {
     int rc = COS_OK;
     {
         DevSel dev(s->device);
+        // finish every submitted request (the host keeps feeding), unless the server failed
+        for (;;) {
+            if (pump(s) != COS_OK) break;
+            bool pending = false;
+            for (const Srv::Req& q : s->reqs) pending |= q.active && !q.done;
+            if (!pending || s->failed) break;
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
         if (s->running) {
             // ask the CTAs to leave once the published work is done, then wait for them
             cudaError_t e = cudaMemcpyAsync(&s->d_pub->shutdown, s->h_one, sizeof(int), cudaMemcpyHostToDevice, s->cs);

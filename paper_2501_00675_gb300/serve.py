@@ -353,6 +353,149 @@ class Server:
         self.idle_lru.clear()
 
 
+class ResidentScheduler:
+    """Continuous batching on the resident server (cos_server_*): one persistent
+    kernel stays on the GPU and a request is handed to it as soon as a handle of its
+    graph is free, so its work items start behind those already queued instead of
+    at the next launch.  The kernel draws every request's sample times from the
+    request's seed (counter-based generator), so admitting a request runs no kernel.
+
+    Device memory is taken once, at construction: per graph one handle (workspace
+    of one tile, time buffer and result buffer of max_samples), then a second
+    handle per graph, smallest graphs first, while the budget lasts.  A request's
+    per-sample values stay in its handle's result buffer until the handle's next
+    request.  Same submit/step/drain/close interface as ``Server``.
+    """
+
+    def __init__(self, graphs, mode: int, budget_bytes: int = 150 << 30, max_samples: int = 1_000_000,
+                 handles_per_graph: int = 2, tile_samples: int = 8192, workspace_bytes: int = 512 << 20,
+                 max_queue: int = 4096, beta: float = 10.0, queue_tasks: int = 1 << 20, max_requests: int = 512,
+                 idle_ms: int = 50):
+        import torch
+        from . import binding as cg
+        self.torch, self.cg = torch, cg
+        self.graphs = [g for g, _ in graphs]
+        self.eps = [np.ascontiguousarray(e, dtype=np.float64) for _, e in graphs]
+        self.info = [g.info() for g in self.graphs]
+        self.mode, self.beta, self.tile, self.ws_bytes = mode, beta, tile_samples, workspace_bytes
+        self.max_samples = int(max_samples)
+        self.max_queue = int(max_queue)
+        D = max(i["D"] for i in self.info)
+        self.srv = cg.ResidentServer(mode, D, max_requests=max_requests, queue_tasks=queue_tasks, idle_ms=idle_ms)
+        self.free: Dict[int, List] = collections.defaultdict(list)
+        self.handles = []
+        self.reserved = 0
+        dt = torch.int64 if mode == cg.COS_MODE_COUNT_I64 else torch.float64
+        order = sorted(range(len(self.graphs)), key=self.handle_bytes)
+        for rnd in range(max(1, handles_per_graph)):
+            for gid in order:
+                need = self.handle_bytes(gid)
+                if rnd > 0 and self.reserved + need > budget_bytes:
+                    break
+                h = self.graphs[gid].share()
+                h.set_tuning(tile_samples=self.tile_for(gid))
+                h.set_samples_uniform(self.max_samples, 0, self.eps[gid], beta)
+                out = torch.empty(self.max_samples, dtype=dt, device="cuda")
+                self.free[gid].append((h, out))
+                self.handles.append(h)
+                self.reserved += need
+        torch.cuda.synchronize()
+        self.queue: Deque[Request] = collections.deque()
+        self.inflight: List[Request] = []
+        self.requests: List[Request] = []
+        self._lock = threading.Lock()
+        self._inbox: Deque[Request] = collections.deque()
+        self._rid = 0
+        self.shed = 0
+        self.units_done = 0.0
+
+    def tile_for(self, graph_id: int) -> int:
+        inf = self.info[graph_id]
+        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"]
+        return int(max(128, min(self.tile, (self.ws_bytes // psb) // 128 * 128)))
+
+    def handle_bytes(self, graph_id: int) -> int:
+        """Workspace of one tile, times [D][max_samples] and results [max_samples]."""
+        inf = self.info[graph_id]
+        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"]
+        s_pad = (self.max_samples + 127) // 128 * 128
+        return int(psb * self.tile_for(graph_id) + (8 << 20) + s_pad * 8 * (inf["D"] + 1))
+
+    def submit(self, spec: RequestSpec) -> Request:
+        with self._lock:
+            self._rid += 1
+            req = Request(spec, 0, time.perf_counter(), self._rid)
+            self._inbox.append(req)
+            self.requests.append(req)
+        return req
+
+    def step(self) -> bool:
+        """One scheduling pass; returns True if anything is queued or in flight."""
+        with self._lock:
+            while self._inbox:
+                r = self._inbox.popleft()
+                if len(self.queue) >= self.max_queue or r.spec.num_samples > self.max_samples:
+                    r.status = "shed"
+                    self.shed += 1
+                else:
+                    self.queue.append(r)
+        now = time.perf_counter()
+        still = []
+        for r in self.inflight:
+            try:
+                m = self.srv.poll(r._sid, allow_overflow=True)
+            except self.cg.CosError as exc:
+                r.status, r.error, m = "failed", str(exc), 0.0
+            if m is None:
+                still.append(r)
+                continue
+            r.t_done = now
+            if r.status != "failed":
+                r.status, r.mean = "done", float(m)
+                self.units_done += float(self.info[r.spec.graph_id]["E"]) * r.spec.num_samples
+            self.free[r.spec.graph_id].append(r._slot)
+            r._slot = None
+        self.inflight = still
+        # admission: oldest first; a request whose graph has no free handle waits
+        # without holding up requests on other graphs
+        waiting = collections.deque()
+        while self.queue:
+            r = self.queue.popleft()
+            hl = self.free[r.spec.graph_id]
+            if not hl:
+                waiting.append(r)
+                continue
+            h, out = hl[-1]
+            sid = self.srv.submit(h, r.spec.num_samples, r.spec.seed, out)
+            if sid is None:   # no request slot or queue space: try again next pass
+                waiting.append(r)
+                waiting.extend(self.queue)
+                self.queue.clear()
+                break
+            hl.pop()
+            r._sid, r._slot = sid, (h, out)
+            r.t_admit = r.t_launch = time.perf_counter()
+            r.status = "running"
+            self.inflight.append(r)
+        self.queue = waiting
+        return bool(self.inflight) or bool(self.queue) or bool(self._inbox)
+
+    def drain(self, timeout_s: float = 600.0):
+        t0 = time.perf_counter()
+        while self.step():
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError("server did not drain")
+            time.sleep(0.0002)
+
+    def close(self):
+        self.drain()
+        self.srv.close()
+        for h in self.handles:
+            h.close()
+        self.handles = []
+        self.free.clear()
+
+
 def poisson_run(server: Server, specs: Sequence[RequestSpec], rate_per_s: float, duration_s: float,
                 seed: int = 0) -> Tuple[List[Request], float]:
     """Submit specs at Poisson arrival times (rate_per_s) for at most duration_s while the

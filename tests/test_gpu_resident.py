@@ -236,3 +236,31 @@ def test_dependency_timeout_fails_server(cg):
     x = torch.ones(4, device="cuda") * 2
     assert float(x.sum()) == 8.0
     h.close()
+
+
+def test_resident_scheduler_poisson_stream(cg):
+    """The serving loop on the resident server: a Poisson stream over a small pool,
+    every request completed, its mean equal to the oracle's on the request's own
+    counter-based times, and all of it served by one kernel launch."""
+    from paper_2501_00675_gb300.serve import RequestSpec, ResidentScheduler, latency_summary, poisson_run
+    from workloads import batched
+    wls = batched(seed=11, num_graphs=5, max_nodes=2e4, max_samples=4096, min_samples=1024)
+    pool = [(cg.Graph.from_workload_graph(w.graph), w.samples.eps) for w in wls]
+    srv = ResidentScheduler(pool, mode=cg.COS_MODE_FP32_MIXED, budget_bytes=8 << 30, max_samples=6000,
+                            workspace_bytes=128 << 20, idle_ms=5000)
+    rng = np.random.default_rng(3)
+    specs = [RequestSpec(int(rng.integers(0, len(pool))), int(rng.integers(1, 6000)), 1000 + i) for i in range(30)]
+    reqs, wall = poisson_run(srv, specs, rate_per_s=400.0, duration_s=5.0)
+    done = [r for r in reqs if r.status == "done"]
+    assert len(done) == len(specs)
+    for r in done:
+        w = wls[r.spec.graph_id]
+        t = counter_times(r.spec.seed, 0, r.spec.num_samples, w.graph.num_times, srv.beta)
+        R, A = oracle.evaluate(w.graph, w.samples.eps, srv.beta, t)
+        assert abs(r.mean - R.mean()) <= TOL[1] * A.mean()
+    s = latency_summary(reqs)
+    assert s["completed"] == len(specs) and s["p99_ms"] >= s["p50_ms"] > 0
+    assert srv.srv.stats()["launches"] == 1
+    srv.close()
+    for g, _ in pool:
+        g.close()
