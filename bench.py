@@ -470,8 +470,9 @@ def run_batched(args, rank, world, local):
 # ------------------------------------------------------------------ serving
 
 def run_serving(args, rank, world, local):
-    """Poisson request stream against the resident pool: continuous batching in the
-    FP32/FP64-mixed mode next to one-request-at-a-time plain FP64."""
+    """Poisson request stream against the resident pool in the FP32/FP64-mixed mode:
+    the resident server (the headline value), batched launches on two streams, and
+    one-request-at-a-time plain FP64."""
     import torch
     import paper_2501_00675_gb300 as cg
     from paper_2501_00675_gb300.serve import RequestSpec, ResidentScheduler, Server, latency_summary, poisson_run
@@ -520,7 +521,7 @@ def run_serving(args, rank, world, local):
         g.close()
     if rank != 0:
         return None
-    b = out["batched_mixed"]
+    b = out["resident_mixed"]
     return {
         "metric": "served edge·sample updates/s", "value": b["edge_sample_updates_per_s"],
         "unit": "edge·sample updates/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak",
