@@ -494,6 +494,8 @@ typedef struct cos_server_info {
     int32_t grid;             /* CTAs per launch */
     int32_t samples_per_lane;
     int32_t failed;           /* 0, or the cos_status every pending request fails with */
+    int64_t stale_claims;     /* items claimed through a cursor value a whole queue behind (the
+                                 slot already held a later task, whose item was taken instead) */
 } cos_server_info;
 int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning, int32_t max_requests,
                       int64_t queue_tasks, int32_t idle_ms, cos_server_t* out);

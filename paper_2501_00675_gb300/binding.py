@@ -55,7 +55,8 @@ class CosError(RuntimeError):
 class CosServerInfo(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("completed", ctypes.c_int64), ("in_flight", ctypes.c_int64),
                 ("queued_tasks", ctypes.c_int64), ("published_tasks", ctypes.c_int64), ("running", ctypes.c_int32),
-                ("grid", ctypes.c_int32), ("samples_per_lane", ctypes.c_int32), ("failed", ctypes.c_int32)]
+                ("grid", ctypes.c_int32), ("samples_per_lane", ctypes.c_int32), ("failed", ctypes.c_int32),
+                ("stale_claims", ctypes.c_int64)]
 
 
 class CosTuning(ctypes.Structure):

@@ -83,6 +83,7 @@ struct SvCtl {          // device memory
     long long cursor;   // task whose items are being handed out
     int err;
     int pad;
+    unsigned long long stale_claims;   // claims whose slot already held a later task
 };
 
 struct SvComp {                 // host-mapped, one per request slot
@@ -112,6 +113,8 @@ struct ServeArgs {
     long long jmask;
     long long timeout_ns;
     long long idle_ns;
+    int test_stale;     // test hook: about one claim in test_stale reads a stale cursor (0: off)
+    int pad;
 };
 
 __device__ __forceinline__ long long ld_volatile_s64(const long long* p) { return *(const volatile long long*)p; }
@@ -139,10 +142,17 @@ __device__ __forceinline__ void sv_fail(const ServeArgs& a, int code, long long 
 // published item is handed out, 2 when 64 tasks in a row turned out exhausted.
 __device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out, int& item_out) {
     for (int attempt = 0; attempt < 64; ++attempt) {
-        const long long k = ld_volatile_s64(&a.ctl->cursor);
+        long long k = ld_volatile_s64(&a.ctl->cursor);
         if (k >= pub) {
             pub = ld_acquire_gpu_s64(&a.pub->tasks);
             if (k >= pub) return 0;
+        }
+        if (a.test_stale > 0 && pub - k > 1) {
+            // test hook: act on a cursor value one ring behind a published task t ahead of the
+            // cursor, as a CTA would that read the cursor that long ago
+            const unsigned long long h = global_timer_ns() * 0x9E3779B97F4A7C15ull + blockIdx.x;
+            if ((h >> 40) % (unsigned long long)a.test_stale == 0)
+                k = k + 1 + (long long)((h >> 20) % (unsigned long long)(pub - k - 1)) - (a.mask + 1);
         }
         const unsigned long long old = atomicAdd(a.claim + (k & a.mask), ~0ull);   // minus one
         const int age = (int)((unsigned)(old >> 32) - (unsigned)k);   // > 0: the slot holds a later task
@@ -151,6 +161,7 @@ __device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out
         if (left > 0x80000000u) {
             k_out = k + age;
             item_out = (int)(left - 0x80000001u);
+            if (age > 0) atomicAdd(&a.ctl->stale_claims, 1ull);
             return 1;
         }
         // task k is exhausted: move the cursor on
@@ -374,6 +385,8 @@ struct cos_server {
     int grid = 0, smem = 0;
     const void* kernel = nullptr;
     long long timeout_ns = 0, idle_ns = 0;
+    int test_stale = 0;              // COS_TEST_STALE_CLAIMS (test hook)
+    unsigned long long* h_stale = nullptr;   // pinned: stale-claim count read back by stats
     // device
     SvTask* d_ring = nullptr;
     unsigned long long* d_joins = nullptr;
@@ -453,6 +466,7 @@ void free_server(Srv* s) {
     cudaFreeHost(s->h_status);
     cudaFreeHost(s->h_tdone);
     cudaFreeHost(s->h_cursor);
+    cudaFreeHost(s->h_stale);
     for (cudaEvent_t& e : s->pub_ev)
         if (e) cudaEventDestroy(e);
     if (s->kdone) cudaEventDestroy(s->kdone);
@@ -626,6 +640,8 @@ int launch(Srv* s) {
     a.jmask = s->jcap - 1;
     a.timeout_ns = s->timeout_ns;
     a.idle_ns = s->idle_ns;
+    a.test_stale = s->test_stale;
+    a.pad = 0;
     cudaError_t e;
     if ((e = cudaEventRecord(s->cev, s->cs)) != cudaSuccess) return cuda_err(e, "record publish event");
     if ((e = cudaStreamWaitEvent(s->ks, s->cev, 0)) != cudaSuccess) return cuda_err(e, "order launch after publish");
@@ -709,6 +725,7 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
     s->backlog = std::min<int64_t>(s->cap / 2, 16384);
     s->timeout_ns = (long long)(t.timeout_ms > 0 ? t.timeout_ms : 10000) * 1000000LL;
     s->idle_ns = (long long)(idle_ms > 0 ? idle_ms : 50) * 1000000LL;
+    if (const char* env = getenv("COS_TEST_STALE_CLAIMS")) s->test_stale = std::max(0, atoi(env));
     s->kernel = select_serve_kernel(mode, s->vec);
     s->smem = walk_smem_bytes(mode, s->vec, 1, max_times);
     int rc = COS_OK;
@@ -743,6 +760,7 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
             (e = cudaMallocHost(&s->h_claim, sizeof(unsigned long long) * cap)) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_pubval, sizeof(long long) * kPubRing)) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_one, sizeof(int))) != cudaSuccess ||
+            (e = cudaMallocHost(&s->h_stale, sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaHostAlloc(&s->h_comp, sizeof(SvComp) * nr, cudaHostAllocMapped)) != cudaSuccess ||
             (e = cudaHostAlloc(&s->h_status, sizeof(SvStatus), cudaHostAllocMapped)) != cudaSuccess ||
             (e = cudaHostAlloc(&s->h_tdone, sizeof(unsigned) * cap, cudaHostAllocMapped)) != cudaSuccess ||
@@ -889,6 +907,11 @@ int cos_server_stats(cos_server_t s, cos_server_info* info) {
     info->grid = s->grid;
     info->samples_per_lane = s->vec;
     info->failed = s->failed;
+    cudaError_t e = cudaMemcpyAsync(s->h_stale, &s->d_ctl->stale_claims, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, s->cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
+    if (e != cudaSuccess) return cuda_err(e, "read claim counters");
+    info->stale_claims = (int64_t)*s->h_stale;
     return COS_OK;
 }
 

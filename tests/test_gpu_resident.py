@@ -264,3 +264,38 @@ def test_resident_scheduler_poisson_stream(cg):
     srv.close()
     for g, _ in pool:
         g.close()
+
+
+def test_stale_cursor_claims_stay_exact(cg, monkeypatch):
+    """Test hook (COS_TEST_STALE_CLAIMS=8): about one claim in eight acts on a cursor
+    value a whole queue behind a published task ahead of the cursor, as a CTA would
+    that read the cursor that long ago; the slot then holds that task and its item
+    is taken out of order, waiting for its dependencies.  Every request must still
+    match the oracle (each item run exactly once, after its dependencies), and the
+    out-of-order path must have been taken."""
+    monkeypatch.setenv("COS_TEST_STALE_CLAIMS", "8")
+    works = [tiny(num_samples=8), medium(num_samples=8)]
+    D = max(w.graph.num_times for w in works)
+    srv = cg.ResidentServer(1, D, max_requests=8, queue_tasks=256, idle_ms=2000)
+    hs = [(0, h) for h in _handles(cg, works[0], 4, 3000)] + [(1, h) for h in _handles(cg, works[1], 3, 4096)]
+    pending, done, k = [], 0, 0
+    while done < 24:
+        free = [(wi, h) for wi, h in hs if all(p[1] is not h for p in pending)]
+        if k < 24 and free:
+            wi, h = free[k % len(free)]
+            S = 3000 if wi == 0 else 4096
+            out = torch.empty(S, dtype=torch.float64, device="cuda")
+            rid = srv.submit(h, S, 500 + k, out, 0)
+            if rid is not None:
+                pending.append((rid, h, wi, S, 500 + k, out))
+                k += 1
+                continue
+        rid, h, wi, S, seed, out = pending.pop(0)
+        m = srv.wait(rid, 120000)
+        _check(works[wi], 1, S, seed, 0, out, m)
+        done += 1
+    st = srv.stats()
+    assert st["stale_claims"] > 0 and st["failed"] == 0, st
+    srv.close()
+    for _, h in hs:
+        h.close()
