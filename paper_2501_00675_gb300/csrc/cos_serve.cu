@@ -138,9 +138,11 @@ __device__ __forceinline__ void sv_fail(const ServeArgs& a, int code, long long 
     }
 }
 
-// One attempt to claim an item (thread 0).  Returns 1 with (k, item), 0 when every
-// published item is handed out, 2 when 64 tasks in a row turned out exhausted.
-__device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out, int& item_out) {
+// One attempt to claim an item (thread 0).  Returns 1 with (k, item) -- ooo set when
+// the item came through a stale cursor and belongs to a task ahead of the cursor --,
+// 0 when every published item is handed out, 2 when 64 tasks in a row turned out
+// exhausted.
+__device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out, int& item_out, int& ooo) {
     for (int attempt = 0; attempt < 64; ++attempt) {
         long long k = ld_volatile_s64(&a.ctl->cursor);
         if (k >= pub) {
@@ -161,7 +163,8 @@ __device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out
         if (left > 0x80000000u) {
             k_out = k + age;
             item_out = (int)(left - 0x80000001u);
-            if (age > 0) atomicAdd(&a.ctl->stale_claims, 1ull);
+            ooo = age > 0;
+            if (ooo) atomicAdd(&a.ctl->stale_claims, 1ull);
             return 1;
         }
         // task k is exhausted: move the cursor on
@@ -175,11 +178,11 @@ __device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out
 
 // Claim an item, waiting (bounded by the idle time) for work to be published.
 // Returns 1 with (k, item), 0 to leave (shutdown, idle, or another CTA's error).
-__device__ int sv_claim(const ServeArgs& a, long long& pub, long long& k_out, int& item_out) {
+__device__ int sv_claim(const ServeArgs& a, long long& pub, long long& k_out, int& item_out, int& ooo) {
     unsigned long long t0 = global_timer_ns();
     unsigned sleep_ns = 64;
     for (unsigned long long spin = 0;; ++spin) {
-        const int r = sv_try_claim(a, pub, k_out, item_out);
+        const int r = sv_try_claim(a, pub, k_out, item_out, ooo);
         if (r == 1) return 1;
         if (ld_volatile_s32(&a.ctl->err) != 0) return 0;
         if (r == 2) {   // work is there: not idle
@@ -210,6 +213,44 @@ __device__ __forceinline__ void item_times(const WalkParams& p, unsigned long lo
     }
 }
 
+// Dependencies of task `t` (its chain predecessor, then its joins) complete now?
+__device__ __forceinline__ bool sv_deps_ready(const ServeArgs& a, int dep_slot, unsigned dep_need, long long join_off,
+                                              int join_cnt) {
+    for (int q = -1; q < join_cnt; ++q) {
+        int dslot = dep_slot;
+        unsigned need = dep_need;
+        if (q >= 0) {
+            const unsigned long long j = __ldcg(a.joins + ((join_off + q) & a.jmask));
+            dslot = (int)(j >> 32);
+            need = (unsigned)j;
+        }
+        if (dslot >= 0 && (int)(ld_acquire_gpu_u32(a.done + dslot) - need) < 0) return false;
+    }
+    return true;
+}
+
+// Wait (bounded by the timeout) until the dependencies of the task in s_tk are complete.
+__device__ bool sv_wait_deps(const ServeArgs& a, const SvTask& tk) {
+    const unsigned long long t0 = global_timer_ns();
+    for (unsigned long long spin = 0;; ++spin) {
+        if (sv_deps_ready(a, tk.dep_slot, tk.dep_need, tk.join_off, tk.join_cnt)) return true;
+        if (ld_volatile_s32(&a.ctl->err) != 0) return false;
+        if ((spin & 31) == 31 && ((long long)(global_timer_ns() - t0) > a.timeout_ns || spin > (1ull << 32))) {
+            sv_fail(a, KERR_BARRIER_TIMEOUT, tk.self);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+// A CTA holds at most three items: the current one, one claimed ahead and one set
+// aside.  It only ever waits for the dependencies of the earliest item it holds
+// (they are earlier still, so none is held by this CTA): when the current item is
+// not ready and an item it holds is earlier, that one runs first.  An item claimed
+// out of order (through a stale cursor) that is not ready is set aside -- at most
+// one per CTA -- while the CTA keeps claiming in order; it runs at the first item
+// boundary at which its dependencies are complete, and the CTA does not leave
+// while it holds one (with no other work left it waits for them).
 template <int MODE, int V>
 __global__ void __launch_bounds__(kThreads, (MODE == COS_MODE_FP64 && V > 2) ? 2 : 3) serve_kernel(const ServeArgs a) {
     constexpr int CHV = chunk_samples<V, LAYOUT_WIDE>();
@@ -218,16 +259,18 @@ __global__ void __launch_bounds__(kThreads, (MODE == COS_MODE_FP64 && V > 2) ? 2
     __shared__ SvTask s_tk;
     __shared__ long long s_k[2];
     __shared__ int s_item[2];
+    __shared__ int s_ooo[2];
     __shared__ int s_ok;
-    long long pub = 0;            // thread 0: published tasks last seen
-    long long nk = -1;            // thread 0: claimed-ahead item
-    int nitem = 0;
+    // thread 0 only: published tasks last seen, the item claimed ahead, the item set aside
+    long long pub = 0, nk = -1, dk = -1;
+    int nitem = 0, nooo = 0, ditem = 0;
     if (threadIdx.x == 0) {
         long long k = -1;
-        int item = 0;
-        if (!sv_claim(a, pub, k, item)) k = -1;
+        int item = 0, ooo = 0;
+        if (!sv_claim(a, pub, k, item, ooo)) k = -1;
         s_k[0] = k;
         s_item[0] = item;
+        s_ooo[0] = ooo;
     }
     __syncthreads();
     long long cur_k = -1, cur_seq = -1;
@@ -250,42 +293,60 @@ __global__ void __launch_bounds__(kThreads, (MODE == COS_MODE_FP64 && V > 2) ? 2
                     reinterpret_cast<unsigned long long*>(&s_p)[w] = __ldcg(src + w);
                 cur_seq = s_tk.seq;
             }
-            if (threadIdx.x == 0) {   // dependencies: the chain predecessor, then the joins
-                int ok = 1;
-                const unsigned long long t0 = global_timer_ns();
-                unsigned long long spin = 0;
-                for (int q = -1; ok && q < s_tk.join_cnt; ++q) {
-                    int dslot;
-                    unsigned need;
-                    if (q < 0) {
-                        dslot = s_tk.dep_slot;
-                        need = s_tk.dep_need;
-                    } else {
-                        const unsigned long long j = __ldcg(a.joins + ((s_tk.join_off + q) & a.jmask));
-                        dslot = (int)(j >> 32);
-                        need = (unsigned)j;
+            if (threadIdx.x == 0) {
+                if (sv_deps_ready(a, s_tk.dep_slot, s_tk.dep_need, s_tk.join_off, s_tk.join_cnt)) {
+                    s_ok = 1;
+                } else if (nk >= 0 && nk < k && (dk < 0 || nk < dk)) {
+                    // the item claimed ahead is earlier (this one came out of order or was set
+                    // aside): run it first, keep this one as the item claimed ahead
+                    const long long k2 = nk;
+                    const int item2 = nitem, ooo2 = nooo;
+                    nk = k, nitem = item, nooo = s_ooo[buf];
+                    s_k[buf] = k2, s_item[buf] = item2, s_ooo[buf] = ooo2;
+                    s_ok = 2;
+                } else if (dk >= 0 && dk < k) {
+                    // the item set aside is earlier: run it first, set this one aside instead
+                    const long long k2 = dk;
+                    const int item2 = ditem;
+                    dk = k, ditem = item;
+                    s_k[buf] = k2, s_item[buf] = item2, s_ooo[buf] = 0;
+                    s_ok = 2;
+                } else if (s_ooo[buf] && dk < 0) {
+                    // ahead of the cursor and not ready: set it aside and take other work instead
+                    dk = k;
+                    ditem = item;
+                    long long k2 = -1;
+                    int item2 = 0, ooo2 = 0;
+                    if (nk >= 0) {
+                        k2 = nk, item2 = nitem, ooo2 = nooo;
+                        nk = -1;
+                    } else if (sv_try_claim(a, pub, k2, item2, ooo2) != 1) {
+                        k2 = -1;
                     }
-                    if (dslot < 0) continue;
-                    for (;; ++spin) {
-                        if ((int)(ld_acquire_gpu_u32(a.done + dslot) - need) >= 0) break;
-                        if (ld_volatile_s32(&a.ctl->err) != 0) { ok = 0; break; }
-                        if ((spin & 31) == 31 &&
-                            ((long long)(global_timer_ns() - t0) > a.timeout_ns || spin > (1ull << 32))) {
-                            sv_fail(a, KERR_BARRIER_TIMEOUT, k);
-                            ok = 0;
-                            break;
-                        }
-                        __nanosleep(64);
+                    // nothing claimable now: every published item is held by a running CTA,
+                    // its dependencies among them, so run it after all
+                    if (k2 < 0 && ld_volatile_s32(&a.ctl->err) == 0) {
+                        k2 = dk, item2 = ditem, ooo2 = 0;
+                        dk = -1;
                     }
+                    s_k[buf] = k2, s_item[buf] = item2, s_ooo[buf] = ooo2;
+                    s_ok = 2;
+                } else {
+                    // the earliest item this CTA holds: its dependencies are earlier still,
+                    // so none of them is held here
+                    s_ok = sv_wait_deps(a, s_tk) ? 1 : 0;
                 }
-                s_ok = ok;
             }
             __syncthreads();
-            if (!s_ok) return;   // holds only an item that can no longer matter: the launch is failing
+            if (s_ok == 0) return;   // the launch is failing: every CTA leaves
+            if (s_ok == 2) {         // this buffer now names another item: start over
+                cur_k = -1;
+                continue;
+            }
             cur_k = k;
         }
         if (threadIdx.x == 0 && nk < 0) {   // claim the next item while this one runs
-            if (sv_try_claim(a, pub, nk, nitem) != 1) nk = -1;
+            if (sv_try_claim(a, pub, nk, nitem, nooo) != 1) nk = -1;
         }
         const WalkParams& p = s_p;
         TileCtx tc;
@@ -327,10 +388,33 @@ __global__ void __launch_bounds__(kThreads, (MODE == COS_MODE_FP64 && V > 2) ? 2
                 asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(&c->seq), "l"((unsigned long long)s_tk.seq)
                              : "memory");
             }
-            if (nk < 0 && !sv_claim(a, pub, nk, nitem)) nk = -1;
-            s_k[buf ^ 1] = nk;
-            s_item[buf ^ 1] = nitem;
-            nk = -1;
+            // the next item: the one set aside once it can run, else the one claimed ahead,
+            // else a new claim, else (no other work) the one set aside, waiting for it
+            long long k2 = -1;
+            int item2 = 0, ooo2 = 0;
+            bool ready_aside = false;
+            if (dk >= 0) {
+                const SvTask* d = a.ring + (dk & a.mask);
+                ready_aside = sv_deps_ready(a, __ldcg(&d->dep_slot), __ldcg(&d->dep_need), __ldcg(&d->join_off),
+                                            __ldcg(&d->join_cnt));
+            }
+            if (ready_aside) {
+                k2 = dk, item2 = ditem;
+                dk = -1;
+            } else if (nk >= 0) {
+                k2 = nk, item2 = nitem, ooo2 = nooo;
+                nk = -1;
+            } else if (dk >= 0 ? sv_try_claim(a, pub, k2, item2, ooo2) != 1   // holding one: no idle wait
+                               : !sv_claim(a, pub, k2, item2, ooo2)) {
+                k2 = -1;
+            }
+            if (k2 < 0 && dk >= 0 && ld_volatile_s32(&a.ctl->err) == 0) {
+                k2 = dk, item2 = ditem, ooo2 = 0;
+                dk = -1;
+            }
+            s_k[buf ^ 1] = k2;
+            s_item[buf ^ 1] = item2;
+            s_ooo[buf ^ 1] = ooo2;
         }
         __syncthreads();
         buf ^= 1;
