@@ -1,0 +1,178 @@
+"""A step-by-step model of the resident server's work protocol, run under random
+interleavings on the CPU.  The model follows the kernel's decision rules:
+- a global cursor;
+- per-slot claim words (tag, items left), decremented by every claim attempt;
+- cumulative per-slot completion counters, with each dependent carrying the
+  (slot, value) it waits for;
+- in-order reuse of ring entries once flagged complete;
+- a host feeder bounded by the backlog and the free ring space;
+- stale cursor reads a whole ring behind a published task (the test hook);
+- per CTA an item claimed ahead and one set aside, where a CTA waits only for the
+  earliest item it holds.
+
+Every item must run exactly once, after its dependencies have completed.  Every
+schedule must finish (no state in which nothing can move).  The first set-aside
+rule, which waited on the current item regardless, must deadlock on some of the
+same schedules (the failure the GPU test hook found)."""
+import random
+
+import pytest
+
+
+class Model:
+    def __init__(self, seed, rule="earliest", ctas=5, cap=16, backlog=8, tasks=240, stale=8):
+        self.rng = random.Random(seed)
+        self.rule, self.cap, self.backlog, self.stale = rule, cap, backlog, stale
+        # the task stream in publication order: items (some zero) and earlier dependencies
+        self.items, self.deps = [], []
+        for t in range(tasks):
+            self.items.append(0 if self.rng.random() < 0.08 else self.rng.randint(1, 4))
+            near = list(range(max(0, t - 10), t))
+            self.deps.append(sorted(self.rng.sample(near, min(len(near), self.rng.randint(0, 2)))))
+        self.T = tasks
+        self.cursor = self.next = self.tail = 0
+        self.claim = [[-cap, 0] for _ in range(cap)]       # (tag, items left)
+        self.done = [0] * cap                               # cumulative per slot
+        self.slot_total = [0] * cap
+        self.flag = [-cap - 1] * cap                         # tag of the last task completed in the slot
+        self.need = {}                                      # task -> completion value of its slot
+        self.run_count = {}
+        self.completed_items = [0] * tasks
+        self.ctas = [dict(cur=None, ahead=None, aside=None, phase="next") for _ in range(ctas)]
+
+    # -- host
+    def publish(self):
+        moved = False
+        while self.next < self.T and self.next - self.cursor < self.backlog and self.next - self.tail < self.cap:
+            t, s = self.next, self.next % self.cap
+            assert self.flag[s] == t - self.cap or t < self.cap   # the entry's previous task is complete
+            self.claim[s] = [t, self.items[t]]
+            self.slot_total[s] += self.items[t]
+            self.need[t] = self.slot_total[s]
+            if self.items[t] == 0:
+                self.flag[s] = t
+            self.next += 1
+            moved = True
+        return moved
+
+    def reclaim(self):
+        moved = False
+        while self.tail < self.next and self.flag[self.tail % self.cap] == self.tail:
+            self.tail += 1
+            moved = True
+        return moved
+
+    # -- device
+    def ready(self, t):
+        return all(self.done[d % self.cap] >= self.need[d] for d in self.deps[t])
+
+    def try_claim(self):
+        for _ in range(64):
+            k = self.cursor
+            if k >= self.next:
+                return None
+            if self.stale and self.next - k > 1 and self.rng.randrange(self.stale) == 0:
+                k = self.rng.randrange(k + 1, self.next) - self.cap     # a cursor read a whole ring behind
+            s = k % self.cap
+            tag, left = self.claim[s]
+            self.claim[s][1] -= 1
+            age = tag - k
+            if age < 0:
+                return None
+            if left > 0:
+                return (k + age, left - 1, age > 0)
+            if self.cursor == k:
+                self.cursor += 1
+        return None
+
+    def step_cta(self, c):
+        """One step of CTA c; returns True if its state changed."""
+        if c["phase"] == "next":
+            if c["aside"] is not None and self.ready(c["aside"][0]):
+                c["cur"], c["aside"] = (c["aside"][0], c["aside"][1], False), None
+            elif c["ahead"] is not None:
+                c["cur"], c["ahead"] = c["ahead"], None
+            else:
+                c["cur"] = self.try_claim()
+                if c["cur"] is None and c["aside"] is not None:
+                    c["cur"], c["aside"] = (c["aside"][0], c["aside"][1], False), None
+            if c["cur"] is None:
+                return False
+            c["phase"] = "decide"
+            return True
+        if c["phase"] == "decide":
+            k, item, ooo = c["cur"]
+            if self.ready(k):
+                c["phase"] = "run"
+            elif self.rule == "earliest" and c["ahead"] is not None and c["ahead"][0] < k and (
+                    c["aside"] is None or c["ahead"][0] < c["aside"][0]):
+                c["cur"], c["ahead"] = c["ahead"], c["cur"]
+            elif self.rule == "earliest" and c["aside"] is not None and c["aside"][0] < k:
+                c["cur"], c["aside"] = (c["aside"][0], c["aside"][1], False), (k, item)
+            elif ooo and c["aside"] is None:
+                c["aside"] = (k, item)
+                if c["ahead"] is not None:
+                    c["cur"], c["ahead"] = c["ahead"], None
+                else:
+                    c["cur"] = self.try_claim()
+                if c["cur"] is None:
+                    c["cur"], c["aside"] = (k, item, False), None
+            else:
+                c["phase"] = "wait"
+            return True
+        if c["phase"] == "wait":
+            if not self.ready(c["cur"][0]):
+                return False
+            c["phase"] = "run"
+            return True
+        # run: claim ahead, then the item itself
+        k, item, _ = c["cur"]
+        if c["ahead"] is None:
+            c["ahead"] = self.try_claim()
+        for d in self.deps[k]:
+            assert self.completed_items[d] == self.items[d], "ran before a dependency completed"
+        assert 0 <= item < self.items[k]
+        assert (k, item) not in self.run_count, "item ran twice"
+        self.run_count[(k, item)] = 1
+        self.completed_items[k] += 1
+        s = k % self.cap
+        self.done[s] += 1
+        if self.done[s] == self.need[k]:
+            self.flag[s] = k
+        c["cur"], c["phase"] = None, "next"
+        return True
+
+    def run(self, max_steps=200000):
+        """True when every task completed; False on a state in which nothing can move."""
+        for _ in range(max_steps):
+            if sum(self.completed_items) == sum(self.items) and self.next == self.T:
+                return True
+            moved = self.reclaim() | self.publish()
+            order = list(range(len(self.ctas)))
+            self.rng.shuffle(order)
+            for i in order[: self.rng.randint(1, len(order))]:
+                moved |= self.step_cta(self.ctas[i])
+            if not moved and not any(self.step_cta(c) for c in self.ctas):
+                return False
+        raise AssertionError("step limit")
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_protocol_finishes_exactly_once(seed):
+    m = Model(seed)
+    assert m.run()
+    assert len(m.run_count) == sum(m.items)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_protocol_without_stale_reads(seed):
+    m = Model(1000 + seed, stale=0)
+    assert m.run()
+    assert len(m.run_count) == sum(m.items)
+
+
+def test_first_set_aside_rule_deadlocks():
+    """Sensitivity: waiting on the current item regardless of what the CTA holds
+    deadlocks on some schedules (a CTA waits for a task whose item it set aside)."""
+    stuck = sum(not Model(seed, rule="first").run() for seed in range(40))
+    assert stuck > 0
