@@ -793,9 +793,12 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
     if (t.rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
     if (t.window_chunks < 0 || t.prefetch < 0 || t.prefetch > 3)
         return set_error(COS_ERR_INVALID, "window_chunks must be >= 0 and prefetch 0..3");
+    int device = -1;
+    const cudaError_t de = cudaGetDevice(&device);
+    if (de != cudaSuccess) return set_error(COS_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(de));
     Srv* s = new (std::nothrow) Srv();
     if (!s) return set_error(COS_ERR_OOM, "host allocation failed");
-    cudaGetDevice(&s->device);
+    s->device = device;
     s->mode = mode;
     s->vec = t.samples_per_lane > 0 ? t.samples_per_lane : (mode == COS_MODE_FP32_MIXED ? 4 : 2);
     s->max_D = max_times;

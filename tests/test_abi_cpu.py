@@ -125,3 +125,37 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         binding.load_library()
+
+
+def test_server_arguments_checked_before_any_cuda_call(lib):
+    """cos_server_*: argument errors come back as COS_ERR_INVALID without touching the
+    device; NULL handles are refused (destroy accepts NULL)."""
+    h = ctypes.c_void_p()
+    create = lib.cos_server_create
+    assert create(3, 4, None, 0, 0, 0, ctypes.byref(h)) == binding.COS_ERR_INVALID          # mode
+    assert create(0, 0, None, 0, 0, 0, ctypes.byref(h)) == binding.COS_ERR_INVALID          # max_times
+    assert create(0, 4, None, -1, 0, 0, ctypes.byref(h)) == binding.COS_ERR_INVALID         # max_requests
+    assert create(0, 4, None, 0, -5, 0, ctypes.byref(h)) == binding.COS_ERR_INVALID         # queue_tasks
+    assert create(0, 4, None, 0, 0, -1, ctypes.byref(h)) == binding.COS_ERR_INVALID         # idle_ms
+    assert create(0, 4, None, 0, 0, 0, None) == binding.COS_ERR_INVALID
+    for field, value in (("samples_per_lane", 3), ("layout", 2), ("rows_per_warp", 32), ("prefetch", 4),
+                         ("window_chunks", -1)):
+        t = binding.CosTuning()
+        setattr(t, field, value)
+        assert create(0, 4, ctypes.byref(t), 0, 0, 0, ctypes.byref(h)) == binding.COS_ERR_INVALID, field
+    rid = ctypes.c_int64()
+    m = ctypes.c_double()
+    assert lib.cos_server_submit(None, None, 1, 1, 0, None, ctypes.byref(rid)) == binding.COS_ERR_INVALID
+    assert lib.cos_server_poll(None, 1, ctypes.byref(m)) == binding.COS_ERR_INVALID
+    assert lib.cos_server_wait(None, 1, 0, ctypes.byref(m)) == binding.COS_ERR_INVALID
+    assert lib.cos_server_stats(None, None) == binding.COS_ERR_INVALID
+    assert lib.cos_server_destroy(None) == binding.COS_OK
+
+
+def test_server_without_a_device_reports_cuda_error(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = lib.cos_server_create(0, 4, None, 0, 0, 0, ctypes.byref(h))
+    assert rc == binding.COS_ERR_CUDA and "device" in lib.cos_last_error().decode()
