@@ -9,10 +9,10 @@
 // all active requests into a task ring in device memory round-robin, one task per
 // request per round (consecutive tasks are then independent, as in the batched
 // plan), keeping a bounded backlog ahead of the kernel's cursor so that a new
-// request joins the rotation within that backlog.  Ring entries, claim words and
-// finally the published-task counter are written by host-to-device copies on one
-// copy stream, so the counter is never seen before what it publishes; no kernel has
-// to run to admit a request.  The host feeds from every submit, poll, wait and
+// request joins the rotation within that backlog.  Descriptors, join entries, claim
+// words and finally the published-task counter are written by host-to-device copies
+// on one copy stream, so neither a claim word nor the counter is seen before what
+// it announces; no kernel has to run to admit a request.  The host feeds from every submit, poll, wait and
 // stats call.
 //
 // Claiming: a global cursor names the task whose items are handed out; a CTA reads
@@ -22,10 +22,11 @@
 // into it.  The returned value names the item (or, if the slot already holds a
 // later task, an item of that task, which is as good a claim); a task whose items
 // are all handed out moves the cursor on.  No compare-and-swap retry is on the
-// path of an item.  Items are therefore handed out in task order, and a
-// CTA holds a claimed item only while it runs, so the lowest unfinished item can
-// always run (its dependencies are earlier tasks): no co-residency is required and
-// an idle CTA, which holds nothing, may leave at any time.  Completion counters
+// path of an item.  Items are handed out in task order except through a stale
+// cursor; a CTA waits only for the dependencies of the earliest item it holds and
+// sets aside an out-of-order item that is not ready (see serve_kernel), so the
+// lowest unfinished item can run: no co-residency is required and an idle CTA,
+// which holds nothing, may leave at any time.  Completion counters
 // per ring slot are cumulative over the tasks the slot has held (a task is
 // complete once its slot's counter reaches the value the host assigned, which
 // every dependent carries in its own descriptor); the CTA that completes a task
