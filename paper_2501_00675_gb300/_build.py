@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcosgpu.so")
 SOURCES = ["cos_graph.cu", "cos_walk.cu", "cos_batch.cu", "cos_noalloc.cu", "cos_mc.cu", "cos_serve.cu"]
-HEADERS = ["cos_internal.cuh", "cos_items.cuh", "cos_tasks.cuh"]
+HEADERS = ["cos_internal.cuh", "cos_items.cuh", "cos_tasks.cuh", "cos_feed.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

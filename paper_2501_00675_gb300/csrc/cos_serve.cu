@@ -49,29 +49,12 @@
 #include <vector>
 
 #include "cos_items.cuh"
+#include "cos_feed.h"
 #include "cos_tasks.cuh"
 
 namespace cosgpu {
 namespace {
 
-struct SvTask {
-    int64_t self;       // absolute task index (publication order); its ring slot is self & mask
-    int64_t seq;        // request number (key of the CTAs' parameter cache)
-    int64_t tix;        // tile index (TK_TIMES: number of the request's first sample)
-    int64_t join_off;   // absolute index of the first join entry
-    uint64_t seed;      // TK_TIMES: generator key
-    int32_t req;        // request slot: walker parameters and completion record
-    int32_t kind;
-    int32_t level;
-    int32_t items;
-    int32_t c0;
-    int32_t join_cnt;
-    int32_t dep_slot;   // ring slot of the task that must be complete first, or -1 ...
-    uint32_t dep_need;  // ... and the value that slot's counter has reached then
-    uint32_t need;      // value of done[self & mask] once this task is complete
-    int32_t pad;
-};
-static_assert(sizeof(SvTask) % 8 == 0, "descriptor is copied as 8-byte words");
 static_assert(sizeof(WalkParams) % 8 == 0, "parameters are copied as 8-byte words");
 
 struct SvPub {          // device memory, written only by host-to-device copies
@@ -465,7 +448,6 @@ struct cos_server {
     int32_t max_D = 0;
     cos_tuning force{};
     int32_t max_req = 0;
-    int64_t cap = 0, jcap = 0;
     int64_t backlog = 0;             // tasks published ahead of the kernel's cursor at most
     int grid = 0, smem = 0;
     const void* kernel = nullptr;
@@ -480,11 +462,9 @@ struct cos_server {
     unsigned* d_done = nullptr;
     SvCtl* d_ctl = nullptr;
     SvPub* d_pub = nullptr;
-    // pinned host mirrors (sources of the publishing copies)
-    SvTask* h_ring = nullptr;
-    unsigned long long* h_joins = nullptr;
+    // pinned host mirrors (sources of the publishing copies); the ring's in fr
+    FeedRing fr;
     WalkParams* h_params = nullptr;
-    unsigned long long* h_claim = nullptr;
     long long* h_pubval = nullptr;   // [kPubRing]: sources of the counter copies
     cudaEvent_t pub_ev[kPubRing / kPubBlock] = {};
     int64_t n_pub = 0;
@@ -494,31 +474,20 @@ struct cos_server {
     SvComp* d_comp = nullptr;
     SvStatus* h_status = nullptr;
     SvStatus* d_status = nullptr;
-    unsigned* h_tdone = nullptr;     // [cap]: tag of the last task completed in each ring slot
-    unsigned* d_tdone = nullptr;
+    unsigned* d_tdone = nullptr;     // device alias of fr.tdone (host-mapped)
     unsigned long long* h_cursor = nullptr;
     unsigned long long* d_cursor = nullptr;
     cudaStream_t ks = nullptr, cs = nullptr;
     cudaEvent_t kdone = nullptr, cev = nullptr;
     bool running = false;
     int failed = 0;                  // cos_status once the kernel has reported an error
-    int64_t next_task = 0, tail_task = 0, next_join = 0, tail_join = 0, next_seq = 1;
-    std::vector<uint32_t> slot_total;   // per ring slot: items of every task it has held
-    std::vector<int64_t> join_end;      // per ring slot: next_join after its task's joins
-    struct Req {
-        int64_t seq = 0;
+    int64_t next_seq = 1;
+    struct Req : FeedReq {
         cos_graph_t g = nullptr;
         bool active = false, done = false;
         int overflow = 0;
         int err = 0;
         double mean = 0.0;
-        uint64_t seed = 0;
-        int64_t first_sample = 0;
-        std::vector<Task> tasks;                 // the request's chain (local dep indices)
-        std::vector<std::vector<int32_t>> joins;
-        size_t next = 0;                         // tasks published so far
-        std::vector<int32_t> slot_of;            // ring slot of each published task
-        std::vector<uint32_t> need_of;           // its completion value
     };
     std::vector<Req> reqs;
     std::deque<int32_t> feeding;     // request slots with tasks left to publish, oldest first
@@ -541,15 +510,15 @@ void free_server(Srv* s) {
     cudaFree(s->d_done);
     cudaFree(s->d_ctl);
     cudaFree(s->d_pub);
-    cudaFreeHost(s->h_ring);
-    cudaFreeHost(s->h_joins);
+    cudaFreeHost(s->fr.ring);
+    cudaFreeHost(s->fr.joins);
     cudaFreeHost(s->h_params);
-    cudaFreeHost(s->h_claim);
+    cudaFreeHost(s->fr.claim);
     cudaFreeHost(s->h_pubval);
     cudaFreeHost(s->h_one);
     cudaFreeHost(s->h_comp);
     cudaFreeHost(s->h_status);
-    cudaFreeHost(s->h_tdone);
+    cudaFreeHost(s->fr.tdone);
     cudaFreeHost(s->h_cursor);
     cudaFreeHost(s->h_stale);
     for (cudaEvent_t& e : s->pub_ev)
@@ -598,12 +567,7 @@ void collect(Srv* s) {
             q.done = true;
         }
     }
-    while (s->tail_task < s->next_task) {
-        const int64_t at = s->tail_task & (s->cap - 1);
-        if (*(volatile unsigned*)&s->h_tdone[at] != (unsigned)s->tail_task) break;
-        s->tail_join = s->join_end[(size_t)at];
-        s->tail_task++;
-    }
+    feed_reclaim(s->fr);
     __atomic_thread_fence(__ATOMIC_ACQUIRE);
 }
 
@@ -619,40 +583,6 @@ cudaError_t copy_ring(T* dst, const T* src, int64_t cap, int64_t first, int64_t 
         n -= m;
     }
     return e;
-}
-
-// Write one task of request slot r into the ring mirrors at position next_task.
-void stage_task(Srv* s, int32_t r) {
-    Srv::Req& q = s->reqs[(size_t)r];
-    const size_t li = q.next++;
-    const Task& t = q.tasks[li];
-    const int64_t self = s->next_task++;
-    const int64_t at = self & (s->cap - 1);
-    SvTask& e = s->h_ring[at];
-    memset(&e, 0, sizeof(e));
-    e.self = self;
-    e.seq = q.seq;
-    e.tix = t.kind == TK_TIMES ? q.first_sample : t.tix;
-    e.seed = q.seed;
-    e.req = r;
-    e.kind = t.kind;
-    e.level = t.level;
-    e.items = t.items;
-    e.c0 = t.c0;
-    e.dep_slot = t.dep >= 0 ? q.slot_of[(size_t)t.dep] : -1;
-    e.dep_need = t.dep >= 0 ? q.need_of[(size_t)t.dep] : 0u;
-    e.join_off = s->next_join;
-    e.join_cnt = (int32_t)q.joins[li].size();
-    for (int32_t d : q.joins[li])
-        s->h_joins[s->next_join++ & (s->jcap - 1)] =
-            ((unsigned long long)(uint32_t)q.slot_of[(size_t)d] << 32) | q.need_of[(size_t)d];
-    s->slot_total[(size_t)at] += (uint32_t)t.items;
-    e.need = s->slot_total[(size_t)at];
-    s->join_end[(size_t)at] = s->next_join;
-    s->h_claim[at] = ((unsigned long long)(uint32_t)self << 32) | (0x80000000ull + (uint32_t)t.items);
-    q.slot_of.push_back((int32_t)at);
-    q.need_of.push_back(e.need);
-    if (t.items == 0) *(volatile unsigned*)&s->h_tdone[at] = (unsigned)self;   // complete as soon as published
 }
 
 // Publish the counter value v: its source stays untouched until the copy has run.
@@ -673,37 +603,19 @@ int publish_counter(Srv* s, long long v) {
 // the backlog ahead of the kernel's cursor and the free ring space allow.
 int feed(Srv* s) {
     if (s->feeding.empty()) return COS_OK;
+    FeedRing& f = s->fr;
     const int64_t cursor = (int64_t)*(volatile unsigned long long*)s->h_cursor;
-    int64_t room = std::min(s->backlog - (s->next_task - cursor), s->cap - (s->next_task - s->tail_task));
+    const int64_t room = std::min(s->backlog - (f.next_task - cursor), f.cap - (f.next_task - f.tail_task));
     if (room <= 0) return COS_OK;
-    const int64_t t0 = s->next_task, j0 = s->next_join;
-    bool progress = true;
-    while (room > 0 && progress) {
-        progress = false;
-        for (int32_t r : s->feeding) {
-            if (room <= 0) break;
-            Srv::Req& q = s->reqs[(size_t)r];
-            if (q.next >= q.tasks.size()) continue;
-            if (s->next_join + (int64_t)q.joins[q.next].size() - s->tail_join > s->jcap) {
-                room = 0;
-                break;
-            }
-            stage_task(s, r);
-            --room;
-            progress = true;
-        }
-    }
-    for (auto it = s->feeding.begin(); it != s->feeding.end();) {
-        const Srv::Req& q = s->reqs[(size_t)*it];
-        it = q.next >= q.tasks.size() ? s->feeding.erase(it) : it + 1;
-    }
-    if (s->next_task == t0) return COS_OK;
+    const int64_t t0 = f.next_task, j0 = f.next_join;
+    if (feed_round_robin(f, s->feeding, room, [s](int32_t r) -> FeedReq& { return s->reqs[(size_t)r]; }) == 0)
+        return COS_OK;
     // descriptors and joins, then the claim words (a CTA that finds a new tag may run the
     // task at once), then the counter (one stream, in order)
-    cudaError_t e = copy_ring(s->d_ring, s->h_ring, s->cap, t0, s->next_task - t0, s->cs);
-    if (e == cudaSuccess) e = copy_ring(s->d_joins, s->h_joins, s->jcap, j0, s->next_join - j0, s->cs);
-    if (e == cudaSuccess) e = copy_ring(s->d_claim, s->h_claim, s->cap, t0, s->next_task - t0, s->cs);
-    int rc = e == cudaSuccess ? publish_counter(s, s->next_task) : cuda_err(e, "publish tasks");
+    cudaError_t e = copy_ring(s->d_ring, f.ring, f.cap, t0, f.next_task - t0, s->cs);
+    if (e == cudaSuccess) e = copy_ring(s->d_joins, f.joins, f.jcap, j0, f.next_join - j0, s->cs);
+    if (e == cudaSuccess) e = copy_ring(s->d_claim, f.claim, f.cap, t0, f.next_task - t0, s->cs);
+    int rc = e == cudaSuccess ? publish_counter(s, f.next_task) : cuda_err(e, "publish tasks");
     if (rc != COS_OK) s->failed = COS_ERR_CUDA;   // the mirrors have moved on: the server cannot continue
     return rc;
 }
@@ -721,8 +633,8 @@ int launch(Srv* s) {
     a.status = s->d_status;
     a.tdone = s->d_tdone;
     a.cursor_out = s->d_cursor;
-    a.mask = s->cap - 1;
-    a.jmask = s->jcap - 1;
+    a.mask = s->fr.cap - 1;
+    a.jmask = s->fr.jcap - 1;
     a.timeout_ns = s->timeout_ns;
     a.idle_ns = s->idle_ns;
     a.test_stale = s->test_stale;
@@ -808,9 +720,9 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
     s->force.layout = 1;
     if (s->force.rows_per_warp <= 0) s->force.rows_per_warp = 31;
     s->max_req = max_requests > 0 ? max_requests : 256;
-    s->cap = pow2_at_least(std::max<int64_t>(queue_tasks > 0 ? queue_tasks : 65536, 64));
-    s->jcap = s->cap;
-    s->backlog = std::min<int64_t>(s->cap / 2, 16384);
+    s->fr.cap = pow2_at_least(std::max<int64_t>(queue_tasks > 0 ? queue_tasks : 65536, 64));
+    s->fr.jcap = s->fr.cap;
+    s->backlog = std::min<int64_t>(s->fr.cap / 2, 16384);
     s->timeout_ns = (long long)(t.timeout_ms > 0 ? t.timeout_ms : 10000) * 1000000LL;
     s->idle_ns = (long long)(idle_ms > 0 ? idle_ms : 50) * 1000000LL;
     if (const char* env = getenv("COS_TEST_STALE_CLAIMS")) s->test_stale = std::max(0, atoi(env));
@@ -834,7 +746,7 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
         s->force.blocks_per_sm = bps;
         s->grid = sms * bps;
         const size_t nr = (size_t)s->max_req;
-        const size_t cap = (size_t)s->cap, jcap = (size_t)s->jcap;
+        const size_t cap = (size_t)s->fr.cap, jcap = (size_t)s->fr.jcap;
         if ((e = cudaMalloc(&s->d_ring, sizeof(SvTask) * cap)) != cudaSuccess ||
             (e = cudaMalloc(&s->d_joins, sizeof(unsigned long long) * jcap)) != cudaSuccess ||
             (e = cudaMalloc(&s->d_params, sizeof(WalkParams) * nr)) != cudaSuccess ||
@@ -842,31 +754,31 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
             (e = cudaMalloc(&s->d_done, sizeof(unsigned) * cap)) != cudaSuccess ||
             (e = cudaMalloc(&s->d_ctl, sizeof(SvCtl))) != cudaSuccess ||
             (e = cudaMalloc(&s->d_pub, sizeof(SvPub))) != cudaSuccess ||
-            (e = cudaMallocHost(&s->h_ring, sizeof(SvTask) * cap)) != cudaSuccess ||
-            (e = cudaMallocHost(&s->h_joins, sizeof(unsigned long long) * jcap)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->fr.ring, sizeof(SvTask) * cap)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->fr.joins, sizeof(unsigned long long) * jcap)) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_params, sizeof(WalkParams) * nr)) != cudaSuccess ||
-            (e = cudaMallocHost(&s->h_claim, sizeof(unsigned long long) * cap)) != cudaSuccess ||
+            (e = cudaMallocHost(&s->fr.claim, sizeof(unsigned long long) * cap)) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_pubval, sizeof(long long) * kPubRing)) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_one, sizeof(int))) != cudaSuccess ||
             (e = cudaMallocHost(&s->h_stale, sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaHostAlloc(&s->h_comp, sizeof(SvComp) * nr, cudaHostAllocMapped)) != cudaSuccess ||
             (e = cudaHostAlloc(&s->h_status, sizeof(SvStatus), cudaHostAllocMapped)) != cudaSuccess ||
-            (e = cudaHostAlloc(&s->h_tdone, sizeof(unsigned) * cap, cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostAlloc(&s->fr.tdone, sizeof(unsigned) * cap, cudaHostAllocMapped)) != cudaSuccess ||
             (e = cudaHostAlloc(&s->h_cursor, sizeof(unsigned long long), cudaHostAllocMapped)) != cudaSuccess ||
             (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_comp), s->h_comp, 0)) != cudaSuccess ||
             (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_status), s->h_status, 0)) != cudaSuccess ||
-            (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_tdone), s->h_tdone, 0)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_tdone), s->fr.tdone, 0)) != cudaSuccess ||
             (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_cursor), s->h_cursor, 0)) != cudaSuccess)
             rc = set_error(COS_ERR_OOM, "server buffers: %s", cudaGetErrorString(e));
     }
     if (rc == COS_OK) {
         memset(s->h_comp, 0, sizeof(SvComp) * (size_t)s->max_req);
         memset(s->h_status, 0, sizeof(SvStatus));
-        for (int64_t i = 0; i < s->cap; ++i) s->h_tdone[i] = (unsigned)(i - s->cap);   // no task's tag yet
+        s->fr.reset();
         *s->h_cursor = 0;
         *s->h_one = 1;
-        if ((e = cudaMemset(s->d_claim, 0, sizeof(unsigned long long) * (size_t)s->cap)) != cudaSuccess ||
-            (e = cudaMemset(s->d_done, 0, sizeof(unsigned) * (size_t)s->cap)) != cudaSuccess ||
+        if ((e = cudaMemset(s->d_claim, 0, sizeof(unsigned long long) * (size_t)s->fr.cap)) != cudaSuccess ||
+            (e = cudaMemset(s->d_done, 0, sizeof(unsigned) * (size_t)s->fr.cap)) != cudaSuccess ||
             (e = cudaMemset(s->d_ctl, 0, sizeof(SvCtl))) != cudaSuccess ||
             (e = cudaMemset(s->d_pub, 0, sizeof(SvPub))) != cudaSuccess ||
             (e = cudaStreamCreateWithFlags(&s->ks, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -884,8 +796,6 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
         delete s;
         return rc;
     }
-    s->slot_total.assign((size_t)s->cap, 0u);
-    s->join_end.assign((size_t)s->cap, 0);
     s->reqs.assign((size_t)s->max_req, Srv::Req{});
     *out = s;
     return COS_OK;
@@ -928,6 +838,13 @@ int cos_server_submit(cos_server_t s, cos_graph_t g, int64_t num_samples, uint64
     graph_task_chain(p, gv.widths_host, s->mode, 32 * s->vec,
                      s->force.window_chunks > 0 ? s->force.window_chunks : tn.window_chunks, slot,
                      s->mode != COS_MODE_COUNT_I64, getenv("COS_TEST_STALL_TASK") != nullptr, q.tasks, q.joins);
+    if ((int64_t)feed_max_joins(q) > s->fr.jcap) {
+        const size_t need = feed_max_joins(q);
+        q = Srv::Req{};
+        restore_samples(g, undo);
+        return set_error(COS_ERR_INVALID, "request joins %zu windows in one task; the queue holds %lld (raise queue_tasks)",
+                         need, (long long)s->fr.jcap);
+    }
     s->h_params[slot] = p;
     // the parameters go ahead of every counter copy that publishes one of the request's tasks
     cudaError_t e = cudaMemcpyAsync(s->d_params + slot, s->h_params + slot, sizeof(WalkParams), cudaMemcpyHostToDevice, s->cs);
@@ -989,8 +906,8 @@ int cos_server_stats(cos_server_t s, cos_server_info* info) {
     info->launches = s->launches;
     info->completed = s->completed;
     for (const Srv::Req& q : s->reqs) info->in_flight += (q.active && !q.done) ? 1 : 0;
-    info->queued_tasks = s->next_task - s->tail_task;
-    info->published_tasks = s->next_task;
+    info->queued_tasks = s->fr.next_task - s->fr.tail_task;
+    info->published_tasks = s->fr.next_task;
     info->running = s->running ? 1 : 0;
     info->grid = s->grid;
     info->samples_per_lane = s->vec;
