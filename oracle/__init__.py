@@ -129,61 +129,125 @@ def tabulated_propagator(table: np.ndarray, tau_max: float, tau) -> np.ndarray:
     linear interpolation of its two neighbours; outside [-tau_max, tau_max] the end
     value.  Two halves keep the jump at tau = 0 (G(0+) - G(0-) = -1 for fermions).
 
-    The arithmetic is fixed, each step rounded once in double: inv_h = T / tau_max,
-    u = tau * inv_h (plus T below zero), m = floor(u) (0 with f = 0 below the grid,
-    T - 1 with f = 1 at or past its end), f = u - m, G = a_m + f * (a_{m+1} - a_m);
-    near zero-crossings of G the position error of any other rounding order would
-    show up relative to G."""
+    The definition is evaluated in extended precision (numpy longdouble: 64-bit
+    significand on x86-64, 113-bit on AArch64) and rounded once to double: grid
+    coordinate x = tau*T/tau_max (plus T below zero), m = floor(x), f = x - m,
+    G = a_m + f*(a_{m+1} - a_m)."""
     table = np.asarray(table, dtype=np.float64)
     if table.ndim != 2 or table.shape[0] != 2 or table.shape[1] < 2:
         raise ValueError("table must be [2, T+1] with T >= 1")
     T = table.shape[1] - 1
     tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
+    ld = np.longdouble
     pos = tau >= 0.0
-    inv_h = float(T) / float(tau_max)
-    u = tau * inv_h
-    u = np.where(pos, u, u + float(T))
-    below = u < 0.0
-    m = np.floor(np.where(below, 0.0, u)).astype(np.int64)
-    f = u - m
-    past = (~below) & (m >= T)
-    m = np.where(below, 0, np.where(past, T - 1, m))
-    f = np.where(below, 0.0, np.where(past, 1.0, f))
+    x = tau.astype(ld) * ld(T) / ld(tau_max)
+    x = np.where(pos, x, x + ld(T))
+    m, f = _grid_interval(x, T)
     half = np.where(pos[:, None], table[0][None, :], table[1][None, :])
     rows = np.arange(tau.size)
-    a = half[rows, m]
-    slope = half[rows, m + 1] - a
-    return a + f * slope
+    a = half[rows, m].astype(ld)
+    b = half[rows, m + 1].astype(ld)
+    return (a + f * (b - a)).astype(np.float64)
 
 
-def tabulated_edge_weights(graph, tables: np.ndarray, tau_max: float, t_sample: np.ndarray) -> np.ndarray:
-    """Per-edge factors +-G_{k_e}(t_{i_e} - t_{j_e}) from tables[K, 2, T+1] for one sample."""
+def _grid_interval(x: np.ndarray, T: int):
+    """Interval index m in [0, T-1] and position f in [0, 1] of grid coordinates x
+    (before the grid: m = 0, f = 0; at or past its end: m = T-1, f = 1)."""
+    below = x < 0
+    past = x >= T
+    m = np.floor(np.where(below | past, 0, x)).astype(np.int64)
+    f = x - m
+    m = np.where(past, T - 1, m)
+    f = np.where(below, 0, np.where(past, 1, f))
+    return np.minimum(m, T - 1), f
+
+
+UNIT_ROUNDOFF = 2.0 ** -53
+
+
+def tabulated_rounding_scale(table: np.ndarray, tau_max: float, tau) -> np.ndarray:
+    """Bound on the error of any double-precision evaluation of ``tabulated_propagator``
+    that forms the grid coordinate x = tau*T/tau_max (+T) with a few roundings: x is
+    then off by at most 4u(|x| + T) grid units (u = 2^-53), which moves G by at most
+    that times the largest |a_{m+1} - a_m| of the half (the interpolant is continuous,
+    so landing in a neighbouring interval changes nothing beyond the slope), and the
+    multiply-add of the interpolation rounds at most 4u(|a_m| + |a_{m+1}|).  Near a
+    zero of G this absolute error can exceed any bound relative to |G| itself."""
+    table = np.asarray(table, dtype=np.float64)
+    T = table.shape[1] - 1
+    tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
+    pos = tau >= 0.0
+    x = tau * (T / tau_max)
+    x = np.where(pos, x, x + T)
+    m, _ = _grid_interval(x, T)
+    smax = np.max(np.abs(np.diff(table, axis=1)), axis=1)          # per half
+    half = np.where(pos[:, None], table[0][None, :], table[1][None, :])
+    rows = np.arange(tau.size)
+    am, am1 = np.abs(half[rows, m]), np.abs(half[rows, m + 1])
+    return UNIT_ROUNDOFF * (4.0 * (np.abs(x) + T) * np.where(pos, smax[0], smax[1]) + 4.0 * (am + am1))
+
+
+def tabulated_edge_weights(graph, tables: np.ndarray, tau_max: float, t_sample: np.ndarray,
+                           scale: bool = False):
+    """Per-edge factors +-G_{k_e}(t_{i_e} - t_{j_e}) from tables[K, 2, T+1] for one sample;
+    with scale=True also the per-edge rounding scale (``tabulated_rounding_scale``)."""
     e = graph.edges
     tau = t_sample[e[:, 3]] - t_sample[e[:, 4]]
     kind = e[:, 2] & KIND_MASK
     out = np.empty(e.shape[0])
+    sc = np.empty(e.shape[0]) if scale else None
     for k in np.unique(kind):
         m = kind == k
         out[m] = tabulated_propagator(tables[k], tau_max, tau[m])
+        if scale:
+            sc[m] = tabulated_rounding_scale(tables[k], tau_max, tau[m])
     out[(e[:, 2] & SIGN_BIT) != 0] *= -1.0
-    return out
+    return (out, sc) if scale else out
 
 
-def evaluate_tabulated(graph, tables: np.ndarray, tau_max: float, t: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+def evaluate_tabulated(graph, tables: np.ndarray, tau_max: float, t: np.ndarray, with_bound: bool = False):
     """Per-sample sink values R[s] and A[s] = sum of |path| values with tabulated
     propagators: the level-wise DP (``pathsum``) once per sample with that sample's
-    edge factors."""
+    edge factors.  With with_bound=True also B[s], the first-order effect on R of the
+    per-edge rounding scales eps_e of a double evaluation of the tables:
+    B = sum_e eps_e * F(src_e) * Bk(dst_e), where F(v) is the sum over root-to-v
+    paths and Bk(v) the sum over v-to-sink paths of the products of |factor|."""
     tables = np.asarray(tables, dtype=np.float64)
     if tables.ndim != 3 or tables.shape[0] < graph.num_kinds or tables.shape[1] != 2:
         raise ValueError("tables must be [K, 2, T+1]")
     S = t.shape[0]
     R = np.empty(S)
     A = np.empty(S)
+    B = np.empty(S) if with_bound else None
     for s in range(S):
-        w = tabulated_edge_weights(graph, tables, tau_max, t[s])
+        if with_bound:
+            w, sc = tabulated_edge_weights(graph, tables, tau_max, t[s], scale=True)
+        else:
+            w = tabulated_edge_weights(graph, tables, tau_max, t[s])
         R[s] = pathsum(graph, w)[-1]
-        A[s] = pathsum(graph, np.abs(w))[-1]
-    return R, A
+        F = pathsum(graph, np.abs(w))
+        A[s] = F[-1]
+        if with_bound:
+            Bk = _paths_to_sink(graph, np.abs(w))
+            e = graph.edges
+            B[s] = float(np.sum(sc * F[e[:, 0]] * Bk[e[:, 1]]))
+    return (R, A, B) if with_bound else (R, A)
+
+
+def _paths_to_sink(graph, w: np.ndarray) -> np.ndarray:
+    """For every node v, the sum over v-to-sink paths of the products of w (the DP of
+    Fig. 1 run from the last level back to the first)."""
+    e = graph.edges
+    N = graph.num_nodes
+    out = np.zeros(N)
+    out[N - 1] = 1.0
+    hi = e.shape[0]
+    for l in range(graph.num_levels - 1, 0, -1):
+        lo = hi - int(graph.edge_counts[l])
+        src, dst = e[lo:hi, 0], e[lo:hi, 1]
+        out += np.bincount(src, weights=w[lo:hi] * out[dst], minlength=N)
+        hi = lo
+    return out
 
 
 def pathsum(graph, w: np.ndarray) -> np.ndarray:

@@ -361,6 +361,57 @@ def test_tabulated_formula_agrees_with_library_interpolation():
     assert np.max(np.abs(got - want)) <= 8 * np.finfo(float).eps * (11.0 * slope + np.max(np.abs(tab)))
 
 
+def test_tabulated_double_evaluations_within_the_rounding_scale():
+    # The long-double definition against three double-precision evaluations that
+    # round the grid coordinate differently (scaled by T/tau_max and shifted by T;
+    # divided by h after shifting by tau_max; numpy's own interpolation): each stays
+    # within tabulated_rounding_scale of it, including at nodes, near zeros of G and
+    # outside the grid.  A scale without its position term fails here.
+    rng = np.random.default_rng(18)
+    for T, tau_max in ((23, 9.0), (256, 10.0), (7, 3.3)):
+        tab = rng.normal(size=(2, T + 1))
+        tab[0][T // 2] = 1e-9                       # a zero crossing next to a node
+        xs = np.arange(T + 1) * (tau_max / T)
+        tau = np.concatenate([rng.uniform(-1.2 * tau_max, 1.2 * tau_max, 20000), xs, xs - tau_max,
+                              xs[T // 2] + np.array([-1e-12, 1e-12])])
+        exact = oracle.tabulated_propagator(tab, tau_max, tau)
+        scale = oracle.tabulated_rounding_scale(tab, tau_max, tau)
+        pos = tau >= 0
+        evals = []
+        u = np.where(pos, tau * (T / tau_max), tau * (T / tau_max) + T)
+        v = np.where(pos, tau / (tau_max / T), (tau + tau_max) / (tau_max / T))
+        for x in (u, v):
+            m = np.clip(np.floor(x), 0, T - 1).astype(np.int64)
+            f = np.clip(x - m, 0.0, 1.0)
+            half = np.where(pos[:, None], tab[0][None, :], tab[1][None, :])
+            a, b = half[np.arange(tau.size), m], half[np.arange(tau.size), m + 1]
+            evals.append(a + f * (b - a))
+        evals.append(np.where(pos, np.interp(tau, xs, tab[0]), np.interp(tau, xs - tau_max, tab[1])))
+        for got in evals:
+            assert np.all(np.abs(got - exact) <= scale)
+        pos_only = 4.0 * oracle.UNIT_ROUNDOFF * (np.abs(np.concatenate([tab[0], tab[1]])).max())
+        assert np.any(np.abs(evals[0] - exact) > pos_only) or np.any(np.abs(evals[1] - exact) > pos_only)
+
+
+def test_tabulated_rounding_bound_against_brute_force():
+    # B(s) = sum over edges of eps_e times the |paths| through the edge without it
+    # (forward and backward DPs) equals the brute-force sum over paths of
+    # sum_{e in path} eps_e * prod_{e' != e} |w_e'|
+    g, _, t = _random_graph(44, [1, 3, 5, 4, 2, 1], fmax=3)
+    tables = np.random.default_rng(19).normal(size=(g.num_kinds, 2, 11))
+    R, A, B = oracle.evaluate_tabulated(g, tables, 10.0, t, with_bound=True)
+    paths = oracle.brute_force_paths(g)
+    for s in range(t.shape[0]):
+        w, sc = oracle.tabulated_edge_weights(g, tables, 10.0, t[s], scale=True)
+        want = 0.0
+        for path in paths:
+            aw = np.abs(w[path])
+            for q, e in enumerate(path):
+                want += sc[e] * np.prod(np.delete(aw, q))
+        assert abs(B[s] - want) <= 1e-12 * want
+        assert B[s] > 0 and abs(A[s] - oracle.brute_force_sum(paths, w)[1]) <= 1e-13 * A[s]
+
+
 # ------------------------------------------------------------------ long-double reference
 
 def test_tight_oracle_chain_closed_form():
