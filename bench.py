@@ -6,11 +6,14 @@ attach the samples (device-resident times, transposed on the GPU) and evaluate
 the path sums of every sample (propagator table, level walk, sink values,
 compensated mean) through the C ABI.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload medium|large|tiny]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large|medium|tiny|batched|serving]
                   [--impl ours|reference]
 
-Under torchrun each rank evaluates its own batch of samples of the same graph
-(weak scaling, no data-path collective); rank 0 prints one JSON line.
+The default workload is the large graph (2^20 samples per GPU, FP32 bulk / FP64
+sink), the largest configuration that fits one GPU.  With --gpus N > 1 and no
+torchrun environment, the script starts N local ranks itself (torch.distributed.run
+on 127.0.0.1); every rank evaluates its own batch of samples of the same graph
+(weak scaling, no data-path collective) and rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -45,8 +48,17 @@ MODES = {"fp64": 0, "mixed": 1, "count": 2}
 DTYPE = {"fp64": "f64", "mixed": "f32 (sink and sample sums f64)", "count": "int64"}
 L2_FLUSH_BYTES = 512 << 20
 FALLBACK_HBM_GBS = 6800.0
-# FP64 FMA peak: 152 SMs x 2 DFMA/clk/SM x 2070 MHz (the nominal 1.25 TFLOP/s FP64 of GB300).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# Nominal FP64 multiply-add issue rate of GB300 per SM and clock (1.25 TFLOP/s over
+# 152 SMs at 2070 MHz); used only if the live probe (cos_probe_fma_rate) fails.
+NOMINAL_DFMA_PER_CLK_SM = 2.0
+# A step longer than this is timed end to end (e2e) on at most E2E_LONG_STEPS steps.
+E2E_LONG_STEP_S = 0.5
+E2E_LONG_STEPS = 5
+# Oracle check of the timed run's results: every sample up to this many, else the
+# first ORACLE_SLICE samples (a contiguous slice), plus a few for the long-double reference.
+ORACLE_FULL_MAX = 1 << 17
+ORACLE_SLICE = 1024
+ORACLE_TIGHT = 64
 
 
 def parse_args(argv=None):
@@ -55,7 +67,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving", "batched"], default="medium")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving", "batched"], default="large")
     ap.add_argument("--num-graphs", type=int, default=64, help="batched: graphs in the launch")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
@@ -66,6 +78,8 @@ def parse_args(argv=None):
     ap.add_argument("--sweep-rates", type=str, default="", help="serving: extra sustainable rates, e.g. 4,8")
     ap.add_argument("--sweep-duration", type=float, default=30.0, help="serving: seconds per extra rate")
     ap.add_argument("--mode", choices=sorted(MODES), default=None)
+    ap.add_argument("--abs", action="store_true",
+                    help="the same walk also sums |path| values (COS_EVAL_ABS; fp64 and mixed modes)")
     ap.add_argument("--samples", type=int, default=None, help="samples per GPU (default: the workload's)")
     ap.add_argument("--tuning", type=str, default="", help="JSON dict passed to cos_set_tuning")
     ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0)
@@ -109,6 +123,21 @@ def combine_means(local_sum: float, local_count: int, world: int, device=None) -
     t = torch.tensor([local_sum, float(local_count)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t[0].item()) / max(float(t[1].item()), 1.0)
+
+
+def free_port() -> int:
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_ranks(n: int, argv) -> int:
+    """Start n local ranks of this script (one per GPU) under torch.distributed.run on
+    127.0.0.1 and return their exit status; rank 0 prints the JSON line."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()), os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
 
 
 def barrier(world: int):
@@ -173,6 +202,23 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ measured peaks and profiles
 
+def fp64_fma_peak(cg, dev_index: int):
+    """FP64 multiply-add peak in TFLOP/s (2 flops per FMA): measured live by the probe
+    kernel, else the nominal issue rate x SMs x the measured maximum SM clock."""
+    import torch
+    try:
+        return 2.0 * cg.probe_fma_rate(0) / 1e12, "measured: FP64 FMA probe kernel (cos_probe_fma_rate) on this GPU"
+    except Exception:
+        sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz = float(json.load(f)["sm_max_mhz"])
+        except (OSError, KeyError, ValueError):
+            mhz = 2070.0
+        return (2.0 * NOMINAL_DFMA_PER_CLK_SM * sms * mhz * 1e6 / 1e12,
+                f"nominal: {sms} SMs x {NOMINAL_DFMA_PER_CLK_SM:g} DFMA/clk x {mhz:g} MHz")
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -223,6 +269,10 @@ def run_ours(args, rank, world, local):
     factory, default_mode, desc = WORKLOADS[args.workload]
     mode_name = args.mode or default_mode
     mode = MODES[mode_name]
+    if args.abs and mode == 2:
+        raise SystemExit("--abs needs a floating-point mode")
+    emode = mode | (cg.COS_EVAL_ABS if args.abs else 0)     # the mode argument of cos_evaluate
+    nout = 2 if args.abs else 1                              # per-sample outputs: R, then A
     kw = {} if args.samples is None else {"num_samples": args.samples}
     base = factory(**kw)
     wl = factory(seed=rank_seed({"medium": 1, "large": 2, "tiny": 0}[args.workload], rank), **kw) if rank else base
@@ -239,18 +289,18 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     t_dev = torch.from_numpy(s.t).to(dev)                                   # [S][D], resident in HBM
     out_dtype = torch.int64 if mode == 2 else torch.float64
-    out = torch.empty(S, dtype=out_dtype, device=dev)
+    out = torch.empty(nout * S, dtype=out_dtype, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
         gr.set_samples(t_dev, s.eps, s.beta, cg.COS_T_SAMPLE_MAJOR, stream=stream)
-        gr.evaluate(mode, out=out, want_mean=False, stream=stream, allow_overflow=True)
+        gr.evaluate(emode, out=out, want_mean=False, stream=stream, allow_overflow=True)
 
     for _ in range(args.warmup):
         step()
     gr.get_result(stream)
     torch.cuda.synchronize()
-    tuning = gr.get_tuning(mode)
+    tuning = gr.get_tuning(emode)
 
     uuid = None
     try:
@@ -267,7 +317,7 @@ def run_ours(args, rank, world, local):
         ev[k][0].record(stream)
         gr.set_samples(t_dev, s.eps, s.beta, cg.COS_T_SAMPLE_MAJOR, stream=stream)
         ev[k][1].record(stream)
-        gr.evaluate(mode, out=out, want_mean=False, stream=stream, allow_overflow=True)
+        gr.evaluate(emode, out=out, want_mean=False, stream=stream, allow_overflow=True)
         ev[k][2].record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -284,6 +334,8 @@ def run_ours(args, rank, world, local):
     # roofline of the walker kernel (one launch per evaluate)
     w_bytes = 4 if mode == 1 else 8
     alg_bytes = S * (2.0 * N * w_bytes + D * 8 + 8)
+    if args.abs:                                                        # A's float node values and result
+        alg_bytes += S * (2.0 * N * 4 + 8)
     walk_s = statistics.mean(walk_ms) / 1e3
     peak, peak_kind = hbm_peak()
     hbm = {"bound": "hbm", "achieved": alg_bytes / walk_s / 1e9, "peak": peak, "unit": "GB/s",
@@ -293,8 +345,9 @@ def run_ours(args, rank, world, local):
            "algorithmic_bytes_per_launch": alg_bytes}
     if mode == 0:
         tflops = 2.0 * E * S / walk_s / 1e12
-        alu = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "frac": tflops / FP64_PEAK_TFLOPS, "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2070 MHz",
+        fp64_peak, fp64_src = fp64_fma_peak(cg, local)
+        alu = {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+               "frac": tflops / fp64_peak, "peak_source": fp64_src,
                "traffic": hbm["traffic"], "algorithmic_flops_per_launch": 2.0 * E * S}
         roofline, other = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
     else:
@@ -304,49 +357,66 @@ def run_ours(args, rank, world, local):
     e2e = None
     if not args.no_e2e:
         t_host = torch.from_numpy(s.t).pin_memory()
-        r_host = torch.empty(S, dtype=out_dtype).pin_memory()
+        r_host = torch.empty(nout * S, dtype=out_dtype).pin_memory()
         for _ in range(2):
             gr.set_samples(t_host, s.eps, s.beta, cg.COS_T_HOST | cg.COS_T_SAMPLE_MAJOR, stream=stream)
-            gr.evaluate(mode, out=out, want_mean=False, stream=stream, allow_overflow=True)
+            gr.evaluate(emode, out=out, want_mean=False, stream=stream, allow_overflow=True)
             r_host.copy_(out, non_blocking=True)
         torch.cuda.synchronize()
         e_ms = []
+        e2e_steps = args.steps if total_s / args.steps <= E2E_LONG_STEP_S else min(args.steps, E2E_LONG_STEPS)
         barrier(world)
-        for k in range(args.steps):
+        for k in range(e2e_steps):
             flush.zero_()
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
             gr.set_samples(t_host, s.eps, s.beta, cg.COS_T_HOST | cg.COS_T_SAMPLE_MAJOR, stream=stream)
-            gr.evaluate(mode, out=out, want_mean=False, stream=stream, allow_overflow=True)
+            gr.evaluate(emode, out=out, want_mean=False, stream=stream, allow_overflow=True)
             r_host.copy_(out, non_blocking=True)
             b.record(stream)
             b.synchronize()
             e_ms.append(a.elapsed_time(b))
         barrier(world)
         e_total = max_over_ranks(sum(e_ms) / 1e3, world, dev)
-        e2e = {"value": units / e_total, "unit": "edge·sample updates/s",
-               "h2d_bytes_per_step": int(S * D * 8 + K * 8), "d2h_bytes_per_step": int(S * 8)}
+        e2e = {"value": float(E) * S * e2e_steps * world / e_total, "unit": "edge·sample updates/s",
+               "h2d_bytes_per_step": int(S * D * 8 + K * 8), "d2h_bytes_per_step": int(nout * S * 8),
+               "steps": e2e_steps}
 
     # error of the timed run's results against the FP64 oracle, relative to sum |paths|
     err = None
     if rank == 0 and not args.no_oracle_check:
         import oracle
-        idx = np.unique(np.r_[0, S - 1, np.linspace(0, S - 1, 30).astype(np.int64)])
-        R_or, A_or = oracle.evaluate(g, s.eps, s.beta, s.t[idx])
-        got = out.cpu().numpy()[idx]
+        full = S <= ORACLE_FULL_MAX
+        n_chk = S if full else min(S, ORACLE_SLICE)      # every sample, or the first ORACLE_SLICE
+        out_all = out.cpu().numpy()
+        got_all = out_all[:S]
+        got = got_all[:n_chk]
         if mode == 2:
             cnt, _ = oracle.count_paths(g)
-            err = {"bit_exact": bool(np.all(got == cnt)), "samples_checked": int(idx.size)}
+            err = {"bit_exact": bool(np.all(got_all == cnt)), "samples_checked": int(S)}
         else:
+            t0 = time.perf_counter()
+            R_or, A_or = oracle.evaluate(g, s.eps, s.beta, s.t[:n_chk])
+            oracle_s = time.perf_counter() - t0
             rel = np.abs(got - R_or) / A_or
-            R_ld = oracle.evaluate_tight(g, s.eps, s.beta, s.t[idx])   # long-double reference
-            rel_ld = np.abs(got - R_ld) / A_or
-            err = {"max_err_over_abs_path_sum": float(rel.max()), "median_err_over_abs_path_sum": float(np.median(rel)),
-                   "max_err_vs_long_double": float(rel_ld.max()),
-                   "oracle_max_err_vs_long_double": float((np.abs(R_or - R_ld) / A_or).max()),
-                   "tolerance": 1e-12 if mode == 0 else 1e-5, "samples_checked": int(idx.size)}
+            tol = 1e-12 if mode == 0 else 1e-5
+            err = {"max_err_over_abs_path_sum": float(rel.max()) if n_chk else 0.0,
+                   "median_err_over_abs_path_sum": float(np.median(rel)) if n_chk else 0.0,
+                   "tolerance": tol, "samples_checked": int(n_chk),
+                   "samples": "all" if full else f"the first {n_chk} (contiguous)", "oracle_s": oracle_s,
+                   "within_tolerance": bool(np.all(np.abs(got - R_or) <= tol * A_or))}
+            if full and S:
+                # the timed run's compensated mean against the oracle's Neumaier mean of all samples
+                err["mean_err_over_mean_abs_path_sum"] = float(abs(mean - oracle.neumaier_mean(R_or)) / np.mean(A_or))
+            if args.abs and n_chk:                                        # A(s) from the same walk
+                err["abs_max_rel_err"] = float(np.max(np.abs(out_all[S:S + n_chk] - A_or) / A_or))
+            nt = min(n_chk, ORACLE_TIGHT)                  # long-double reference on a few samples
+            R_ld = oracle.evaluate_tight(g, s.eps, s.beta, s.t[:nt])
+            err["max_err_vs_long_double"] = float((np.abs(got[:nt] - R_ld) / A_or[:nt]).max()) if nt else 0.0
+            err["oracle_max_err_vs_long_double"] = float((np.abs(R_or[:nt] - R_ld) / A_or[:nt]).max()) if nt else 0.0
+            err["long_double_samples"] = int(nt)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -361,7 +431,7 @@ def run_ours(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[mode_name],
         "data": "synthetic (seeded random leveled DAG and uniform sample times)",
-        "config": {"workload": desc, "mode": mode_name, "samples_per_gpu": S, "graph": {"L": g.num_levels, "N": N, "E": E,
+        "config": {"workload": desc, "mode": mode_name + ("+abs" if args.abs else ""), "samples_per_gpu": S, "graph": {"L": g.num_levels, "N": N, "E": E,
                    "K": K, "D": D}, "parallelism": f"sample-sharded x{world}, graph replicated, no collective",
                    "l2": "flushed between timed steps (512 MB write); working set larger than L2",
                    "tuning": tuning},
@@ -576,7 +646,10 @@ def run_reference(args, rank, world):
 
 
 def main(argv=None):
+    argv = sys.argv[1:] if argv is None else list(argv)
     args = parse_args(argv)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return launch_ranks(args.gpus, argv)
     rank, world, local = dist_env()
     if world > 1:
         import torch

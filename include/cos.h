@@ -60,7 +60,14 @@ enum cos_mode {
     COS_MODE_FP64 = 0,        /* propagators, products and sums in IEEE double */
     COS_MODE_FP32_MIXED = 1,  /* propagators (formed in double, rounded once) and per-level products
                                  in float; sink node and cross-sample sums in double, compensated */
-    COS_MODE_COUNT_I64 = 2    /* unit edge weights, int64 sums modulo 2^64: the number of paths */
+    COS_MODE_COUNT_I64 = 2,   /* unit edge weights, int64 sums modulo 2^64: the number of paths */
+    COS_EVAL_ABS = 16         /* flag, with modes 0 and 1: the same walk also accumulates
+                                 A(s) = sum over paths of |path value| (every factor replaced by
+                                 its absolute value), the scale against which the accuracy of R(s)
+                                 is stated.  A's node values and products are float (about 1e-6
+                                 relative: a scale, not a result), its sink and sample sums double.
+                                 Results double: per-sample outputs hold 2*S values (R(s) for s < S,
+                                 then A(s)), means two (mean R, mean A).  Wide layout only. */
 };
 
 enum cos_t_flags {
@@ -155,14 +162,16 @@ int cos_copy_times(cos_graph_t g, double* dst, void* stream);
  * the work-queue schedule plans its task list on every call and uploads it when it
  * changed (a host wait for the previous upload's copy to run precedes a new
  * upload; buffers are allocated on first use), so it is not meant for capture.
- *   mode            cos_mode
+ *   mode            cos_mode, optionally | COS_EVAL_ABS (modes 0 and 1)
  *   per_sample_out  device pointer or NULL: double[S] (FP64, FP32_MIXED) or
- *                   int64[S] (COUNT_I64), index = sample index
+ *                   int64[S] (COUNT_I64), index = sample index; with COS_EVAL_ABS
+ *                   double[2*S]: R(s) at s, A(s) at S + s
  *   mean_out        host pointer or NULL.  If non-NULL the call waits for the
  *                   stream and stores the mean over samples (Neumaier-compensated
  *                   double; in count mode the mean of the counts), and reports
- *                   kernel-side errors.  If NULL the call returns at once; use
- *                   cos_get_result to wait and collect.
+ *                   kernel-side errors; with COS_EVAL_ABS mean_out[0] = mean R and
+ *                   mean_out[1] = mean A (two doubles).  If NULL the call returns
+ *                   at once; use cos_get_result to wait and collect.
  * Errors: COS_ERR_STATE (no samples attached), COS_ERR_INVALID (mode),
  *         COS_ERR_CUDA, COS_ERR_TIMEOUT, COS_ERR_OVERFLOW (count mode, exact
  *         count > 2^63-1; the wrapped results are still written).
@@ -180,7 +189,8 @@ int cos_evaluate_abs(cos_graph_t g, int32_t mode, void* per_sample_out, double* 
 
 /*
  * Wait for the last cos_evaluate on this graph (stream = the one it ran on) and
- * return its status; if mean_out is non-NULL store its mean there.
+ * return its status; if mean_out is non-NULL store its mean there (two doubles,
+ * mean R and mean A, when that evaluation had COS_EVAL_ABS).
  */
 int cos_get_result(cos_graph_t g, double* mean_out, void* stream);
 
@@ -280,6 +290,9 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *                     exceeds 32 MB, i.e. does not stay in L2 (automatic); 3 = on
  *                     every level.  When on, each warp issues an L2 prefetch of the
  *                     next 4 edges' parent runs while it loads the current 4.
+ *                     4 and 5: as 2 and 3, but every lane of a warp issues one bulk
+ *                     L2 prefetch (cp.async.bulk.prefetch) of a whole parent run, for
+ *                     the 32 edges of the next metadata window (and of the first).
  */
 typedef struct cos_tuning {
     int32_t samples_per_lane;
@@ -320,11 +333,14 @@ int cos_autotune(cos_graph_t g, int32_t mode, void* per_sample_out, void* stream
  * and replayed by every later cos_batch_launch.
  *
  *   cos_batch_create  n distinct graph handles (each with samples attached, all on
- *                     one device), one mode for the batch, per_sample_outs[n]
+ *                     one device), one mode for the batch (optionally | COS_EVAL_ABS:
+ *                     then per-sample outputs hold 2*S doubles as in cos_evaluate),
+ *                     per_sample_outs[n]
  *                     device pointers (entries may be NULL; NULL array = none).
- *                     The handles must outlive the batch; re-attaching samples to
- *                     one of them requires a new batch (the plan captures the
- *                     workspace layout).
+ *                     The handles must outlive the batch.  Re-attaching samples to
+ *                     a member, or changing its tuning or propagator tables, makes
+ *                     the next cos_batch_launch plan again (and capture again): the
+ *                     plan holds the member's buffers and sizes.
  *   cos_batch_reset   replace the members (same rules as create) keeping the device
  *                     buffers; the previous launch must have been collected.
  *   cos_batch_set_tuning  batch-wide overrides (fields > 0): samples_per_lane and
@@ -339,9 +355,16 @@ int cos_autotune(cos_graph_t g, int32_t mode, void* per_sample_out, void* stream
  *                     kernel directly; the second captures counter reset + kernel
  *                     into a CUDA graph, which every later launch replays.
  *   cos_batch_results wait for `stream`; means[n] (host, may be NULL) receives each
- *                     graph's mean; errors as cos_evaluate (COS_ERR_TIMEOUT if a
- *                     dependency wait gave up).
- *   cos_evaluate_batch  create + launch + results + destroy in one call.
+ *                     graph's mean -- means[n][2] (mean R, mean A) for a batch whose
+ *                     mode has COS_EVAL_ABS; errors as cos_evaluate (COS_ERR_TIMEOUT
+ *                     if a dependency wait gave up).
+ *   cos_evaluate_batch  modes[n]: a cos_mode per graph (optionally | COS_EVAL_ABS);
+ *                     the graphs of each distinct mode form one batch (one persistent
+ *                     launch each, all enqueued on `stream` before the first wait),
+ *                     created, launched, collected and destroyed in this call.
+ *                     per_sample_outs as cos_batch_create (NULL = none);
+ *                     means[n][2] (host, may be NULL): [g][0] = mean R of graph g,
+ *                     [g][1] = its mean A with COS_EVAL_ABS, else NaN.
  * Per-sample results are identical to cos_evaluate's for the same tuning.
  */
 typedef struct cos_batch* cos_batch_t;
@@ -354,7 +377,7 @@ int cos_batch_autotune(cos_batch_t b, void* stream, cos_tuning* best);
 int cos_batch_launch(cos_batch_t b, void* stream);
 int cos_batch_results(cos_batch_t b, double* means, void* stream);
 int cos_batch_destroy(cos_batch_t b);
-int cos_evaluate_batch(int32_t n, const cos_graph_t* graphs, int32_t mode, void* const* per_sample_outs,
+int cos_evaluate_batch(int32_t n, const cos_graph_t* graphs, const int32_t* modes, void* const* per_sample_outs,
                        double* means, void* stream);
 
 /*
@@ -373,26 +396,38 @@ int cos_get_trace(cos_graph_t g, int64_t* out, int32_t capacity, int32_t* count)
 /*
  * cos_evaluate_static -- evaluate an existing graph without allocating device memory.
  *
- * The paper has no counterpart; this entry point exists for callers that cannot
- * call cudaMalloc when they evaluate: code running while its stream is being
- * captured into a CUDA graph, latency-bound serving loops that cannot afford an
- * allocation or the device-wide synchronisation cudaFree may imply, and host
- * applications whose own memory manager owns the device budget.  Such callers
- * create the graph once at set-up time (cos_create_graph allocates) and then
- * call this function with their own device buffers for the times and results.
+ * The paper has no counterpart.  This entry point is for callers that must not
+ * call cudaMalloc or cudaFree while they evaluate: a host framework whose own
+ * caching allocator owns the device memory budget (an allocation by this library
+ * would fail or fragment its pool), and latency-bound serving loops, where
+ * cudaMalloc and cudaFree can synchronise the device and stall other streams.
+ * Such callers create the graph once at set-up time (cos_create_graph allocates)
+ * and then call this function with their own device buffers for the times,
+ * energies and results.
  *
- * Scratch memory.  All working memory of the evaluation (node-value slabs of one
- * tile of samples, propagator table, exponential factors, partial sums, the grid
- * barrier counter and the result) lives in one file-scope __device__ array of
+ * Scratch memory.  The working memory of the evaluation -- the node-value slabs
+ * and propagator table of one tile of samples, the per-kind coefficients, the
+ * partial sums of the sample reduction, the grid-barrier counter, the error word
+ * and the result -- lives in one file-scope __device__ array of
  * COS_STATIC_SCRATCH_BYTES (64 MiB) inside the library; every GPU that loads the
  * library holds it until the process exits.  The function calls no cudaMalloc,
- * cudaFree or other allocating routine.  The control block is cleared on every
- * call; the rest keeps the last call's contents and is overwritten before use.
- * Every call on a device shares the one array, so calls whose execution overlaps
- * on the GPU (different streams, or host threads) race and give wrong results:
- * serialise them.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, which may load the module); make that first call before
- * any stream capture begins.
+ * cudaFree or other allocating routine.  The barrier counter and result are
+ * cleared on every call; the rest keeps the last call's contents and is
+ * overwritten before use.  Every call on a device shares the one array, so calls
+ * whose execution overlaps on the GPU (different streams, or host threads) race
+ * and give wrong results: serialise them.  Set-up: the first call on a device,
+ * with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress, which may load the module); it is looked up again only
+ * if the device's context changes.  Make that first call before any stream
+ * capture begins.
+ *
+ * Errors from the kernel.  With mean_out == NULL the call returns right after the
+ * launch.  A bounded wait that gives up inside the kernel (limit: the handle's
+ * timeout_ms tuning, default 10 s) leaves a failure recorded in the array; the
+ * next call that passes mean_out returns COS_ERR_TIMEOUT for it and clears it.
+ * The results of every call from the failed one up to that reporting call are
+ * then invalid.  A call with num_samples = 0 and mean_out non-NULL collects the
+ * status cheaply.
  *
  * Limits.  The tile of samples is sized to fit the array; a graph whose working
  * set for 32 samples exceeds it (roughly 2 * W_max * w + P * w bytes
@@ -409,8 +444,8 @@ int cos_get_trace(cos_graph_t g, int64_t* out, int32_t capacity, int32_t* count)
  *   beta            inverse temperature (> 0)
  *   per_sample_out  device, double[S] (FP64, FP32_MIXED) or int64[S] (COUNT_I64);
  *                   required when S > 0
- *   mean_out        host pointer or NULL; as in cos_evaluate (non-NULL waits for
- *                   the stream and reports kernel-side errors)
+ *   mean_out        host pointer or NULL; non-NULL waits for the stream, stores
+ *                   the mean over samples and reports kernel-side errors (above)
  *   stream          cudaStream_t as void*
  * Results equal those of cos_evaluate on the same samples (the per-sample sums
  * do not depend on the tile size).  Errors: as cos_evaluate, plus
@@ -427,6 +462,17 @@ int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samples, const 
  * 15 (1989)).  g supplies the device and the 2^{j/64} table.  Asynchronous on stream.
  */
 int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, double* ep, void* stream);
+
+/*
+ * Throughput of the fused multiply-add pipe of the current device, measured by a
+ * probe kernel: *fma_per_second receives multiply-adds per second (precision 0:
+ * double, 1: float) -- the denominator of the arithmetic roofline of the FP64
+ * walk, whose every edge and sample is one double multiply-add (Fig. 1: the
+ * parent's value times the propagator, added to the child).  Synchronous; takes a
+ * few milliseconds; allocates and frees a small output buffer.
+ * Errors: COS_ERR_INVALID, COS_ERR_CUDA.
+ */
+int cos_probe_fma_rate(int32_t precision, double* fma_per_second);
 
 /*
  * Resident server (continuous batching at work-item granularity).  One persistent

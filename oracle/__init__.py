@@ -12,8 +12,9 @@ Contents
   * ``brute_force_paths`` / ``brute_force_sum``: pure-Python enumeration of all
     root-to-sink paths (one path = one diagram, Sec. II.B) for tiny graphs.
   * ``tabulated_propagator`` / ``evaluate_tabulated``: a user-tabulated G(tau) per
-    kind (linear interpolation on a uniform grid, one table per sign of tau), and
-    the DP with those factors.
+    kind (linear interpolation on a uniform grid, one table per sign of tau,
+    evaluated in extended precision), the DP with those factors, and a bound on the
+    effect of a double evaluation's grid-position rounding on R.
   * ``metropolis``: Metropolis walkers over the vertex times (weight |R|,
     single-time proposals from counter-based random numbers).
 

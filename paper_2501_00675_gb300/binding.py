@@ -28,6 +28,7 @@ COS_ERR_BUSY = -7
 COS_MODE_FP64 = 0
 COS_MODE_FP32_MIXED = 1
 COS_MODE_COUNT_I64 = 2
+COS_EVAL_ABS = 16          # flag: the same walk also sums |path| values (A(s) and its mean)
 
 COS_T_DEVICE_DS = 0
 COS_T_HOST = 1
@@ -38,7 +39,7 @@ EXPORTED = ["cos_create_graph", "cos_set_samples", "cos_evaluate", "cos_get_resu
             "cos_set_tuning", "cos_get_tuning", "cos_set_trace", "cos_get_trace", "cos_evaluate_static",
             "cos_graph_share", "cos_batch_create", "cos_batch_reset", "cos_batch_set_tuning", "cos_batch_get_tuning", "cos_batch_autotune",
             "cos_batch_launch", "cos_batch_results", "cos_batch_destroy", "cos_evaluate_batch",
-            "cos_selftest_exp", "cos_set_samples_uniform", "cos_copy_times", "cos_server_create",
+            "cos_selftest_exp", "cos_probe_fma_rate", "cos_set_samples_uniform", "cos_copy_times", "cos_server_create",
             "cos_server_submit", "cos_server_poll", "cos_server_wait", "cos_server_stats", "cos_server_destroy",
             "cos_destroy", "cos_last_error"]
 
@@ -113,8 +114,9 @@ def load_library(build_if_missing: bool = False):
         lib.cos_batch_launch.argtypes = [vp, vp]
         lib.cos_batch_results.argtypes = [vp, vp, vp]
         lib.cos_batch_destroy.argtypes = [vp]
-        lib.cos_evaluate_batch.argtypes = [i32, vp, i32, vp, vp, vp]
+        lib.cos_evaluate_batch.argtypes = [i32, vp, vp, vp, vp, vp]
         lib.cos_selftest_exp.argtypes = [vp, i64, vp, vp, vp, vp]
+        lib.cos_probe_fma_rate.argtypes = [i32, ctypes.POINTER(f64)]
         lib.cos_set_samples_uniform.argtypes = [vp, i64, ctypes.c_uint64, i64, vp, f64, vp]
         lib.cos_copy_times.argtypes = [vp, vp, vp]
         lib.cos_server_create.argtypes = [i32, i32, ctypes.POINTER(CosTuning), i32, i64, i32, ctypes.POINTER(vp)]
@@ -154,6 +156,29 @@ def _stream_handle(stream) -> Optional[int]:
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def evaluate_batch(graphs: Sequence["Graph"], modes: Sequence[int], outs=None, stream=None,
+                   allow_overflow: bool = False) -> np.ndarray:
+    """cos_evaluate_batch: one mode per graph (the graphs of each distinct mode form
+    one persistent launch); returns means [n][2] (mean R, mean A or NaN)."""
+    n = len(graphs)
+    hs = (ctypes.c_void_p * max(n, 1))(*[g.handle for g in graphs])
+    ms = (ctypes.c_int32 * max(n, 1))(*[int(m) for m in modes])
+    optr = None
+    if outs is not None:
+        optr = (ctypes.c_void_p * max(n, 1))(*[_ptr(o) for o in outs])
+    means = np.zeros(max(2 * n, 1))
+    _check(load_library().cos_evaluate_batch(n, hs, ms, optr, _ptr(means), _stream_handle(stream)),
+           allow=(COS_ERR_OVERFLOW,) if allow_overflow else ())
+    return means[:2 * n].reshape(n, 2)
+
+
+def probe_fma_rate(precision: int = 0) -> float:
+    """Multiply-adds per second of the current device (0: double, 1: float)."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().cos_probe_fma_rate(precision, ctypes.byref(out)))
+    return out.value
 
 
 class Graph:
@@ -218,12 +243,15 @@ class Graph:
         _check(load_library().cos_copy_times(self._h, _ptr(dst), _stream_handle(stream)))
 
     def evaluate(self, mode: int, out=None, want_mean: bool = True, stream=None, allow_overflow: bool = False):
-        """Run cos_evaluate; returns the mean (float) if want_mean else None."""
-        mean = ctypes.c_double(0.0)
-        rc = load_library().cos_evaluate(self._h, int(mode), _ptr(out), ctypes.addressof(mean) if want_mean else None,
+        """Run cos_evaluate; returns the mean (float) -- (mean R, mean A) when mode has
+        COS_EVAL_ABS, whose out then holds 2*S values -- if want_mean, else None."""
+        means = (ctypes.c_double * 2)()
+        rc = load_library().cos_evaluate(self._h, int(mode), _ptr(out), ctypes.addressof(means) if want_mean else None,
                                          _stream_handle(stream))
         _check(rc, allow=(COS_ERR_OVERFLOW,) if allow_overflow else ())
-        return mean.value if want_mean else None
+        if not want_mean:
+            return None
+        return (means[0], means[1]) if int(mode) & COS_EVAL_ABS else means[0]
 
     def evaluate_abs(self, mode: int, out=None, want_mean: bool = True, stream=None):
         """cos_evaluate_abs: A(s) = sum of |path| values per sample; returns its mean."""
@@ -232,10 +260,12 @@ class Graph:
                                                ctypes.addressof(mean) if want_mean else None, _stream_handle(stream)))
         return mean.value if want_mean else None
 
-    def get_result(self, stream=None) -> float:
-        mean = ctypes.c_double(0.0)
-        _check(load_library().cos_get_result(self._h, ctypes.addressof(mean), _stream_handle(stream)))
-        return mean.value
+    def get_result(self, stream=None, both: bool = False):
+        """cos_get_result: the last evaluation's mean (both=True: (mean R, mean A), the
+        second meaningful after an evaluation with COS_EVAL_ABS)."""
+        means = (ctypes.c_double * 2)()
+        _check(load_library().cos_get_result(self._h, ctypes.addressof(means), _stream_handle(stream)))
+        return (means[0], means[1]) if both else means[0]
 
     def set_tuning(self, samples_per_lane=0, tile_samples=0, rows_per_warp=0, blocks_per_sm=0, timeout_ms=0,
                    layout=0, schedule=0, window_chunks=0, prefetch=0):
@@ -322,6 +352,7 @@ class Batch:
         _check(lib.cos_batch_create(n, hs, int(mode), optr, ctypes.byref(h)))
         self._h = h
         self.n = n
+        self.mode = int(mode)
 
     def reset(self, graphs: Sequence[Graph], outs=None):
         """cos_batch_reset: new members, same device buffers (previous launch must be collected)."""
@@ -356,9 +387,12 @@ class Batch:
         _check(load_library().cos_batch_launch(self._h, _stream_handle(stream)))
 
     def results(self, stream=None, allow_overflow: bool = False) -> np.ndarray:
-        means = np.zeros(max(self.n, 1))
+        """Each graph's mean ([n]); [n][2] (mean R, mean A) for a COS_EVAL_ABS batch."""
+        means = np.zeros(max(2 * self.n, 1))
         _check(load_library().cos_batch_results(self._h, _ptr(means), _stream_handle(stream)),
                allow=(COS_ERR_OVERFLOW,) if allow_overflow else ())
+        if self.mode & COS_EVAL_ABS:
+            return means[:2 * self.n].reshape(self.n, 2)
         return means[:self.n]
 
     def close(self):

@@ -19,6 +19,7 @@
 // required.  The launch (counter reset + kernel) is captured once into a CUDA
 // graph and replayed.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -51,7 +52,7 @@ struct BatchArgs {
 
 template <int MODE, int V>
 constexpr int batch_min_blocks() {
-    return (MODE == COS_MODE_FP64 && V > 2) ? 2 : 3;
+    return (Traits<MODE>::kBase == COS_MODE_FP64 && V > 2) ? 2 : 3;
 }
 
 template <int MODE, int V, int LAYOUT>
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V>()) batch_k
                 // FP64 items are long and bound by the FP64 pipe: balance their warps' edges
                 // (medium 6.56 -> 6.47 ms); the short memory-bound items of the other modes
                 // lose more to the row-pointer search than they gain (large mixed +7 %)
-                if (!item_level<MODE, V, LAYOUT, MODE == COS_MODE_FP64>(p, tk.level, tc, item,
+                if (!item_level<MODE, V, LAYOUT, Traits<MODE>::kBase == COS_MODE_FP64>(p, tk.level, tc, item,
                                                                        reinterpret_cast<unsigned char*>(smem)) &&
                     (threadIdx.x & 31) == 0) {   // a bounded wait gave up: report it for the whole launch
                     const int code = *(volatile int*)&p.ctrl->err;
@@ -155,6 +156,18 @@ const void* select_batch_layout(int mode, int vec) {
 }
 
 const void* select_batch_kernel(int mode, int vec, int layout) {
+    if (mode_has_abs(mode)) {   // sums of |path| values: the wide layout only
+        if (layout != 1) return nullptr;
+        switch (mode * 8 + vec) {
+            case kModeFp64Abs * 8 + 1: return bk<kModeFp64Abs, 1, LAYOUT_WIDE>();
+            case kModeFp64Abs * 8 + 2: return bk<kModeFp64Abs, 2, LAYOUT_WIDE>();
+            case kModeFp64Abs * 8 + 4: return bk<kModeFp64Abs, 4, LAYOUT_WIDE>();
+            case kModeMixedAbs * 8 + 1: return bk<kModeMixedAbs, 1, LAYOUT_WIDE>();
+            case kModeMixedAbs * 8 + 2: return bk<kModeMixedAbs, 2, LAYOUT_WIDE>();
+            case kModeMixedAbs * 8 + 4: return bk<kModeMixedAbs, 4, LAYOUT_WIDE>();
+            default: return nullptr;
+        }
+    }
     if (layout == 3) return select_batch_layout<LAYOUT_BULK>(mode, vec);
     if (layout == 2) return select_batch_layout<LAYOUT_GROUPED>(mode, vec);
     if (layout == 1) return select_batch_layout<LAYOUT_WIDE>(mode, vec);
@@ -169,7 +182,7 @@ using namespace cosgpu;
 struct cos_batch {
     int device = 0;
     int32_t n = 0;
-    int32_t mode = 0;
+    int32_t mode = 0;        // kernel mode id (kernel_mode of the public mode)
     std::vector<cos_graph_t> graphs;
     std::vector<void*> outs;
     cos_tuning tuning{};     // batch-level overrides (samples_per_lane, rows_per_warp, ...)
@@ -179,6 +192,7 @@ struct cos_batch {
     std::vector<WalkParams> params;
     std::vector<int> counts_overflow;
     std::vector<int32_t> joins;
+    std::vector<uint64_t> member_gen;   // each member's generation when the plan was made
     Task* h_tasks = nullptr;
     int32_t* h_joins = nullptr;
     WalkParams* h_params = nullptr;
@@ -307,9 +321,9 @@ int ensure_capacity(cos_batch* b, size_t ntasks, size_t ngraphs, size_t njoins) 
         b->h_means = nullptr;
         const size_t cap = std::max<size_t>(ngraphs, 2 * b->cap_graphs);
         if ((e = cudaMalloc(&b->d_params, sizeof(WalkParams) * cap)) != cudaSuccess ||
-            (e = cudaMalloc(&b->d_means, sizeof(double) * cap)) != cudaSuccess ||
+            (e = cudaMalloc(&b->d_means, 2 * sizeof(double) * cap)) != cudaSuccess ||
             (e = cudaMallocHost(&b->h_params, sizeof(WalkParams) * cap)) != cudaSuccess ||
-            (e = cudaMallocHost(&b->h_means, sizeof(double) * cap)) != cudaSuccess)
+            (e = cudaMallocHost(&b->h_means, 2 * sizeof(double) * cap)) != cudaSuccess)
             return set_error(COS_ERR_OOM, "batch parameters: %s", cudaGetErrorString(e));
         b->cap_graphs = cap;
     }
@@ -321,12 +335,13 @@ int plan(cos_batch* b) {
     const int mode = b->mode;
     // one vector width and layout for the whole launch (kernel template parameters)
     cos_tuning force = b->tuning;
-    if (force.samples_per_lane <= 0) force.samples_per_lane = (mode == COS_MODE_FP32_MIXED) ? 4 : 2;
-    if (force.layout <= 0) force.layout = 1;
+    if (force.samples_per_lane <= 0) force.samples_per_lane = (base_mode(mode) == COS_MODE_FP32_MIXED) ? 4 : 2;
+    if (force.layout <= 0 || mode_has_abs(mode)) force.layout = 1;   // sums of |path|: wide layout only
     const int chv = force.layout == 2 ? 32 : 32 * force.samples_per_lane;   // wide and bulk: 32 * V
     cos_tuning first = force;
     b->params.assign((size_t)b->n, WalkParams{});
     b->counts_overflow.assign((size_t)b->n, 0);
+    b->member_gen.assign((size_t)b->n, 0);
     // per graph: its tasks in issue order; dep and joins as indices into the same list
     std::vector<std::vector<Task>> lists((size_t)b->n);
     std::vector<std::vector<std::vector<int32_t>>> local_joins((size_t)b->n);
@@ -338,7 +353,8 @@ int plan(cos_batch* b) {
         GraphView gv;
         graph_view(b->graphs[(size_t)g], &gv);
         b->counts_overflow[(size_t)g] = gv.count_overflow;
-        graph_task_chain(b->params[(size_t)g], gv.widths_host, mode, chv, force.window_chunks, g, false,
+        b->member_gen[(size_t)g] = gv.generation;
+        graph_task_chain(b->params[(size_t)g], gv.widths_host, base_mode(mode), chv, force.window_chunks, g, false,
                          g == 0 && getenv("COS_TEST_STALL_TASK") != nullptr, lists[(size_t)g],
                          local_joins[(size_t)g]);
     }
@@ -392,7 +408,7 @@ int plan(cos_batch* b) {
     int rc = ensure_capacity(b, std::max<size_t>(b->tasks.size(), 1), std::max<int32_t>(b->n, 1),
                              std::max<size_t>(b->joins.size(), 1));
     if (rc != COS_OK) return rc;
-    for (int32_t g = 0; g < b->n; ++g) b->params[(size_t)g].mean_out = b->d_means + g;
+    for (int32_t g = 0; g < b->n; ++g) b->params[(size_t)g].mean_out = b->d_means + 2 * g;   // (mean R, mean A)
     drop_capture(b);
     b->planned = true;
     b->uploaded = false;
@@ -498,10 +514,11 @@ extern "C" {
 int cos_batch_create(int32_t n, const cos_graph_t* graphs, int32_t mode, void* const* per_sample_outs,
                      cos_batch_t* out) {
     if (!out) return set_error(COS_ERR_INVALID, "out is NULL");
-    if (mode < 0 || mode > 2) return set_error(COS_ERR_INVALID, "bad mode %d", mode);
+    const int km = kernel_mode(mode);
+    if (km < 0) return set_error(COS_ERR_INVALID, "bad mode %d", mode);
     cos_batch* b = new (std::nothrow) cos_batch();
     if (!b) return set_error(COS_ERR_OOM, "host allocation failed");
-    b->mode = mode;
+    b->mode = km;
     int rc = cos_batch_reset(b, n, graphs, per_sample_outs);
     if (rc != COS_OK) {
         delete b;
@@ -542,7 +559,7 @@ int cos_batch_set_tuning(cos_batch_t b, const cos_tuning* t) {
     if (t->rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
     if (t->layout < 0 || t->layout > 3) return set_error(COS_ERR_INVALID, "layout must be 0, 1, 2 or 3");
     if (t->window_chunks < 0) return set_error(COS_ERR_INVALID, "window_chunks must be >= 0");
-    if (t->prefetch < 0 || t->prefetch > 3) return set_error(COS_ERR_INVALID, "prefetch must be 0..3");
+    if (t->prefetch < 0 || t->prefetch > 5) return set_error(COS_ERR_INVALID, "prefetch must be 0..5");
     b->tuning = *t;
     b->planned = false;
     return COS_OK;
@@ -559,6 +576,15 @@ int cos_batch_launch(cos_batch_t b, void* stream) {
     DevGuard dg(b->device);
     cudaStream_t st = (cudaStream_t)stream;
     int rc = COS_OK;
+    if (b->planned) {
+        // a member whose buffers, samples or tuning changed since the plan was made:
+        // the plan (and the captured graph) hold its old pointers and sizes
+        for (int32_t g = 0; g < b->n && b->planned; ++g) {
+            GraphView gv;
+            if ((rc = graph_view(b->graphs[(size_t)g], &gv)) != COS_OK) return rc;
+            if (gv.generation != b->member_gen[(size_t)g]) b->planned = false;
+        }
+    }
     if (!b->planned) rc = plan(b);
     if (rc != COS_OK) return rc;
     if (!b->uploaded) {
@@ -596,15 +622,24 @@ int cos_batch_results(cos_batch_t b, double* means, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, sizeof(BatchCtrl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && b->n)
-        e = cudaMemcpyAsync(b->h_means, b->d_means, sizeof(double) * b->n, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(b->h_means, b->d_means, 2 * sizeof(double) * b->n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "batch results: %s", cudaGetErrorString(e));
     if (b->h_ctrl->err == KERR_BARRIER_TIMEOUT)
         return set_error(COS_ERR_TIMEOUT, "dependency wait timed out (task %d)", b->h_ctrl->err_task);
     if (b->h_ctrl->err != 0)
         return set_error(COS_ERR_CUDA, "batch kernel error %d (detail %d)", b->h_ctrl->err, b->h_ctrl->err_task);
-    if (means)
-        for (int32_t g = 0; g < b->n; ++g) means[g] = b->h_means[g];
+    if (means) {   // [n], or [n][2] (mean R, mean A) for a batch that also sums |path| values
+        const bool abs2 = mode_has_abs(b->mode);
+        for (int32_t g = 0; g < b->n; ++g) {
+            if (abs2) {
+                means[2 * g] = b->h_means[2 * g];
+                means[2 * g + 1] = b->h_means[2 * g + 1];
+            } else {
+                means[g] = b->h_means[2 * g];
+            }
+        }
+    }
     if (b->mode == COS_MODE_COUNT_I64)
         for (int32_t g = 0; g < b->n; ++g)
             if (b->counts_overflow[(size_t)g])
@@ -628,7 +663,8 @@ int cos_batch_autotune(cos_batch_t b, void* stream, cos_tuning* best_out) {
     const int layouts[] = {1, 2, 3};
     for (int lay : layouts)
     for (int v : vecs) {
-        if (b->mode == COS_MODE_FP64 && v == 4) continue;   // register-heavy; never faster in FP64
+        if (mode_has_abs(b->mode) && lay != 1) continue;    // sums of |path|: wide layout only
+        if (base_mode(b->mode) == COS_MODE_FP64 && v == 4) continue;   // register-heavy; never faster in FP64
         if (lay == 2 && v == 1) continue;                   // identical to the wide layout
         for (int r : rpws) {
             cos_tuning t = base;
@@ -682,15 +718,52 @@ int cos_batch_destroy(cos_batch_t b) {
     return COS_OK;
 }
 
-int cos_evaluate_batch(int32_t n, const cos_graph_t* graphs, int32_t mode, void* const* per_sample_outs,
+int cos_evaluate_batch(int32_t n, const cos_graph_t* graphs, const int32_t* modes, void* const* per_sample_outs,
                        double* means, void* stream) {
-    cos_batch_t b = nullptr;
-    int rc = cos_batch_create(n, graphs, mode, per_sample_outs, &b);
-    if (rc != COS_OK) return rc;
-    rc = cos_batch_launch(b, stream);
-    if (rc == COS_OK) rc = cos_batch_results(b, means, stream);
-    cos_batch_destroy(b);
-    return rc;
+    if (n < 0 || (n > 0 && (!graphs || !modes))) return set_error(COS_ERR_INVALID, "bad arguments");
+    for (int32_t g = 0; g < n; ++g)
+        if (kernel_mode(modes[g]) < 0) return set_error(COS_ERR_INVALID, "bad mode %d for graph %d", modes[g], g);
+    // one persistent launch per distinct mode (the mode is a template parameter of the
+    // kernel), in order of first appearance, all enqueued before the first wait
+    std::vector<int32_t> order;
+    for (int32_t g = 0; g < n; ++g)
+        if (std::find(order.begin(), order.end(), modes[g]) == order.end()) order.push_back(modes[g]);
+    std::vector<cos_batch_t> batches(order.size(), nullptr);
+    std::vector<std::vector<int32_t>> members(order.size());
+    int rc = COS_OK;
+    for (size_t q = 0; q < order.size() && rc == COS_OK; ++q) {
+        std::vector<cos_graph_t> gs;
+        std::vector<void*> outs;
+        for (int32_t g = 0; g < n; ++g)
+            if (modes[g] == order[q]) {
+                members[q].push_back(g);
+                gs.push_back(graphs[g]);
+                outs.push_back(per_sample_outs ? per_sample_outs[g] : nullptr);
+            }
+        rc = cos_batch_create((int32_t)gs.size(), gs.data(), order[q], outs.data(), &batches[q]);
+        if (rc == COS_OK) rc = cos_batch_launch(batches[q], stream);
+    }
+    int first_err = rc;
+    for (size_t q = 0; q < order.size(); ++q) {
+        if (!batches[q]) continue;
+        if (first_err == COS_OK) {
+            std::vector<double> m(2 * members[q].size());
+            int r = cos_batch_results(batches[q], m.data(), stream);
+            if (r == COS_OK || r == COS_ERR_OVERFLOW) {
+                const bool abs2 = mode_has_abs(kernel_mode(order[q]));
+                if (means)
+                    for (size_t j = 0; j < members[q].size(); ++j) {
+                        const int32_t g = members[q][j];
+                        means[2 * g] = abs2 ? m[2 * j] : m[j];
+                        means[2 * g + 1] = abs2 ? m[2 * j + 1] : std::nan("");
+                    }
+            }
+            if (r != COS_OK && rc == COS_OK) rc = r;
+            if (r != COS_OK && r != COS_ERR_OVERFLOW) first_err = r;
+        }
+        cos_batch_destroy(batches[q]);
+    }
+    return first_err != COS_OK ? first_err : rc;
 }
 
 }  // extern "C"

@@ -139,22 +139,29 @@ struct cos_graph {
     int last_status_pending = 0;    // 1 while an evaluate has not been collected
     unsigned long long* d_trace = nullptr;   // per-barrier timestamps of the last evaluate
     int32_t trace_cap = 0;
-    int last_mode = 0;
+    int last_mode = 0;              // kernel mode id of the last evaluate
     cos_batch_t wave = nullptr;     // one-graph batch of the windowed schedule (created on first use)
     int abs_next = 0;               // the next walk uses |factor| (cos_evaluate_abs)
     double* d_ptab = nullptr;       // user-tabulated propagators [K][2][ptab_T+1], or none
     int32_t ptab_T = 0;
     double ptab_tau_max = 0.0;
     int last_wave = 0;              // the last evaluate ran the windowed schedule
+    // Bumped whenever something a batch plan copies from the handle may change: the
+    // sample buffers, sample count or layout, the workspace, the internal result
+    // buffer, the propagator tables or the tuning.  A batch re-plans when it differs.
+    uint64_t generation = 0;
 };
 
 namespace {
 
-// Bytes of workspace per sample of a tile in a given mode.
-size_t per_sample_bytes(const cos_graph* g, int mode) {
+// Bytes of workspace per sample of a tile in a given kernel mode (two node-value slabs,
+// the propagator table, and two float slabs of A when the walk also sums |path| values).
+size_t per_sample_bytes(const cos_graph* g, int kmode) {
+    const int mode = base_mode(kmode);
     size_t val = (mode == COS_MODE_FP32_MIXED) ? 4 : 8;
     size_t gt = (mode == COS_MODE_COUNT_I64) ? 0 : val;
-    return 2 * val * (size_t)g->Wmax + gt * (size_t)g->P;
+    size_t ab = mode_has_abs(kmode) ? 2 * sizeof(float) * (size_t)g->Wmax : 0;
+    return 2 * val * (size_t)g->Wmax + gt * (size_t)g->P + ab;
 }
 
 size_t default_budget_bytes() {
@@ -163,10 +170,11 @@ size_t default_budget_bytes() {
     return (size_t)16 << 30;
 }
 
-int default_vec(int mode) { return mode == COS_MODE_FP32_MIXED ? 4 : 2; }
+int default_vec(int kmode) { return base_mode(kmode) == COS_MODE_FP32_MIXED ? 4 : 2; }
 
 // Carve the arena for one tile; returns false if it does not fit.
-bool carve(cos_graph* g, int mode, int64_t tile, WalkParams& p) {
+bool carve(cos_graph* g, int kmode, int64_t tile, WalkParams& p) {
+    const int mode = base_mode(kmode);
     size_t val = (mode == COS_MODE_FP32_MIXED) ? 4 : 8;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -178,11 +186,18 @@ bool carve(cos_graph* g, int mode, int64_t tile, WalkParams& p) {
     size_t s1 = take(val * g->Wmax * tile);
     size_t gt = 0;
     if (mode != COS_MODE_COUNT_I64) gt = take(val * g->P * tile);
+    size_t a0 = 0, a1 = 0;
+    if (mode_has_abs(kmode)) {
+        a0 = take(sizeof(float) * g->Wmax * tile);
+        a1 = take(sizeof(float) * g->Wmax * tile);
+    }
     const size_t cf = take(sizeof(double) * 2 * g->K);
     if (off > g->arena_bytes) return false;
     char* base = (char*)g->d_arena;
     p.slab[0] = base + s0;
     p.slab[1] = base + s1;
+    p.aslab[0] = mode_has_abs(kmode) ? (void*)(base + a0) : nullptr;
+    p.aslab[1] = mode_has_abs(kmode) ? (void*)(base + a1) : nullptr;
     p.gtab = (mode != COS_MODE_COUNT_I64) ? (void*)(base + gt) : nullptr;
     p.coef = (double*)(base + cf);
     return true;
@@ -496,15 +511,17 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
     if (t->schedule < 0 || t->schedule > 2)
         return fail(COS_ERR_INVALID, "schedule must be 0 (auto), 1 (level-synchronous) or 2 (windowed)");
     if (t->window_chunks < 0) return fail(COS_ERR_INVALID, "window_chunks must be >= 0");
-    if (t->prefetch < 0 || t->prefetch > 3)
-        return fail(COS_ERR_INVALID, "prefetch must be 0 (auto), 1 (off), 2 (large parent slices) or 3 (always)");
+    if (t->prefetch < 0 || t->prefetch > 5)
+        return fail(COS_ERR_INVALID, "prefetch must be 0 (auto), 1 (off), 2/4 (large parent slices) or 3/5 (always)");
     g->tuning = *t;
+    g->generation++;
     return COS_OK;
 }
 
-static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* tile_out) {
+static int resolve_tuning(cos_graph_t g, int kmode, cos_tuning* out, int64_t* tile_out) {
+    const int mode = base_mode(kmode);
     cos_tuning t = g->tuning;
-    if (t.samples_per_lane <= 0) t.samples_per_lane = default_vec(mode);
+    if (t.samples_per_lane <= 0) t.samples_per_lane = default_vec(kmode);
     // Measured on GB300: the work queue (dynamic item assignment, dependency counters)
     // is ahead on large FP64 walks and on graphs with very wide levels; the cooperative
     // kernel on the FP32 and count walks of smaller graphs and on small evaluations,
@@ -512,15 +529,15 @@ static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* til
     if (t.schedule <= 0)
         t.schedule = ((mode == COS_MODE_FP64 && (double)g->E * (double)g->S >= 1e9) || g->Wmax >= 65536) ? 2 : 1;
     if (t.rows_per_warp <= 0) t.rows_per_warp = t.schedule == 2 ? 31 : (mode == COS_MODE_FP64 ? 4 : 16);
-    if (t.layout <= 0) t.layout = 1;
+    if (t.layout <= 0 || mode_has_abs(kmode)) t.layout = 1;   // sums of |path| values: wide layout only
     if (t.timeout_ms <= 0) {
         const char* env = getenv("COS_TIMEOUT_MS");
         t.timeout_ms = (env && atoi(env) > 0) ? atoi(env) : 10000;
     }
     // the propagator phase keeps 4 x D x (32 * samples_per_lane) doubles in shared memory
-    while (t.samples_per_lane > 1 && t.layout == 1 && walk_smem_bytes(mode, t.samples_per_lane, t.layout, g->D) > (160 << 10))
+    while (t.samples_per_lane > 1 && t.layout == 1 && walk_smem_bytes(kmode, t.samples_per_lane, t.layout, g->D) > (160 << 10))
         t.samples_per_lane /= 2;
-    int dev_max = max_coresident_blocks(mode, t.samples_per_lane, t.layout, g->D, g->device);
+    int dev_max = max_coresident_blocks(kmode, t.samples_per_lane, t.layout, g->D, g->device);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     if (dev_max <= 0 || sms <= 0) return fail(COS_ERR_CUDA, "cannot query occupancy of the walker kernel");
@@ -531,8 +548,15 @@ static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* til
     int64_t tile;
     if (t.tile_samples > 0) {
         tile = round_up(t.tile_samples, ch);
+        if (mode_has_abs(kmode)) {
+            // the workspace was sized for the walks without A: a fixed tile is an upper
+            // bound for the walk that also keeps A's node values
+            const size_t slack = (size_t)4 << 20;
+            const int64_t fit = g->arena_bytes > slack ? (int64_t)((g->arena_bytes - slack) / (per_sample_bytes(g, kmode) + 1)) : 0;
+            tile = std::min<int64_t>(tile, std::max<int64_t>(ch, fit / ch * ch));
+        }
     } else {
-        size_t psb = per_sample_bytes(g, mode);
+        size_t psb = per_sample_bytes(g, kmode);
         const size_t slack = (size_t)4 << 20;   // alignment padding and coefficients
         int64_t fit = g->arena_bytes > slack ? (int64_t)((g->arena_bytes - slack) / (psb + 1)) : 0;
         tile = std::max<int64_t>(ch, fit / ch * ch);
@@ -551,14 +575,16 @@ static int resolve_tuning(cos_graph_t g, int mode, cos_tuning* out, int64_t* til
 
 int cos_get_tuning(cos_graph_t g, int32_t mode, cos_tuning* tuning) {
     if (!g || !tuning) return fail(COS_ERR_INVALID, "bad arguments");
-    if (mode < 0 || mode > 2) return fail(COS_ERR_INVALID, "bad mode %d", mode);
+    const int km = kernel_mode(mode);
+    if (km < 0) return fail(COS_ERR_INVALID, "bad mode %d", mode);
     int64_t tile;
-    return resolve_tuning(g, mode, tuning, &tile);
+    return resolve_tuning(g, km, tuning, &tile);
 }
 
 int cos_autotune(cos_graph_t g, int32_t mode, void* per_sample_out, void* stream, cos_tuning* best_out) {
     if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
-    if (mode < 0 || mode > 2) return fail(COS_ERR_INVALID, "bad mode %d", mode);
+    const int km = kernel_mode(mode);
+    if (km < 0) return fail(COS_ERR_INVALID, "bad mode %d", mode);
     if (!g->has_samples) return fail(COS_ERR_STATE, "cos_set_samples has not been called");
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -568,7 +594,8 @@ int cos_autotune(cos_graph_t g, int32_t mode, void* per_sample_out, void* stream
     const int scheds[] = {1, 2};
     const int rpws[] = {8, 16, 31};
     const int vecs_fp64[] = {2, 1}, vecs_mixed[] = {4, 2}, vecs_count[] = {2, 4};
-    const int* vecs = mode == COS_MODE_FP64 ? vecs_fp64 : mode == COS_MODE_FP32_MIXED ? vecs_mixed : vecs_count;
+    const int* vecs = base_mode(km) == COS_MODE_FP64 ? vecs_fp64
+                      : base_mode(km) == COS_MODE_FP32_MIXED ? vecs_mixed : vecs_count;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(COS_ERR_CUDA, "cannot create timing events");
@@ -606,10 +633,11 @@ int cos_autotune(cos_graph_t g, int32_t mode, void* per_sample_out, void* stream
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g->tuning = rc == COS_OK ? best : base;
+    g->generation++;
     if (rc != COS_OK) return rc;
     if (best_out) {
         int64_t tile;
-        return resolve_tuning(g, mode, best_out, &tile);
+        return resolve_tuning(g, km, best_out, &tile);
     }
     return COS_OK;
 }
@@ -644,12 +672,14 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
     if (nblk > g->partial_cap) {
         dfree(g->d_partials);
         const int64_t cap = std::max<int64_t>(nblk, 4096);   // room for 4M samples without regrowth
-        COS_CUDA(cudaMalloc(&g->d_partials, sizeof(double) * cap), "cudaMalloc partials");
+        // two arrays: partial sums of R, then of A (when the walk also sums |path| values)
+        COS_CUDA(cudaMalloc(&g->d_partials, 2 * sizeof(double) * cap), "cudaMalloc partials");
         g->partial_cap = cap;
     }
     // Workspace arena: enough for the FP64 mode over all samples, up to the budget.
     {
         size_t psb = std::max(per_sample_bytes(g, COS_MODE_FP64), per_sample_bytes(g, COS_MODE_FP32_MIXED));
+        // (the walks that also sum |path| values need more per sample; their tiles shrink to fit)
         size_t want = psb * (size_t)std::max<int64_t>(round_up(std::max<int64_t>(S, 1), 128), 128) + ((size_t)8 << 20);
         size_t budget = default_budget_bytes();
         size_t minimum = psb * 128 + ((size_t)8 << 20);
@@ -693,6 +723,7 @@ int cos_set_samples(cos_graph_t g, int64_t num_samples, const double* t, int32_t
     g->t_ld = t_ld;
     g->beta = beta;
     g->has_samples = true;
+    g->generation++;
     return COS_OK;
 }
 
@@ -714,6 +745,7 @@ int cos_set_samples_uniform(cos_graph_t g, int64_t num_samples, uint64_t seed, i
     if (rc != COS_OK) return rc;
     // ... then fill the graph's own time buffer with the counter-based draws
     g->t_borrowed = nullptr;
+    g->generation++;
     COS_CUDA(cudaMemsetAsync(g->d_t, 0, sizeof(double) * t_ld * g->D, st), "clear t");
     if (num_samples > 0) {
         rc = launch_uniform_times(seed, first_sample, num_samples, g->D, beta, g->d_t, t_ld, st);
@@ -735,12 +767,16 @@ int cos_copy_times(cos_graph_t g, double* dst, void* stream) {
 }
 
 static int collect(cos_graph_t g, double* mean_out, cudaStream_t st) {
+    const bool abs2 = mode_has_abs(g->last_mode);   // mean_out holds (mean R, mean A)
     if (g->last_wave && g->wave) {   // windowed schedule: errors are in the batch's control block
-        double m = 0.0;
-        const int rc = cos_batch_results(g->wave, &m, st);
+        double m[2] = {0.0, 0.0};
+        const int rc = cos_batch_results(g->wave, m, st);
         g->last_status_pending = 0;
         if (rc != COS_OK && rc != COS_ERR_OVERFLOW) return rc;
-        if (mean_out) *mean_out = m;
+        if (mean_out) {
+            mean_out[0] = m[0];
+            if (abs2) mean_out[1] = m[1];
+        }
         return rc;
     }
     Ctrl c;
@@ -749,7 +785,10 @@ static int collect(cos_graph_t g, double* mean_out, cudaStream_t st) {
     g->last_status_pending = 0;
     if (c.err == KERR_BARRIER_TIMEOUT) return fail(COS_ERR_TIMEOUT, "grid barrier timed out (phase %d)", c.err_detail);
     if (c.err != 0) return fail(COS_ERR_CUDA, "kernel reported error %d (detail %d)", c.err, c.err_detail);
-    if (mean_out) *mean_out = c.mean;
+    if (mean_out) {
+        mean_out[0] = c.mean;
+        if (abs2) mean_out[1] = c.mean_abs;
+    }
     if (g->last_mode == COS_MODE_COUNT_I64 && g->count_overflow)
         return fail(COS_ERR_OVERFLOW, "path count exceeds 2^63-1; results wrap modulo 2^64");
     return COS_OK;
@@ -760,9 +799,13 @@ int cos_evaluate(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean
     DeviceGuard dg(g->device);
     if (!dg.ok) return fail(COS_ERR_CUDA, "cannot select device %d", g->device);
     cudaStream_t st = (cudaStream_t)stream;
+    const int km = kernel_mode(mode);
+    if (km < 0) return fail(COS_ERR_INVALID, "bad mode %d", mode);
+    if (mode_has_abs(km) && g->abs_next)
+        return fail(COS_ERR_INVALID, "COS_EVAL_ABS and cos_evaluate_abs do not combine");
     WalkParams p;
     cos_tuning tn;
-    int rc = cosgpu::prepare_walk(g, mode, nullptr, per_sample_out, &p, &tn);
+    int rc = cosgpu::prepare_walk(g, km, nullptr, per_sample_out, &p, &tn);
     if (rc != COS_OK) return rc;
     if (const char* env = getenv("COS_TEST_SKIP_BARRIER_PHASE")) p.skip_barrier_phase = atoi(env);
     if (g->d_trace) {
@@ -772,7 +815,7 @@ int cos_evaluate(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean
     }
     COS_CUDA(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), st), "reset control block");
     if (tn.schedule == 2) {
-        rc = launch_windowed(g, &g->wave, mode, per_sample_out, tn, st);
+        rc = launch_windowed(g, &g->wave, km, per_sample_out, tn, st);
         if (rc != COS_OK) return rc;
         g->last_wave = 1;
     } else {
@@ -780,11 +823,11 @@ int cos_evaluate(cos_graph_t g, int32_t mode, void* per_sample_out, double* mean
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
         const int grid = sms * tn.blocks_per_sm;
         char msg[256] = {0};
-        rc = launch_walk(mode, tn.samples_per_lane, tn.layout, p, grid, st, msg, sizeof(msg));
+        rc = launch_walk(km, tn.samples_per_lane, tn.layout, p, grid, st, msg, sizeof(msg));
         if (rc != COS_OK) return fail(rc, "walker launch failed: %s", msg);
         g->last_wave = 0;
     }
-    g->last_mode = mode;
+    g->last_mode = km;
     g->last_status_pending = 1;
     if (mean_out) return collect(g, mean_out, st);
     return COS_OK;
@@ -830,6 +873,13 @@ int cos_selftest_exp(cos_graph_t g, int64_t n, const double* x, double* em, doub
     return rc == COS_OK ? COS_OK : fail(rc, "exp self-test launch failed");
 }
 
+int cos_probe_fma_rate(int32_t precision, double* fma_per_second) {
+    if ((precision != 0 && precision != 1) || !fma_per_second) return fail(COS_ERR_INVALID, "bad arguments");
+    char msg[256] = {0};
+    const int rc = probe_fma_rate(precision, fma_per_second, msg, sizeof(msg));
+    return rc == COS_OK ? COS_OK : fail(rc, "%s", msg);
+}
+
 int cos_set_propagator_table(cos_graph_t g, int32_t T, const double* table, double tau_max) {
     if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
     if (T < 0 || T > (1 << 24)) return fail(COS_ERR_INVALID, "T must be in [0, 2^24]");
@@ -838,6 +888,7 @@ int cos_set_propagator_table(cos_graph_t g, int32_t T, const double* table, doub
         dfree(g->d_ptab);
         g->ptab_T = 0;
         g->ptab_tau_max = 0.0;
+        g->generation++;
         return COS_OK;
     }
     if (!table) return fail(COS_ERR_INVALID, "table is NULL");
@@ -864,6 +915,7 @@ int cos_set_propagator_table(cos_graph_t g, int32_t T, const double* table, doub
     g->d_ptab = d;
     g->ptab_T = T;
     g->ptab_tau_max = tau_max;
+    g->generation++;
     return COS_OK;
 }
 
@@ -910,13 +962,20 @@ int graph_view(cos_graph_t g, GraphView* out) {
     out->t = g->t_borrowed ? const_cast<double*>(g->t_borrowed) : g->d_t;
     out->t_ld = g->t_ld;
     out->beta = g->beta;
+    out->generation = g->generation;
+    out->timeout_ms = g->tuning.timeout_ms;
+    if (out->timeout_ms <= 0) {
+        const char* env = getenv("COS_TIMEOUT_MS");
+        out->timeout_ms = (env && atoi(env) > 0) ? atoi(env) : 10000;
+    }
     return COS_OK;
 }
 
 int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sample_out, WalkParams* out,
                  cos_tuning* tn_out) {
     if (!g) return fail(COS_ERR_INVALID, "graph is NULL");
-    if (mode < 0 || mode > 2) return fail(COS_ERR_INVALID, "bad mode %d", mode);
+    if (mode < 0 || mode > kModeMixedAbs) return fail(COS_ERR_INVALID, "bad mode %d", mode);
+    const bool abs2 = mode_has_abs(mode);
     if (!g->has_samples) return fail(COS_ERR_STATE, "cos_set_samples has not been called");
     const cos_tuning saved = g->tuning;
     if (force) {
@@ -951,21 +1010,26 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
     p.beta = g->beta;
     p.S = g->S;
     p.t_ld = g->t_ld;
-    if (!per_sample_out && std::max<int64_t>(g->S, 1) > g->R_cap) {
+    const int64_t nout = std::max<int64_t>(g->S, 1) * (abs2 ? 2 : 1);   // R, then A
+    if (!per_sample_out && nout > g->R_cap) {
         // no caller buffer: the per-sample values go to an internal buffer (allocated on first need)
         if (g->d_R) cudaFree(g->d_R);
         g->d_R = nullptr;
         g->R_cap = 0;
-        COS_CUDA(cudaMalloc(&g->d_R, sizeof(double) * std::max<int64_t>(g->S, 1)), "cudaMalloc R");
-        g->R_cap = std::max<int64_t>(g->S, 1);
+        COS_CUDA(cudaMalloc(&g->d_R, sizeof(double) * nout), "cudaMalloc R");
+        g->R_cap = nout;
+        g->generation++;
     }
     p.R = per_sample_out ? per_sample_out : g->d_R;
     p.partials = g->d_partials;
+    p.Rabs = abs2 ? static_cast<double*>(p.R) + g->S : nullptr;
+    p.partials_abs = abs2 ? g->d_partials + g->partial_cap : nullptr;
     p.ctrl = g->d_ctrl;
     p.tile = tile;
     p.rows_per_warp = tn.rows_per_warp;
     p.wmax = (int32_t)g->Wmax;
-    p.pf_slice_bytes = tn.prefetch == 1 ? INT64_MAX : tn.prefetch == 3 ? 0 : ((int64_t)32 << 20);
+    p.pf_slice_bytes = tn.prefetch == 1 ? INT64_MAX : (tn.prefetch == 3 || tn.prefetch == 5) ? 0 : ((int64_t)32 << 20);
+    p.pf_bulk = tn.prefetch >= 4 ? 1 : 0;
     p.ptab = g->d_ptab;
     p.ptab_T = g->ptab_T;
     p.ptab_tau_max = g->ptab_tau_max;
@@ -994,6 +1058,7 @@ int attach_own_samples(cos_graph_t g, int64_t num_samples, SampleState* undo) {
     g->S = num_samples;
     g->t_ld = t_ld;
     g->t_borrowed = nullptr;
+    g->generation++;
     return COS_OK;
 }
 
@@ -1001,6 +1066,7 @@ void restore_samples(cos_graph_t g, const SampleState& s) {
     g->S = s.S;
     g->t_ld = s.t_ld;
     g->t_borrowed = s.t_borrowed;
+    g->generation++;
 }
 
 int set_error(int code, const char* fmt, ...) {

@@ -23,7 +23,8 @@ struct LevelDesc {
 };
 
 // Per-launch control block in device memory: grid-barrier counter, error word,
-// and the reduced result (mean and its compensated sum).
+// and the reduced result (mean and its compensated sum; the mean of A(s) when the
+// walk also accumulates sums of |path| values).
 struct Ctrl {
     unsigned long long barrier;
     int err;
@@ -31,8 +32,23 @@ struct Ctrl {
     double mean;
     double sum;
     double comp;
-    double pad;
+    double mean_abs;
 };
+
+// Kernel mode ids: the public cos_mode values 0..2, and the two floating-point modes
+// that also accumulate A(s) = sum of |path| in the same walk (COS_EVAL_ABS).
+constexpr int kModeFp64Abs = 3;
+constexpr int kModeMixedAbs = 4;
+// Kernel mode id of a public mode argument (COS_EVAL_ABS folded in); -1 if invalid.
+inline int kernel_mode(int mode) {
+    if (mode == COS_MODE_FP64 || mode == COS_MODE_FP32_MIXED || mode == COS_MODE_COUNT_I64) return mode;
+    if (mode == (COS_MODE_FP64 | COS_EVAL_ABS)) return kModeFp64Abs;
+    if (mode == (COS_MODE_FP32_MIXED | COS_EVAL_ABS)) return kModeMixedAbs;
+    return -1;
+}
+inline bool mode_has_abs(int kmode) { return kmode == kModeFp64Abs || kmode == kModeMixedAbs; }
+// The arithmetic of the R walk (0, 1 or 2) of a kernel mode id.
+inline int base_mode(int kmode) { return kmode >= kModeFp64Abs ? kmode - kModeFp64Abs : kmode; }
 
 // Everything the persistent walker needs, passed by value.
 struct WalkParams {
@@ -57,6 +73,10 @@ struct WalkParams {
                                // 128 values as float-float (hi, lo) pairs (256 floats)
     void* R;                   // [S] sink value per sample (double, or int64 in count mode)
     double* partials;          // [ceil(S/kReduceBlock)] compensated partial sums
+    // sums of |path| values in the same walk (kernel modes kModeFp64Abs, kModeMixedAbs)
+    void* aslab[2];            // [nchunk][W][CH] float node values of A, as slab[]
+    double* Rabs;              // [S] A(s) per sample
+    double* partials_abs;      // [ceil(S/kReduceBlock)] compensated partial sums of A
     Ctrl* ctrl;
     int64_t tile;              // samples per tile (multiple of CH)
     int32_t rows_per_warp;
@@ -75,6 +95,8 @@ struct WalkParams {
     int32_t ptab_T;
     int32_t abs_weights;         // 1: every factor replaced by its absolute value (A(s) = sum of |path|)
     int64_t pf_slice_bytes;      // wide layout: L2-prefetch parents on levels whose parent slice per chunk exceeds this
+    int32_t pf_bulk;             // 1: that prefetch is one bulk copy per edge run, a window of 32 edges ahead
+    int32_t pad_;
 };
 
 constexpr int kThreads = 256;           // 8 warps per CTA
@@ -102,6 +124,8 @@ struct GraphView {
     double* t;                    // attached times [D][t_ld] (the handle's or the caller's borrowed buffer)
     int64_t t_ld;
     double beta;
+    int32_t timeout_ms;           // limit of the kernels' bounded waits (the handle's tuning, else the default)
+    uint64_t generation;          // changes whenever buffers, samples, tables or tuning of the handle change
 };
 int graph_view(cos_graph_t g, GraphView* out);
 // Resolve the launch tuning of `mode` (fields of `force` > 0 override the graph's own
@@ -138,6 +162,9 @@ int max_coresident_blocks(int mode, int vec, int layout, int D, int device);
 // in shared memory), and the once-per-kernel opt-in to sizes above 48 KB.
 int walk_smem_bytes(int mode, int vec, int layout, int D);
 int prepare_kernel_attrs(const void* kernel, int smem_bytes);
+// Multiply-adds per second of the current device (precision 0: double, 1: float),
+// measured by a throughput kernel (cos_probe_fma_rate).
+int probe_fma_rate(int precision, double* per_second, char* msg, size_t msglen);
 // e^{-x} and e^{+x} with the evaluator's table-driven exponentials (self test).
 int launch_exp_pair(const double* x, int64_t n, const double* tab, double* em, double* ep, cudaStream_t stream);
 // Counter-based uniform times t[i][s] in [0, beta) for samples first..first+S-1.

@@ -210,6 +210,12 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
     return ok != 0;
 }
 
+// Bulk prefetch of `bytes` (multiple of 16, 16-byte aligned address) of global memory
+// into L2 by one thread; nothing to wait for and no registers held.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // One bulk copy global -> shared of `bytes` (multiple of 16, both addresses 16-byte
 // aligned), completing as transaction bytes on `bar`.
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
@@ -238,6 +244,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 
 // ---------------------------------------------------------------- mode traits
 
+// kBase: the arithmetic of the R walk; kAbs: the same walk also accumulates A(s), the
+// sum of |path| values, with float node values and products (a scale, not a result).
 template <int MODE>
 struct Traits;
 template <>
@@ -246,6 +254,8 @@ struct Traits<COS_MODE_FP64> {       // everything in double
     using Prop = double;
     using SinkAcc = double;
     static constexpr bool kCount = false;
+    static constexpr bool kAbs = false;
+    static constexpr int kBase = COS_MODE_FP64;
 };
 template <>
 struct Traits<COS_MODE_FP32_MIXED> { // float propagators and products, double sink
@@ -253,6 +263,8 @@ struct Traits<COS_MODE_FP32_MIXED> { // float propagators and products, double s
     using Prop = float;
     using SinkAcc = double;
     static constexpr bool kCount = false;
+    static constexpr bool kAbs = false;
+    static constexpr int kBase = COS_MODE_FP32_MIXED;
 };
 template <>
 struct Traits<COS_MODE_COUNT_I64> {  // unit weights, sums modulo 2^64
@@ -260,7 +272,28 @@ struct Traits<COS_MODE_COUNT_I64> {  // unit weights, sums modulo 2^64
     using Prop = unsigned long long;
     using SinkAcc = unsigned long long;
     static constexpr bool kCount = true;
+    static constexpr bool kAbs = false;
+    static constexpr int kBase = COS_MODE_COUNT_I64;
 };
+template <>
+struct Traits<kModeFp64Abs> : Traits<COS_MODE_FP64> {
+    static constexpr bool kAbs = true;
+};
+template <>
+struct Traits<kModeMixedAbs> : Traits<COS_MODE_FP32_MIXED> {
+    static constexpr bool kAbs = true;
+};
+
+// |x| as a float, rounded toward zero, by integer operations only (no instruction of
+// GB300's slow FP64 pipe); 0 below the float normal range, the largest float above it.
+__device__ __forceinline__ float abs_to_float(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned e = (unsigned)(b >> 52);
+    if (e < 1023u - 126u) return 0.0f;
+    if (e > 1023u + 127u) return __uint_as_float(0x7f7fffffu);
+    return __uint_as_float(((e - 1023u + 127u) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+__device__ __forceinline__ float abs_to_float(float x) { return __uint_as_float(__float_as_uint(x) & 0x7fffffffu); }
 
 // Bulk-copy ring of the level walk: edges in flight per warp, and the shared memory of
 // one CTA: kWarps x kRing mbarriers (8 B each) first, then per warp kRing slots of
@@ -469,8 +502,10 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
     const int c = tc.c0 + cl;
     const int k = item - cl * nk;
     if (warp == 0 && k == 0)
-        for (int v = lane; v < CHV; v += 32)
+        for (int v = lane; v < CHV; v += 32) {
             static_cast<typename Tr::Val*>(p.slab[0])[(int64_t)c * p.wmax * CHV + v] = (typename Tr::Val)1;
+            if constexpr (Tr::kAbs) static_cast<float*>(p.aslab[0])[(int64_t)c * p.wmax * CHV + v] = 1.0f;
+        }
     if constexpr (!Tr::kCount) {
         const int D = p.D;
         const double eps = p.eps[k], cpos = p.coef[k], cneg = p.coef[p.K + k];
@@ -525,7 +560,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
         // prefactors and products in float-float FP32 arithmetic (about 1e-10 relative
         // before the single rounding of G to float), instead of double operations on
         // GB300's slow FP64 pipe.
-        bool use_ff = (MODE == COS_MODE_FP32_MIXED && fabs(eps) * p.beta <= 30.0);
+        bool use_ff = (Tr::kBase == COS_MODE_FP32_MIXED && fabs(eps) * p.beta <= 30.0);
         if (use_ff) {
             long long* sk = reinterpret_cast<long long*>(sm);             // [D][CHV] time order keys
             float2* fp_ = reinterpret_cast<float2*>(sm + CHV * D);        // [D][CHV] coef+ e^{-eps t}
@@ -633,25 +668,51 @@ __device__ __forceinline__ void store_row(const WalkParams& p, bool sink, typena
 }
 
 // Sink row in FP32 mixed mode: in-edges accumulated as exact double products in double.
-// pc / gc already point at this lane's samples of the chunk.
-template <int V, int CHV>
+// pc / gc (and pa, the A values, when ABS) already point at this lane's samples of the chunk.
+template <int V, int CHV, bool ABS = false>
 __device__ __forceinline__ void sink_row_mixed(const WalkParams& p, const float* pc, const float* gc, int beg, int end,
-                                               int c, const TileCtx& tc, int off) {
-    double acc[V];
+                                               int c, const TileCtx& tc, int off, const float* pa = nullptr) {
+    double acc[V], acca[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = 0.0;
+    for (int v = 0; v < V; ++v) acc[v] = acca[v] = 0.0;
     for (int e = beg; e < end; ++e) {
         const int2 m = __ldg(p.edges + e);
         const VecT<float, V> pv = load_cg<float, V>(pc + (int64_t)m.x * CHV);
         const VecT<float, V> gv = load_ca<float, V>(gc + (int64_t)m.y * CHV);
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] += (double)pv.v[v] * (double)gv.v[v];   // exact product
+        if constexpr (ABS) {
+            const VecT<float, V> av = load_cg<float, V>(pa + (int64_t)m.x * CHV);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acca[v] += (double)av.v[v] * (double)abs_to_float(gv.v[v]);
+        }
     }
     double* R = static_cast<double*>(p.R);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int64_t s = tc.base + (int64_t)c * CHV + off + v;
-        if (s < p.S) R[s] = acc[v];
+        if (s < p.S) {
+            R[s] = acc[v];
+            if constexpr (ABS) p.Rabs[s] = acca[v];
+        }
+    }
+}
+
+// Store the V accumulated A values of row r (in the sink level, the per-sample A(s)).
+template <int V, int CHV>
+__device__ __forceinline__ void store_row_abs(const WalkParams& p, bool sink, float* achild, int c, int r,
+                                              const TileCtx& tc, int off, const float (&acc)[V]) {
+    if (sink) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int64_t s = tc.base + (int64_t)c * CHV + off + v;
+            if (s < p.S) p.Rabs[s] = (double)acc[v];
+        }
+    } else {
+        VecT<float, V> out;
+#pragma unroll
+        for (int v = 0; v < V; ++v) out.v[v] = acc[v];
+        store_cs<float, V>(achild + ((int64_t)c * p.wmax + r) * CHV + off, out);
     }
 }
 
@@ -682,15 +743,25 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
     const Val* pc = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * p.wmax * CHV + off;
     Val* child = static_cast<Val*>(p.slab[l & 1]);
     const Prop* gc = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV + off;
-    // levels whose parent slice per chunk is too large for L2 to keep: prefetch ahead
-    const bool pf = (int64_t)ld.prev_width * (int64_t)(CHV * sizeof(Val)) > p.pf_slice_bytes;
+    // sums of |path| values in the same walk: float node values of A beside those of R
+    constexpr bool ABS = Tr::kAbs;
+    const float* pa = ABS ? static_cast<const float*>(p.aslab[(l - 1) & 1]) + (int64_t)c * p.wmax * CHV + off : nullptr;
+    float* achild = ABS ? static_cast<float*>(p.aslab[l & 1]) : nullptr;
+    // levels whose parent slice per chunk is too large for L2 to keep: prefetch ahead,
+    // either the next U edges' parent runs line by line (pf) or, one bulk prefetch per
+    // lane, the parent runs of a whole window of 32 edges (pfb: the current window at the
+    // first window of a row range, the next window at every window)
+    const bool pf_level = (int64_t)ld.prev_width * (int64_t)(CHV * sizeof(Val)) > p.pf_slice_bytes;
+    const bool pf = pf_level && !p.pf_bulk;
+    const bool pfb = pf_level && p.pf_bulk;
     // rows [r0, r0 + nr) of the item, nr <= 31, summed by this warp in CSR order
     auto do_rows = [&](const int r0, const int nr) {
-        if constexpr (MODE == COS_MODE_FP32_MIXED) {
+        if constexpr (Tr::kBase == COS_MODE_FP32_MIXED) {
             if (sink) {
                 for (int r = r0; r < r0 + nr; ++r) {
                     const int node = ld.row_begin + r;
-                    sink_row_mixed<V, CHV>(p, pc, gc, __ldg(p.row_ptr + node), __ldg(p.row_ptr + node + 1), c, tc, off);
+                    sink_row_mixed<V, CHV, ABS>(p, pc, gc, __ldg(p.row_ptr + node), __ldg(p.row_ptr + node + 1), c,
+                                                tc, off, pa);
                 }
                 return;
             }
@@ -703,14 +774,32 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
         const unsigned nonempty = __ballot_sync(0xffffffffu, lane < nr && rp_next > rp);
         const unsigned empty = __ballot_sync(0xffffffffu, lane < nr && rp_next == rp);
         Val acc[V];
+        float acca[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = (Val)0;
-        for (unsigned m = empty; m; m &= m - 1)   // rows without in-edges hold 0
+        for (int v = 0; v < V; ++v) {
+            acc[v] = (Val)0;
+            acca[v] = 0.0f;
+        }
+        for (unsigned m = empty; m; m &= m - 1) {   // rows without in-edges hold 0
             store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(m) - 1, tc, off, acc);
+            if constexpr (ABS) store_row_abs<V, CHV>(p, sink, achild, c, r0 + __ffs(m) - 1, tc, off, acca);
+        }
         unsigned rows_left = nonempty;
         for (int w0 = beg; w0 < end; w0 += 32) {
             const int n = min(32, end - w0);
             const int2 meta = (lane < n) ? __ldg(p.edges + w0 + lane) : make_int2(0, 0);
+            if (pfb) {
+                constexpr unsigned RUNB = CHV * sizeof(Val);
+                if (w0 == beg && lane < n) {
+                    bulk_prefetch_l2(pc - off + (int64_t)meta.x * CHV, RUNB);
+                    if constexpr (ABS) bulk_prefetch_l2(pa - off + (int64_t)meta.x * CHV, 4u * CHV);
+                }
+                if (w0 + 32 + lane < end) {
+                    const int src2 = __ldg(&p.edges[w0 + 32 + lane].x);
+                    bulk_prefetch_l2(pc - off + (int64_t)src2 * CHV, RUNB);
+                    if constexpr (ABS) bulk_prefetch_l2(pa - off + (int64_t)src2 * CHV, 4u * CHV);
+                }
+            }
             // bit q set <=> edge w0+q is the last in-edge of its row
             const int pos = rp_next - 1 - w0;
             const unsigned ends = __reduce_or_sync(
@@ -722,17 +811,21 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
                     for (int u = 0; u < U; ++u) {
                         const int qn = q0 + U + u;
                         const int sn = __shfl_sync(0xffffffffu, meta.x, qn & 31);
-                        if (qn < n && (lane & LPL) == 0)
+                        if (qn < n && (lane & LPL) == 0) {
                             asm volatile("prefetch.global.L2 [%0];" ::"l"(pc + (int64_t)sn * CHV));
+                            if constexpr (ABS) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + (int64_t)sn * CHV));
+                        }
                     }
                 }
                 VecT<Val, V> pv[U];
                 VecT<Prop, V> gv[U];
+                VecT<float, V> av[ABS ? U : 1];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int q = q0 + u;
                     const int src = __shfl_sync(0xffffffffu, meta.x, q & 31);
                     pv[u] = load_cg<Val, V>(pc + (int64_t)(q < n ? src : 0) * CHV);
+                    if constexpr (ABS) av[u] = load_cg<float, V>(pa + (int64_t)(q < n ? src : 0) * CHV);
                     if constexpr (!Tr::kCount) {
                         const int slot = __shfl_sync(0xffffffffu, meta.y, q & 31);
                         gv[u] = load_ca<Prop, V>(gc + (int64_t)(q < n ? slot : 0) * CHV);
@@ -748,12 +841,22 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
                         } else {
 #pragma unroll
                             for (int v = 0; v < V; ++v) acc[v] = madd(pv[u].v[v], gv[u].v[v], acc[v]);
+                            if constexpr (ABS) {
+#pragma unroll
+                                for (int v = 0; v < V; ++v)
+                                    acca[v] = fmaf(av[u].v[v], abs_to_float(gv[u].v[v]), acca[v]);
+                            }
                         }
                         if ((ends >> q) & 1u) {
-                            store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(rows_left) - 1, tc, off, acc);
+                            const int r = r0 + __ffs(rows_left) - 1;
+                            store_row<MODE, V, CHV>(p, sink, child, c, r, tc, off, acc);
+                            if constexpr (ABS) store_row_abs<V, CHV>(p, sink, achild, c, r, tc, off, acca);
                             rows_left &= rows_left - 1;
 #pragma unroll
-                            for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+                            for (int v = 0; v < V; ++v) {
+                                acc[v] = (Val)0;
+                                acca[v] = 0.0f;
+                            }
                         }
                     }
                 }
@@ -820,7 +923,7 @@ __device__ __forceinline__ void item_level_grouped(const WalkParams& p, int l, c
     const int r0 = rb * rows_per_item + warp * rpw;
     if (r0 >= ld.width) return;
     const int nr = min(rpw, ld.width - r0);
-    if constexpr (MODE == COS_MODE_FP32_MIXED) {
+    if constexpr (Tr::kBase == COS_MODE_FP32_MIXED) {
         if (sink) {
             if (gid == 0)
                 for (int r = r0; r < r0 + nr; ++r) {
@@ -935,7 +1038,7 @@ __device__ __forceinline__ bool item_level_bulk(const WalkParams& p, int l, cons
     const int r0 = rb * rows_per_item + warp * rpw;
     if (r0 >= ld.width) return true;
     const int nr = min(rpw, ld.width - r0);
-    if constexpr (MODE == COS_MODE_FP32_MIXED) {
+    if constexpr (Tr::kBase == COS_MODE_FP32_MIXED) {
         if (sink) {
             for (int r = r0; r < r0 + nr; ++r) {
                 const int node = ld.row_begin + r;
@@ -1060,6 +1163,7 @@ __device__ __forceinline__ bool item_level_bulk(const WalkParams& p, int l, cons
 template <int MODE, int V, int LAYOUT, bool BALANCE = false>
 __device__ __forceinline__ bool item_level(const WalkParams& p, int l, const TileCtx& tc, int item,
                                            unsigned char* smem) {
+    static_assert(!Traits<MODE>::kAbs || LAYOUT == LAYOUT_WIDE, "sums of |path| values: wide layout only");
     if constexpr (LAYOUT == LAYOUT_BULK) return item_level_bulk<MODE, V>(p, l, tc, item, smem);
     if constexpr (LAYOUT == LAYOUT_WIDE) item_level_wide<MODE, V, BALANCE>(p, l, tc, item);
     else item_level_grouped<MODE, V>(p, l, tc, item);
@@ -1095,50 +1199,71 @@ __device__ __forceinline__ int partial_items(const WalkParams& p) {
     return (int)((nblk + kWarps - 1) / kWarps);
 }
 
-template <int MODE>
-__device__ __forceinline__ void item_partials(const WalkParams& p, int item) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nblk = (p.S + kReduceBlock - 1) / kReduceBlock;
-    const int64_t b = (int64_t)item * kWarps + warp;
-    if (b >= nblk) return;
+// Compensated sum of block b (kReduceBlock samples) of x, returned on every lane.
+template <typename T>
+__device__ __forceinline__ double block_sum(const T* __restrict__ x, int64_t S, int64_t b, int lane) {
     constexpr int per_lane = kReduceBlock / 32;
     constexpr int AHEAD = 8;
     const int64_t s0 = b * kReduceBlock + lane;
     double sum = 0.0, comp = 0.0;
 #pragma unroll 1
     for (int u0 = 0; u0 < per_lane; u0 += AHEAD) {
-        double x[AHEAD];
+        double v[AHEAD];
 #pragma unroll
         for (int u = 0; u < AHEAD; ++u) {
             const int64_t s = s0 + (int64_t)(u0 + u) * 32;
-            if (s < p.S) {
-                if constexpr (MODE == COS_MODE_COUNT_I64) x[u] = (double)static_cast<const long long*>(p.R)[s];
-                else x[u] = static_cast<const double*>(p.R)[s];
-            } else {
-                x[u] = 0.0;
-            }
+            v[u] = s < S ? (double)x[s] : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < AHEAD; ++u) neumaier_add(sum, comp, x[u]);
+        for (int u = 0; u < AHEAD; ++u) neumaier_add(sum, comp, v[u]);
     }
     warp_sum(sum, comp);
-    if (lane == 0) p.partials[b] = sum + comp;
+    return sum + comp;
 }
 
-// Final compensated sum of the block partials (lane-strided Neumaier, then the lane
-// tree) by warp 0 of one CTA; the mean over samples.
+template <int MODE>
+__device__ __forceinline__ void item_partials(const WalkParams& p, int item) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nblk = (p.S + kReduceBlock - 1) / kReduceBlock;
+    const int64_t b = (int64_t)item * kWarps + warp;
+    if (b >= nblk) return;
+    double v;
+    if constexpr (Traits<MODE>::kBase == COS_MODE_COUNT_I64) v = block_sum(static_cast<const long long*>(p.R), p.S, b, lane);
+    else v = block_sum(static_cast<const double*>(p.R), p.S, b, lane);
+    if (lane == 0) p.partials[b] = v;
+    if constexpr (Traits<MODE>::kAbs) {
+        v = block_sum(p.Rabs, p.S, b, lane);
+        if (lane == 0) p.partials_abs[b] = v;
+    }
+}
+
+// Compensated sum of n block partials (lane-strided Neumaier, then the lane tree).
+__device__ __forceinline__ void partials_sum(const double* x, int64_t n, int lane, double& sum, double& comp) {
+    sum = 0.0;
+    comp = 0.0;
+    for (int64_t b = lane; b < n; b += 32) neumaier_add(sum, comp, x[b]);
+    warp_sum(sum, comp);
+}
+
+// Final compensated sum of the block partials by warp 0 of one CTA; the mean over
+// samples (and the mean of A(s) when the walk accumulated it).
 __device__ __forceinline__ void item_final(const WalkParams& p) {
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     const int64_t nblk = (p.S + kReduceBlock - 1) / kReduceBlock;
-    double sum = 0.0, comp = 0.0;
-    for (int64_t b = lane; b < nblk; b += 32) neumaier_add(sum, comp, p.partials[b]);
-    warp_sum(sum, comp);
+    double sum, comp;
+    partials_sum(p.partials, nblk, lane, sum, comp);
+    double sa = 0.0, ca = 0.0;
+    if (p.partials_abs) partials_sum(p.partials_abs, nblk, lane, sa, ca);
     if (lane == 0) {
         p.ctrl->sum = sum;
         p.ctrl->comp = comp;
         p.ctrl->mean = p.S > 0 ? (sum + comp) / (double)p.S : 0.0;
-        if (p.mean_out) *p.mean_out = p.ctrl->mean;
+        p.ctrl->mean_abs = p.S > 0 ? (sa + ca) / (double)p.S : 0.0;
+        if (p.mean_out) {   // [0] the mean; [1] the mean of A(s), only when the walk accumulated it
+            p.mean_out[0] = p.ctrl->mean;
+            if (p.partials_abs) p.mean_out[1] = p.ctrl->mean_abs;
+        }
     }
 }
 

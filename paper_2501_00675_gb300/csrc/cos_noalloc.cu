@@ -1,20 +1,30 @@
 // cos_evaluate_static: evaluation of an existing graph that allocates no device
-// memory.  All scratch (node-value slabs, propagator table, exponential factors,
-// per-kind coefficients, partial sums, barrier counter and result) lives in one
-// file-scope __device__ array of COS_STATIC_SCRATCH_BYTES, which every GPU that
-// loads this library holds until the process exits.
+// memory.  All scratch -- the control block (grid-barrier counter, error word,
+// result), the partial sums of the sample reduction, the per-kind coefficients,
+// and one tile's node-value slabs and propagator table -- lives in one file-scope
+// __device__ array of COS_STATIC_SCRATCH_BYTES, which every GPU that loads this
+// library holds until the process exits.  The graph structure and the 2^{j/64}
+// table come from the graph handle, the times, energies and result buffer from the
+// caller.
 //
-// Why it exists: some callers cannot call cudaMalloc at evaluation time -- code
-// that runs while a stream is being captured into a CUDA graph, latency-bound
-// serving loops where an allocation (and the device synchronisation cudaFree can
-// imply) is not acceptable, and hosts whose memory manager owns the whole device
-// budget.  They create the graph once at set-up time, then evaluate with their
-// own device buffers for the times and results only.
+// Who needs it: callers that must not call cudaMalloc/cudaFree while they evaluate --
+// a host framework whose own caching allocator owns the device memory budget (an
+// allocation by this library would fail or fragment its pool), and latency-bound
+// serving loops, where cudaMalloc and cudaFree can synchronise the device and
+// stall other streams.  They create the graph once at set-up time, then evaluate
+// with their own buffers.
+//
+// In host code, g_static_scratch names a host-side stand-in, not device memory:
+// the kernel is given the device address that cudaGetSymbolAddress returns, looked
+// up once per device (and again if the device's context changes).
 #include <algorithm>
+#include <cstddef>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
 #include <cstdint>
+#include <cuda.h>
 
 #include "cos_internal.cuh"
 
@@ -25,21 +35,51 @@ static __device__ __align__(256) unsigned char g_static_scratch[COS_STATIC_SCRAT
 
 constexpr int kMaxDevices = 64;
 std::mutex g_addr_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+    void* ctx;    // the context the address belongs to
+    void* ptr;    // device address of g_static_scratch in that context
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on `device` (which must be current),
-// looked up once per device.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+// The current context (driver entry point reached through the runtime, so the
+// library needs no link-time dependency on the driver library); nullptr if unknown.
+void* current_context() {
+    static CtxGetCurrentFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    CUcontext c = nullptr;
+    if (fn && fn(&c) == CUDA_SUCCESS) return c;
+    return nullptr;
+}
+
+// Device address of the scratch array on `device`, which must be current.  Set-up,
+// once per device: cudaGetSymbolAddress (which may load the module).  The address
+// is kept together with the context it was taken in and looked up again when the
+// device's context differs (after cudaDeviceReset, a new primary context may load
+// the module elsewhere).
 int scratch_address(int device, void** out) {
     if (device < 0 || device >= kMaxDevices) return set_error(COS_ERR_INVALID, "device ordinal %d not supported", device);
+    void* ctx = current_context();
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_scratch_addr[device]) {
+    ScratchAddr& a = g_scratch_addr[device];
+    if (!a.ptr || !ctx || a.ctx != ctx) {
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess || !ptr)
+        if (e != cudaSuccess || !ptr) {
+            a.ptr = nullptr;
             return set_error(COS_ERR_CUDA, "cudaGetSymbolAddress(static scratch) failed: %s", cudaGetErrorString(e));
-        g_scratch_addr[device] = ptr;
+        }
+        a.ptr = ptr;
+        a.ctx = ctx;
     }
-    *out = g_scratch_addr[device];
+    *out = a.ptr;
     return COS_OK;
 }
 
@@ -135,7 +175,9 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     p.ptab_T = gv.ptab_T;
     p.ptab_tau_max = gv.ptab_tau_max;
     p.ptab_inv_h = gv.ptab ? (double)gv.ptab_T / gv.ptab_tau_max : 0.0;
-    p.timeout_ns = 10000LL * 1000000LL;
+    p.timeout_ns = (long long)gv.timeout_ms * 1000000LL;
+    // failure-detection test hook (as in cos_evaluate): CTA 0 leaves before this barrier
+    if (const char* env = getenv("COS_TEST_SKIP_BARRIER_PHASE")) p.skip_barrier_phase = atoi(env);
 
     int per_sm = 0, sms = 0;
     const int dev_max = max_coresident_blocks(mode, vec, 1, gv.D, gv.device);
@@ -143,8 +185,14 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     if (dev_max <= 0 || sms <= 0) return set_error(COS_ERR_CUDA, "cannot query occupancy");
     per_sm = dev_max / sms;
     cudaStream_t st = (cudaStream_t)stream;
-    // The barrier counter, error word and result start at zero on every call.
-    cudaError_t e = cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), st);
+    // The barrier counter and the result fields start at zero on every call.  The error
+    // word and its detail are not cleared here: a failure of a call made without
+    // mean_out stays recorded until a call with mean_out reports (and clears) it.
+    static_assert(offsetof(Ctrl, err) == sizeof(unsigned long long) && offsetof(Ctrl, mean) == 16,
+                  "control block layout");
+    char* cb = reinterpret_cast<char*>(p.ctrl);
+    cudaError_t e = cudaMemsetAsync(cb, 0, offsetof(Ctrl, err), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cb + offsetof(Ctrl, mean), 0, sizeof(Ctrl) - offsetof(Ctrl, mean), st);
     if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "clear control block: %s", cudaGetErrorString(e));
     char msg[256] = {0};
     rc = launch_walk(mode, vec, 1, p, sms * per_sm, st, msg, sizeof(msg));
@@ -154,8 +202,18 @@ extern "C" int cos_evaluate_static(cos_graph_t g, int32_t mode, int64_t num_samp
     e = cudaMemcpyAsync(&c, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "read result: %s", cudaGetErrorString(e));
-    if (c.err == KERR_BARRIER_TIMEOUT) return set_error(COS_ERR_TIMEOUT, "grid barrier timed out (phase %d)", c.err_detail);
-    if (c.err != 0) return set_error(COS_ERR_CUDA, "kernel reported error %d", c.err);
+    if (c.err != 0) {
+        // report once: clear the recorded failure so that the next call starts clean
+        e = cudaMemsetAsync(cb + offsetof(Ctrl, err), 0, 2 * sizeof(int), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return set_error(COS_ERR_CUDA, "clear error word: %s", cudaGetErrorString(e));
+        if (c.err == KERR_BARRIER_TIMEOUT)
+            return set_error(COS_ERR_TIMEOUT,
+                             "a grid barrier timed out (phase %d) in this call or in a call since the last one that "
+                             "passed mean_out; the results of those calls are invalid",
+                             c.err_detail);
+        return set_error(COS_ERR_CUDA, "kernel reported error %d", c.err);
+    }
     *mean_out = c.mean;
     if (mode == COS_MODE_COUNT_I64 && gv.count_overflow)
         return set_error(COS_ERR_OVERFLOW, "path count exceeds 2^63-1; results wrap modulo 2^64");

@@ -64,7 +64,7 @@ __device__ __noinline__ bool grid_sync(const WalkParams& p, unsigned long long& 
 // Resident CTAs per SM the register budget is tuned for (no spills at these bounds).
 template <int MODE, int V>
 constexpr int min_blocks() {
-    return (MODE == COS_MODE_FP64 && V > 2) ? 2 : 3;
+    return (Traits<MODE>::kBase == COS_MODE_FP64 && V > 2) ? 2 : 3;
 }
 
 template <int MODE, int V, int LAYOUT>
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<MODE, V>()) walk_kernel(c
         p.trace[0] = global_timer_ns();
         p.trace[1] = 0;
     }
-    if constexpr (MODE != COS_MODE_COUNT_I64) {
+    if constexpr (Traits<MODE>::kBase != COS_MODE_COUNT_I64) {
         if (blockIdx.x == 0) item_coef(p);
         if (!grid_sync(p, epoch, 1)) return;
     }
@@ -136,6 +136,26 @@ __global__ void exp_pair_kernel(const double* __restrict__ x, int64_t n, const d
     }
 }
 
+// Throughput probe of the fused multiply-add pipe: every thread runs kChains
+// independent dependency chains of `iters` multiply-adds each (far more chains per
+// SM than the pipe's latency needs), so the launch time measures the issue rate.
+// The chains' end values are stored so that nothing is optimised away.
+constexpr int kChains = 8;
+template <typename T>
+__global__ void fma_probe_kernel(T m, T a, int iters, T* __restrict__ out) {
+    T acc[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) acc[k] = (T)(threadIdx.x + k);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) acc[k] = fma(acc[k], m, a);
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += acc[k];
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 template <int MODE, int V, int LAYOUT>
 const void* kernel_ptr() {
     return reinterpret_cast<const void*>(&walk_kernel<MODE, V, LAYOUT>);
@@ -158,6 +178,18 @@ const void* select_kernel_layout(int mode, int vec) {
 }
 
 const void* select_kernel(int mode, int vec, int layout) {
+    if (mode_has_abs(mode)) {   // sums of |path| values: the wide layout only
+        if (layout != 1) return nullptr;
+        switch (mode * 8 + vec) {
+            case kModeFp64Abs * 8 + 1: return kernel_ptr<kModeFp64Abs, 1, LAYOUT_WIDE>();
+            case kModeFp64Abs * 8 + 2: return kernel_ptr<kModeFp64Abs, 2, LAYOUT_WIDE>();
+            case kModeFp64Abs * 8 + 4: return kernel_ptr<kModeFp64Abs, 4, LAYOUT_WIDE>();
+            case kModeMixedAbs * 8 + 1: return kernel_ptr<kModeMixedAbs, 1, LAYOUT_WIDE>();
+            case kModeMixedAbs * 8 + 2: return kernel_ptr<kModeMixedAbs, 2, LAYOUT_WIDE>();
+            case kModeMixedAbs * 8 + 4: return kernel_ptr<kModeMixedAbs, 4, LAYOUT_WIDE>();
+            default: return nullptr;
+        }
+    }
     if (layout == 3) return select_kernel_layout<LAYOUT_BULK>(mode, vec);
     if (layout == 2) return select_kernel_layout<LAYOUT_GROUPED>(mode, vec);
     if (layout == 1) return select_kernel_layout<LAYOUT_WIDE>(mode, vec);
@@ -172,6 +204,7 @@ int ring_bytes(int vec) {
 }
 
 int walk_smem_bytes(int mode, int vec, int layout, int D) {
+    mode = base_mode(mode);
     const int props = mode == COS_MODE_COUNT_I64 ? 0 : prop_smem_bytes(D, layout == 2 ? 32 : 32 * vec);
     if (layout != 3) return props;
     const int ring = mode == COS_MODE_FP64 ? ring_bytes<COS_MODE_FP64>(vec)
@@ -219,6 +252,46 @@ int launch_walk(int mode, int vec, int layout, const WalkParams& p, int grid, cu
         return COS_ERR_CUDA;
     }
     return COS_OK;
+}
+
+int probe_fma_rate(int precision, double* per_second, char* msg, size_t msglen) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        snprintf(msg, msglen, "cannot query the current device");
+        return COS_ERR_CUDA;
+    }
+    const int blocks = sms * 4, threads = 256, iters = 4096;
+    const size_t n = (size_t)blocks * threads;
+    void* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = COS_OK;
+    float best = 1e30f;
+    if (cudaMalloc(&out, n * sizeof(double)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        snprintf(msg, msglen, "probe set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = COS_ERR_CUDA;
+    }
+    for (int rep = 0; rep < 4 && rc == COS_OK; ++rep) {   // the first run warms up
+        cudaEventRecord(e0, 0);
+        if (precision == 0)
+            fma_probe_kernel<double><<<blocks, threads>>>(0.999999, 1e-7, iters, static_cast<double*>(out));
+        else
+            fma_probe_kernel<float><<<blocks, threads>>>(0.999999f, 1e-7f, iters, static_cast<float*>(out));
+        cudaEventRecord(e1, 0);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+            snprintf(msg, msglen, "probe kernel failed");
+            rc = COS_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, ms);
+    }
+    if (rc == COS_OK) *per_second = (double)n * iters * kChains / (best * 1e-3);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
+    return rc;
 }
 
 int launch_exp_pair(const double* x, int64_t n, const double* tab, double* em, double* ep, cudaStream_t stream) {

@@ -365,12 +365,22 @@ class ResidentScheduler:
     handle per graph, smallest graphs first, while the budget lasts.  A request's
     per-sample values stay in its handle's result buffer until the handle's next
     request.  Same submit/step/drain/close interface as ``Server``.
+
+    Order under load: the kernel's feeder shares the GPU round-robin among the
+    requests it holds, so every request it holds slows the others down.  Requests
+    are therefore handed to it oldest first and only while the work it holds (edges
+    x samples of the requests not yet complete) stays within ``max_inflight_work``
+    and their number within ``max_inflight`` -- enough to keep the GPU busy, few
+    enough that a request admitted now finishes soon, whatever its size.  A request
+    larger than the cap runs when it is the oldest and the GPU holds nothing else of
+    the cap.  Younger requests never overtake an older one that waits for the cap
+    (they may overtake one that waits for a handle of its graph).
     """
 
     def __init__(self, graphs, mode: int, budget_bytes: int = 150 << 30, max_samples: int = 1_000_000,
                  handles_per_graph: int = 2, tile_samples: int = 8192, workspace_bytes: int = 512 << 20,
                  max_queue: int = 4096, beta: float = 10.0, queue_tasks: int = 1 << 20, max_requests: int = 512,
-                 idle_ms: int = 50):
+                 idle_ms: int = 50, max_inflight: int = 64, max_inflight_work: float = 1e12):
         import torch
         from . import binding as cg
         self.torch, self.cg = torch, cg
@@ -408,6 +418,12 @@ class ResidentScheduler:
         self._rid = 0
         self.shed = 0
         self.units_done = 0.0
+        self.max_inflight = int(max_inflight)
+        self.max_inflight_work = float(max_inflight_work)
+
+    def work_of(self, r) -> float:
+        """Edges x samples of a request (its share of the GPU)."""
+        return float(self.info[r.spec.graph_id]["E"]) * r.spec.num_samples
 
     def tile_for(self, graph_id: int) -> int:
         inf = self.info[graph_id]
@@ -456,11 +472,20 @@ class ResidentScheduler:
             self.free[r.spec.graph_id].append(r._slot)
             r._slot = None
         self.inflight = still
-        # admission: oldest first; a request whose graph has no free handle waits
-        # without holding up requests on other graphs
+        # admission: oldest first, while the held work and count stay within the caps
+        # (the first request always fits); a request whose graph has no free handle
+        # waits without holding up requests on other graphs
+        cap_n = getattr(self, "max_inflight", 1 << 30)
+        cap_w = getattr(self, "max_inflight_work", float("inf"))
+        held = sum(self.work_of(r) for r in self.inflight)
         waiting = collections.deque()
         while self.queue:
             r = self.queue.popleft()
+            if self.inflight and (len(self.inflight) >= cap_n or held + self.work_of(r) > cap_w):
+                waiting.append(r)              # the caps are full: this one and every younger one wait
+                waiting.extend(self.queue)
+                self.queue.clear()
+                break
             hl = self.free[r.spec.graph_id]
             if not hl:
                 waiting.append(r)
@@ -477,6 +502,7 @@ class ResidentScheduler:
             r.t_admit = r.t_launch = time.perf_counter()
             r.status = "running"
             self.inflight.append(r)
+            held += self.work_of(r)
         self.queue = waiting
         return bool(self.inflight) or bool(self.queue) or bool(self._inbox)
 

@@ -19,6 +19,60 @@ def _free_port():
         return s.getsockname()[1]
 
 
+def _oracle_worker(rank, world, port, q):
+    """One rank of the sample-sharded path: the replicated tiny graph, this rank's own
+    samples, the rank's partial sum from the oracle, then the one exchange (an FP64
+    all-reduce of sum and count) giving the mean over both ranks' samples."""
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, _ = bench.dist_env()
+    base = tiny(num_samples=700 + 300 * r)          # uneven shards
+    mine = tiny(seed=bench.rank_seed(0, r), num_samples=700 + 300 * r)
+    R, _ = oracle.evaluate(base.graph, mine.samples.eps, mine.samples.beta, mine.samples.t)
+    mean = bench.combine_means(oracle.neumaier_sum(R), R.size, w)
+    q.put((r, mean))
+    dist.destroy_process_group()
+
+
+def test_two_rank_oracle_means_combine_over_all_samples():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_oracle_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    import oracle
+    base = tiny(num_samples=700)
+    ts = [tiny(seed=bench.rank_seed(0, r), num_samples=700 + 300 * r).samples for r in range(2)]
+    R_all = np.concatenate([oracle.evaluate(base.graph, s.eps, s.beta, s.t)[0] for s in ts])
+    want = oracle.neumaier_mean(R_all)
+    _, A_all = oracle.evaluate(base.graph, ts[0].eps, ts[0].beta, np.concatenate([s.t for s in ts]))
+    for _, m in res:
+        assert abs(m - want) <= 1e-13 * float(np.mean(A_all))
+
+
+def test_bench_starts_its_own_ranks_for_several_gpus():
+    """bench.py --gpus 2 without a torchrun environment launches two ranks itself;
+    with the reference arm only rank 0 works and prints the one JSON line."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR",
+                                                             "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--impl", "reference",
+                        "--workload", "tiny", "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=600, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1 and lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
+
+
 def _worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)

@@ -177,3 +177,41 @@ def test_queue_plans_enqueued_behind_busy_stream(cg):
         r = o.cpu().numpy()
         assert np.all(np.abs(r - R) <= 1e-12 * A)
     gr.close()
+
+
+def test_batch_replans_when_a_member_reattaches_samples(cg):
+    """A batch launched twice (the second launch captured into a CUDA graph) whose
+    member then attaches a larger sample set (new time, workspace and partial-sum
+    buffers): the next launch must plan again for the new buffers and sizes, not
+    replay the captured graph on the freed ones."""
+    wls = [tiny(num_samples=300), tiny(seed=7, num_samples=200)]
+    graphs = _setup(cg, wls)
+    outs = _outs(wls, 0)
+    b = cg.Batch(graphs, 0, outs)
+    for _ in range(3):                          # direct launch, capture, replay
+        b.launch()
+        b.results()
+    bigger = tiny(seed=8, num_samples=70000)    # > the 4096 partial sums allocated at first attach
+    graphs[0].set_samples(torch.from_numpy(bigger.samples.t).cuda(), bigger.samples.eps, bigger.samples.beta,
+                          cg.COS_T_SAMPLE_MAJOR)
+    out0 = torch.full((70000,), -5.0, dtype=torch.float64, device="cuda")
+    b.reset(graphs, [out0, outs[1]])
+    for _ in range(2):
+        b.launch()
+        means = b.results()
+    # graph 0 keeps its own structure (wls[0].graph) and now holds bigger's 70,000 samples
+    for g, smp, o, m in ((wls[0].graph, bigger.samples, out0, means[0]), (wls[1].graph, wls[1].samples, outs[1],
+                                                                          means[1])):
+        R, A = oracle.evaluate(g, smp.eps, smp.beta, smp.t)
+        assert np.all(np.abs(o.cpu().numpy() - R) <= TOL[0] * A)
+        assert abs(m - oracle.neumaier_mean(R)) <= TOL[0] * A.mean()
+    # same members and outputs, samples re-attached in place: re-planned as well
+    graphs[1].set_samples(torch.from_numpy(bigger.samples.t[:200].copy()).cuda(), bigger.samples.eps,
+                          bigger.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+    b.launch()
+    means = b.results()
+    R, A = oracle.evaluate(wls[1].graph, bigger.samples.eps, bigger.samples.beta, bigger.samples.t[:200])
+    assert np.all(np.abs(outs[1].cpu().numpy() - R) <= TOL[0] * A)
+    b.close()
+    for gr in graphs:
+        gr.close()

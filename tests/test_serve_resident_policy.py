@@ -94,3 +94,24 @@ def test_shedding():
     # the first two enter the queue (bound 2) and one of them starts; the rest are shed
     assert [r.status for r in rs] == ["running", "queued", "shed", "shed"]
     assert sch.shed == 3
+
+
+def test_held_work_cap_keeps_age_order():
+    """The server is handed requests oldest first while the work it holds (edges x
+    samples of unfinished requests) stays within the cap; the first request always
+    fits, a request waiting for the cap holds back every younger one, and a finished
+    request frees its share."""
+    sch = make([4, 4], [10, 10], slots=8)
+    sch.max_inflight, sch.max_inflight_work = 8, 10 * 500
+    big = sch.submit(RequestSpec(0, 900, 1))          # larger than the cap: runs alone
+    small = [sch.submit(RequestSpec(1, 100, 2 + q)) for q in range(5)]
+    sch.step()
+    assert big.status == "running" and all(r.status == "queued" for r in small)
+    sch.srv.finished.add(big._sid)
+    sch.step()                                        # big done: four of 100 (4000 <= 5000) start
+    assert big.status == "done"
+    assert [r.status for r in small] == ["running"] * 4 + ["queued"]
+    sch.max_inflight = 2                              # the count cap binds as well
+    sch.srv.finished.update([small[0]._sid, small[1]._sid, small[2]._sid])
+    sch.step()
+    assert small[4].status == "running" and sum(r.status == "running" for r in small) == 2
