@@ -77,6 +77,11 @@ def parse_args(argv=None):
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: device memory budget")
     ap.add_argument("--sweep-rates", type=str, default="", help="serving: extra sustainable rates, e.g. 4,8")
     ap.add_argument("--sweep-duration", type=float, default=30.0, help="serving: seconds per extra rate")
+    ap.add_argument("--serving-forms", type=str, default="resident,batched,plain",
+                    help="serving: forms to run (resident, batched, plain)")
+    ap.add_argument("--inflight-work", type=float, default=None,
+                    help="serving: resident server's cap on held work (edge x samples)")
+    ap.add_argument("--inflight-max", type=int, default=None, help="serving: resident server's cap on held requests")
     ap.add_argument("--mode", choices=sorted(MODES), default=None)
     ap.add_argument("--abs", action="store_true",
                     help="the same walk also sums |path| values (COS_EVAL_ABS; fp64 and mixed modes)")
@@ -563,9 +568,17 @@ def run_serving(args, rank, world, local):
 
     def one(rate, duration):
         res = {}
-        for name, kw in (("resident_mixed", dict(mode=cg.COS_MODE_FP32_MIXED)),
+        forms = [f.strip() for f in args.serving_forms.split(",") if f.strip()]
+        rkw = dict(mode=cg.COS_MODE_FP32_MIXED)
+        if args.inflight_work is not None:
+            rkw["max_inflight_work"] = args.inflight_work
+        if args.inflight_max is not None:
+            rkw["max_inflight"] = args.inflight_max
+        for name, kw in (("resident_mixed", rkw),
                          ("batched_mixed", dict(mode=cg.COS_MODE_FP32_MIXED, max_batch=64, streams=2)),
                          ("plain_fp64", dict(mode=cg.COS_MODE_FP64, single=True))):
+            if name.split("_")[0] not in forms:
+                continue
             if name.startswith("resident"):
                 srv = ResidentScheduler(pool, budget_bytes=budget, max_queue=args.max_queue, **kw)
             else:
@@ -591,7 +604,7 @@ def run_serving(args, rank, world, local):
         g.close()
     if rank != 0:
         return None
-    b = out["resident_mixed"]
+    b = out.get("resident_mixed") or next(iter(out.values()))
     return {
         "metric": "served edge·sample updates/s", "value": b["edge_sample_updates_per_s"],
         "unit": "edge·sample updates/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak",

@@ -977,6 +977,24 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
     if (mode < 0 || mode > kModeMixedAbs) return fail(COS_ERR_INVALID, "bad mode %d", mode);
     const bool abs2 = mode_has_abs(mode);
     if (!g->has_samples) return fail(COS_ERR_STATE, "cos_set_samples has not been called");
+    if (mode_has_abs(mode) && g->tuning.tile_samples <= 0 && (!force || force->tile_samples <= 0)) {
+        // the workspace was sized for the walks without A; grow it once (allocating path
+        // only) so that the walk with A keeps their tile of samples
+        const size_t want = std::min(per_sample_bytes(g, mode) * (size_t)std::max<int64_t>(round_up(std::max<int64_t>(g->S, 1), 128), 128) +
+                                         ((size_t)8 << 20),
+                                     std::max(default_budget_bytes(), g->arena_bytes));
+        if (want > g->arena_bytes) {
+            void* bigger = nullptr;
+            if (cudaMalloc(&bigger, want) == cudaSuccess) {   // else keep the smaller workspace (smaller tiles)
+                cudaFree(g->d_arena);
+                g->d_arena = bigger;
+                g->arena_bytes = want;
+                g->generation++;
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
     const cos_tuning saved = g->tuning;
     if (force) {
         if (force->samples_per_lane > 0) g->tuning.samples_per_lane = force->samples_per_lane;

@@ -160,6 +160,18 @@ __device__ int sv_try_claim(const ServeArgs& a, long long& pub, long long& k_out
     return 2;
 }
 
+// sv_try_claim retried while it reports exhausted tasks skipped with work left (2),
+// up to 64 times (4,096 tasks): 1 with (k, item), else 0.  Used where a CTA holds an
+// item set aside, so that "nothing claimable" means no published item is unclaimed.
+__device__ int sv_try_claim_settled(const ServeArgs& a, long long& pub, long long& k_out, int& item_out, int& ooo) {
+    for (int r = 0; r < 64; ++r) {
+        const int c = sv_try_claim(a, pub, k_out, item_out, ooo);
+        if (c != 2) return c;
+        if (ld_volatile_s32(&a.ctl->err) != 0) return 0;
+    }
+    return 0;
+}
+
 // Claim an item, waiting (bounded by the idle time) for work to be published.
 // Returns 1 with (k, item), 0 to leave (shutdown, idle, or another CTA's error).
 __device__ int sv_claim(const ServeArgs& a, long long& pub, long long& k_out, int& item_out, int& ooo) {
@@ -304,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == COS_MODE_FP64 && V > 2) ? 2
                     if (nk >= 0) {
                         k2 = nk, item2 = nitem, ooo2 = nooo;
                         nk = -1;
-                    } else if (sv_try_claim(a, pub, k2, item2, ooo2) != 1) {
+                    } else if (sv_try_claim_settled(a, pub, k2, item2, ooo2) != 1) {
                         k2 = -1;
                     }
                     // nothing claimable now: every published item is held by a running CTA,
@@ -388,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == COS_MODE_FP64 && V > 2) ? 2
             } else if (nk >= 0) {
                 k2 = nk, item2 = nitem, ooo2 = nooo;
                 nk = -1;
-            } else if (dk >= 0 ? sv_try_claim(a, pub, k2, item2, ooo2) != 1   // holding one: no idle wait
+            } else if (dk >= 0 ? sv_try_claim_settled(a, pub, k2, item2, ooo2) != 1   // holding one: no idle wait
                                : !sv_claim(a, pub, k2, item2, ooo2)) {
                 k2 = -1;
             }

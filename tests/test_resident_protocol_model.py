@@ -8,7 +8,10 @@ interleavings on the CPU.  The model follows the kernel's decision rules:
 - a host feeder bounded by the backlog and the free ring space;
 - stale cursor reads a whole ring behind a published task (the test hook);
 - per CTA an item claimed ahead and one set aside, where a CTA waits only for the
-  earliest item it holds.
+  earliest item it holds;
+- a claim attempt that gives up after a fixed number of exhausted tasks (the
+  kernel's 64) and says so, and, where a CTA holds an item set aside, claims
+  retried while they say so (bounded) before concluding that nothing is claimable.
 
 Every item must run exactly once, after its dependencies have completed.  Every
 schedule must finish (no state in which nothing can move).  The first set-aside
@@ -20,9 +23,11 @@ import pytest
 
 
 class Model:
-    def __init__(self, seed, rule="earliest", ctas=5, cap=16, backlog=8, tasks=240, stale=8):
+    def __init__(self, seed, rule="earliest", ctas=5, cap=16, backlog=8, tasks=240, stale=8, attempts=64,
+                 settle=True):
         self.rng = random.Random(seed)
         self.rule, self.cap, self.backlog, self.stale = rule, cap, backlog, stale
+        self.attempts, self.settle = attempts, settle
         # the task stream in publication order: items (some zero) and earlier dependencies
         self.items, self.deps = [], []
         for t in range(tasks):
@@ -67,7 +72,9 @@ class Model:
         return all(self.done[d % self.cap] >= self.need[d] for d in self.deps[t])
 
     def try_claim(self):
-        for _ in range(64):
+        """(task, item, out of order), None when nothing is published and unclaimed, or
+        "skipped" after `attempts` exhausted tasks with work still published."""
+        for _ in range(self.attempts):
             k = self.cursor
             if k >= self.next:
                 return None
@@ -83,6 +90,20 @@ class Model:
                 return (k + age, left - 1, age > 0)
             if self.cursor == k:
                 self.cursor += 1
+        return "skipped"
+
+    def claim_any(self):
+        """try_claim where a skip counts as nothing now (the CTA simply tries again)."""
+        r = self.try_claim()
+        return None if r == "skipped" else r
+
+    def claim_settled(self):
+        """try_claim retried while it skips (64 times at most); a skip counts as nothing
+        only without `settle` (the rule before the retry)."""
+        for _ in range(64 if self.settle else 1):
+            r = self.try_claim()
+            if r != "skipped":
+                return r
         return None
 
     def step_cta(self, c):
@@ -93,7 +114,7 @@ class Model:
             elif c["ahead"] is not None:
                 c["cur"], c["ahead"] = c["ahead"], None
             else:
-                c["cur"] = self.try_claim()
+                c["cur"] = self.claim_settled() if c["aside"] is not None else self.claim_any()
                 if c["cur"] is None and c["aside"] is not None:
                     c["cur"], c["aside"] = (c["aside"][0], c["aside"][1], False), None
             if c["cur"] is None:
@@ -114,7 +135,7 @@ class Model:
                 if c["ahead"] is not None:
                     c["cur"], c["ahead"] = c["ahead"], None
                 else:
-                    c["cur"] = self.try_claim()
+                    c["cur"] = self.claim_settled()
                 if c["cur"] is None:
                     c["cur"], c["aside"] = (k, item, False), None
             else:
@@ -128,7 +149,7 @@ class Model:
         # run: claim ahead, then the item itself
         k, item, _ = c["cur"]
         if c["ahead"] is None:
-            c["ahead"] = self.try_claim()
+            c["ahead"] = self.claim_any()
         for d in self.deps[k]:
             assert self.completed_items[d] == self.items[d], "ran before a dependency completed"
         assert 0 <= item < self.items[k]
@@ -176,3 +197,35 @@ def test_first_set_aside_rule_deadlocks():
     deadlocks on some schedules (a CTA waits for a task whose item it set aside)."""
     stuck = sum(not Model(seed, rule="first").run() for seed in range(40))
     assert stuck > 0
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_protocol_with_a_binding_attempt_cap(seed):
+    """With the claim attempt cap small enough to bind (two exhausted tasks), the
+    settled retries still let every schedule finish with every item run once."""
+    m = Model(2000 + seed, attempts=2, tasks=200)
+    assert m.run()
+    assert len(m.run_count) == sum(m.items)
+
+
+def _every_cta_holds_an_item_aside(m):
+    """The residual case of the design: every CTA holds an out-of-order item set aside
+    and waits on a second one (two stale cursor reads on every CTA at once)."""
+    return all(c["aside"] is not None for c in m.ctas)
+
+
+def test_skip_taken_as_nothing_claimable_gets_stuck():
+    """Sensitivity, on a small grid with frequent stale reads and a claim attempt cap of
+    one task: treating a skip as "nothing claimable" where a CTA holds an item set aside
+    (the rule before the retry) gets stuck with a CTA waiting on its taken-back item while
+    published items are still unclaimed; with the settled retries, every schedule that
+    gets stuck is the design's residual case (every CTA holding an item aside)."""
+    old_other, settled_other = 0, 0
+    for seed in range(40):
+        m = Model(3000 + seed, ctas=3, stale=8, attempts=1, tasks=200, settle=False, backlog=16)
+        if not m.run() and not _every_cta_holds_an_item_aside(m):
+            old_other += 1
+        m = Model(3000 + seed, ctas=3, stale=8, attempts=1, tasks=200, settle=True, backlog=16)
+        if not m.run() and not _every_cta_holds_an_item_aside(m):
+            settled_other += 1
+    assert old_other > 0 and settled_other == 0
