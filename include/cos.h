@@ -266,7 +266,10 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *                     served by 32/samples_per_lane lanes; chunks of 32 samples),
  *                     3 = wide with a bulk-copy ring (one lane stages whole parent
  *                     and propagator runs in shared memory with cp.async.bulk on
- *                     mbarriers, 8 edges in flight per warp)
+ *                     mbarriers, 8 edges in flight per warp), 4 = wide with an
+ *                     async-copy ring (every lane stages its own values of the parent
+ *                     and propagator runs with cp.async, 6 edges in flight per warp
+ *                     without registers)
  *   schedule          1 = level-synchronous: one cooperative kernel, every level of a
  *                     tile ends at a grid-wide barrier, work items assigned
  *                     statically; 2 = work queue (Sec. II.C, asynchronous evaluation

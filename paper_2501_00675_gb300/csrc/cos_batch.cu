@@ -50,13 +50,14 @@ struct BatchArgs {
     long long timeout_ns;
 };
 
-template <int MODE, int V>
+template <int MODE, int V, int LAYOUT>
 constexpr int batch_min_blocks() {
+    if (LAYOUT == LAYOUT_ASYNC) return 4;   // no loads held in registers: a fourth CTA per SM
     return (Traits<MODE>::kBase == COS_MODE_FP64 && V > 2) ? 2 : 3;
 }
 
 template <int MODE, int V, int LAYOUT>
-__global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V>()) batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kThreads, batch_min_blocks<MODE, V, LAYOUT>()) batch_kernel(const BatchArgs a) {
     constexpr int CHV = chunk_samples<V, LAYOUT>();
     extern __shared__ __align__(16) double smem[];
     // Tickets: thread 0 claims the next ticket while the current item runs and hands
@@ -168,6 +169,7 @@ const void* select_batch_kernel(int mode, int vec, int layout) {
             default: return nullptr;
         }
     }
+    if (layout == 4) return select_batch_layout<LAYOUT_ASYNC>(mode, vec);
     if (layout == 3) return select_batch_layout<LAYOUT_BULK>(mode, vec);
     if (layout == 2) return select_batch_layout<LAYOUT_GROUPED>(mode, vec);
     if (layout == 1) return select_batch_layout<LAYOUT_WIDE>(mode, vec);
@@ -557,7 +559,7 @@ int cos_batch_set_tuning(cos_batch_t b, const cos_tuning* t) {
     if (t->samples_per_lane > 0 && t->samples_per_lane != 1 && t->samples_per_lane != 2 && t->samples_per_lane != 4)
         return set_error(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
     if (t->rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
-    if (t->layout < 0 || t->layout > 3) return set_error(COS_ERR_INVALID, "layout must be 0, 1, 2 or 3");
+    if (t->layout < 0 || t->layout > 4) return set_error(COS_ERR_INVALID, "layout must be 0, 1, 2, 3 or 4");
     if (t->window_chunks < 0) return set_error(COS_ERR_INVALID, "window_chunks must be >= 0");
     if (t->prefetch < 0 || t->prefetch > 5) return set_error(COS_ERR_INVALID, "prefetch must be 0..5");
     b->tuning = *t;
@@ -660,7 +662,7 @@ int cos_batch_autotune(cos_batch_t b, void* stream, cos_tuning* best_out) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = COS_OK;
-    const int layouts[] = {1, 2, 3};
+    const int layouts[] = {1, 2, 3, 4};
     for (int lay : layouts)
     for (int v : vecs) {
         if (mode_has_abs(b->mode) && lay != 1) continue;    // sums of |path|: wide layout only

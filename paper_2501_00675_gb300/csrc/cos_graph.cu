@@ -506,8 +506,9 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
         return fail(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
     if (t->rows_per_warp > 31) return fail(COS_ERR_INVALID, "rows_per_warp must be <= 31");
     if (t->blocks_per_sm > 32) return fail(COS_ERR_INVALID, "blocks_per_sm must be <= 32");
-    if (t->layout < 0 || t->layout > 3)
-        return fail(COS_ERR_INVALID, "layout must be 0 (auto), 1 (wide), 2 (grouped) or 3 (wide, bulk-copy ring)");
+    if (t->layout < 0 || t->layout > 4)
+        return fail(COS_ERR_INVALID,
+                    "layout must be 0 (auto), 1 (wide), 2 (grouped), 3 (wide, bulk-copy ring) or 4 (wide, async-copy ring)");
     if (t->schedule < 0 || t->schedule > 2)
         return fail(COS_ERR_INVALID, "schedule must be 0 (auto), 1 (level-synchronous) or 2 (windowed)");
     if (t->window_chunks < 0) return fail(COS_ERR_INVALID, "window_chunks must be >= 0");
@@ -535,7 +536,8 @@ static int resolve_tuning(cos_graph_t g, int kmode, cos_tuning* out, int64_t* ti
         t.timeout_ms = (env && atoi(env) > 0) ? atoi(env) : 10000;
     }
     // the propagator phase keeps 4 x D x (32 * samples_per_lane) doubles in shared memory
-    while (t.samples_per_lane > 1 && t.layout == 1 && walk_smem_bytes(kmode, t.samples_per_lane, t.layout, g->D) > (160 << 10))
+    while (t.samples_per_lane > 1 && (t.layout == 1 || t.layout == 4) &&
+           walk_smem_bytes(kmode, t.samples_per_lane, t.layout, g->D) > (160 << 10))
         t.samples_per_lane /= 2;
     int dev_max = max_coresident_blocks(kmode, t.samples_per_lane, t.layout, g->D, g->device);
     int sms = 0;

@@ -24,7 +24,7 @@
 
 namespace cosgpu {
 
-enum Layout : int { LAYOUT_WIDE = 0, LAYOUT_GROUPED = 1, LAYOUT_BULK = 2 };
+enum Layout : int { LAYOUT_WIDE = 0, LAYOUT_GROUPED = 1, LAYOUT_BULK = 2, LAYOUT_ASYNC = 3 };
 
 template <int V, int LAYOUT>
 __host__ __device__ constexpr int chunk_samples() {
@@ -309,6 +309,42 @@ __host__ __device__ constexpr int bulk_ring_bytes() {
                       (Traits<MODE>::kCount ? 0 : 32 * V * (int)sizeof(typename Traits<MODE>::Prop)));
 }
 
+// Async-copy ring of the level walk (LAYOUT_ASYNC): edges in flight per warp; per warp
+// kAsyncRing slots, each the warp's parent run then its propagator run (every lane
+// copies and later reads only its own V values of both).
+constexpr int kAsyncRing = 6;
+
+template <int MODE, int V>
+__host__ __device__ constexpr int async_ring_bytes() {
+    return kWarps * kAsyncRing * 32 * V *
+           ((int)sizeof(typename Traits<MODE>::Val) + (Traits<MODE>::kCount ? 0 : (int)sizeof(typename Traits<MODE>::Prop)));
+}
+
+// Per-thread asynchronous copy global -> shared of 4, 8, 16 or 32 bytes (both addresses
+// aligned to the size, 16 for 32), committed by the caller as part of a group.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_lane(void* dst, const void* src) {
+    if constexpr (BYTES == 32) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst) + 16u),
+                     "l"(static_cast<const char*>(src) + 16)
+                     : "memory");
+    } else if constexpr (BYTES == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// Keep a computed value ahead of later volatile asm (a copy into the slot it was read from).
+__device__ __forceinline__ void order_after(double& x) { asm volatile("" : "+d"(x)); }
+__device__ __forceinline__ void order_after(float& x) { asm volatile("" : "+f"(x)); }
+__device__ __forceinline__ void order_after(unsigned long long& x) { asm volatile("" : "+l"(x)); }
+
 __device__ __forceinline__ double madd(double p, double g, double acc) { return fma(p, g, acc); }
 __device__ __forceinline__ float madd(float p, float g, float acc) { return fmaf(p, g, acc); }
 
@@ -481,8 +517,15 @@ __device__ __forceinline__ long long time_order_key(double t) {
     return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
 }
 
-// Shared memory of one propagator item: times and exponentials of the chunk's samples.
-__host__ __device__ constexpr int prop_smem_bytes(int D, int chv) { return 4 * 8 * D * chv; }
+// Samples of a chunk that one pass of a propagator item keeps in shared memory.
+template <int CHV>
+__host__ __device__ constexpr int prop_pass_samples() {
+    return CHV < 64 ? CHV : 64;
+}
+
+// Shared memory of one propagator item: times and exponentials of one pass's samples
+// (at most 64 of the chunk's samples at a time).
+__host__ __device__ constexpr int prop_smem_bytes(int D, int chv) { return 4 * 8 * D * (chv < 64 ? chv : 64); }
 
 // Load the chunk's t_i for every time i, form e^{-eps_k t_i} (times the tau >= 0 and
 // tau < 0 prefactors) and e^{+eps_k t_i} in shared memory, then write every propagator
@@ -491,11 +534,13 @@ __host__ __device__ constexpr int prop_smem_bytes(int D, int chv) { return 4 * 8
 // formed in double, rounded once to the propagator type.  The kind-k slots are the
 // contiguous range [kind_slot[k], kind_slot[k+1]); bit 30 of a slot's j field marks a
 // fermion-loop edge, whose factor is negated.  The first kind also writes the
-// chunk's root values (node 0 holds 1, Fig. 1 caption).
+// chunk's root values (node 0 holds 1, Fig. 1 caption).  The chunk's samples are
+// taken in passes of at most 64 (the shared memory holds one pass).
 template <int MODE, int CHV>
 __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& tc, int item, double* sm) {
     using Tr = Traits<MODE>;
     using Prop = typename Tr::Prop;
+    constexpr int PCH = prop_pass_samples<CHV>();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nk = Tr::kCount ? 1 : p.K;
     const int cl = item / nk;   // chunk within the item range
@@ -509,16 +554,17 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
     if constexpr (!Tr::kCount) {
         const int D = p.D;
         const double eps = p.eps[k], cpos = p.coef[k], cneg = p.coef[p.K + k];
-        const int64_t s0 = tc.base + (int64_t)c * CHV;
         const int q0 = __ldg(p.kind_slot + k), q1 = __ldg(p.kind_slot + k + 1);
-        Prop* gt = static_cast<Prop*>(p.gtab) + (int64_t)c * p.P * CHV;
+        for (int h0 = 0; h0 < CHV; h0 += PCH) {   // pass: samples [h0, h0 + PCH) of the chunk
+        const int64_t s0 = tc.base + (int64_t)c * CHV + h0;
+        Prop* gt = static_cast<Prop*>(p.gtab) + (int64_t)c * p.P * CHV + h0;
         if (p.ptab) {
             // user-tabulated G_k: linear interpolation on the half of the table that
             // the sign of tau selects (tau = 0 takes the tau >= 0 half), in double,
             // rounded once to the propagator type; end values outside the grid
-            double* st = sm;   // [D][CHV] times
-            for (int x = threadIdx.x; x < CHV * D; x += blockDim.x) {
-                const int i = x / CHV, s = x - i * CHV;
+            double* st = sm;   // [D][PCH] times
+            for (int x = threadIdx.x; x < PCH * D; x += blockDim.x) {
+                const int i = x / PCH, s = x - i * PCH;
                 st[x] = p.t[(int64_t)i * p.t_ld + s0 + s];
             }
             __syncthreads();
@@ -530,12 +576,11 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                 const long long smask = (jw & 0x40000000) ? (long long)0x8000000000000000ULL : 0LL;
                 const long long amask = p.abs_weights ? 0x7FFFFFFFFFFFFFFFLL : -1LL;
 #pragma unroll
-                for (int v = 0; v < CHV / 32; ++v) {
-                    const double tau = st[i * CHV + v * 32 + lane] - st[j * CHV + v * 32 + lane];
+                for (int v = 0; v < PCH / 32; ++v) {
+                    const double tau = st[i * PCH + v * 32 + lane] - st[j * PCH + v * 32 + lane];
                     const bool pos = tau >= 0.0;
                     // grid coordinate: tau/h on the tau >= 0 half, (tau + tau_max)/h = tau/h + T
-                    // below; every step rounded once (no contraction), so that the position in
-                    // the interval is the same on every implementation of the definition
+                    // below; every step rounded once (no contraction)
                     const double u = __dadd_rn(__dmul_rn(tau, p.ptab_inv_h), pos ? 0.0 : (double)T);
                     int m = (int)u;
                     double f = __dsub_rn(u, (double)m);
@@ -552,8 +597,8 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                     __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
                 }
             }
-            __syncthreads();   // the next item reuses the shared memory
-            return;
+            __syncthreads();   // the next pass or item reuses the shared memory
+            continue;
         }
         // FP32 mode with every factor and its low half inside the normal float range
         // (|eps| beta <= 30, so factors lie within e^{+-60}): exponentials,
@@ -562,15 +607,15 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
         // GB300's slow FP64 pipe.
         bool use_ff = (Tr::kBase == COS_MODE_FP32_MIXED && fabs(eps) * p.beta <= 30.0);
         if (use_ff) {
-            long long* sk = reinterpret_cast<long long*>(sm);             // [D][CHV] time order keys
-            float2* fp_ = reinterpret_cast<float2*>(sm + CHV * D);        // [D][CHV] coef+ e^{-eps t}
-            float2* fn_ = fp_ + CHV * D;                                  // [D][CHV] coef- e^{-eps t}
-            float2* fe_ = fn_ + CHV * D;                                  // [D][CHV] e^{+eps t}
+            long long* sk = reinterpret_cast<long long*>(sm);             // [D][PCH] time order keys
+            float2* fp_ = reinterpret_cast<float2*>(sm + PCH * D);        // [D][PCH] coef+ e^{-eps t}
+            float2* fn_ = fp_ + PCH * D;                                  // [D][PCH] coef- e^{-eps t}
+            float2* fe_ = fn_ + PCH * D;                                  // [D][PCH] e^{+eps t}
             const float2 cp2 = split_ff(cpos), cn2 = split_ff(cneg);
             const float2* tff = reinterpret_cast<const float2*>(p.exp_tab + 128);
             bool out_of_range = false;   // times outside [-beta, beta]: take the double path
-            for (int x = threadIdx.x; x < CHV * D; x += blockDim.x) {
-                const int i = x / CHV, s = x - i * CHV;
+            for (int x = threadIdx.x; x < PCH * D; x += blockDim.x) {
+                const int i = x / PCH, s = x - i * PCH;
                 const double t = p.t[(int64_t)i * p.t_ld + s0 + s];
                 const double arg = eps * t;
                 if (!(fabs(arg) <= 30.0)) {
@@ -592,8 +637,8 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                     const unsigned smask = (jw & 0x40000000) ? 0x80000000u : 0u;   // closes a fermion loop
                     const unsigned amask = p.abs_weights ? 0x7FFFFFFFu : 0xFFFFFFFFu;   // |G| for A(s)
 #pragma unroll
-                    for (int v = 0; v < CHV / 32; ++v) {
-                        const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
+                    for (int v = 0; v < PCH / 32; ++v) {
+                        const int xi = i * PCH + v * 32 + lane, xj = j * PCH + v * 32 + lane;
                         const float2 a = (sk[xi] >= sk[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
                         __stcg(reinterpret_cast<float*>(gt) + (int64_t)q * CHV + v * 32 + lane,
                                __uint_as_float((__float_as_uint(mul_ff(a, fe_[xj])) ^ smask) & amask));
@@ -602,12 +647,12 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
             }
         }
         if (!use_ff) {
-            long long* sk = reinterpret_cast<long long*>(sm);   // [D][CHV] time order keys
-            double* sp = sm + CHV * D;        // [D][CHV] coef+ e^{-eps t}
-            double* sn = sm + 2 * CHV * D;    // [D][CHV] coef- e^{-eps t}
-            double* se = sm + 3 * CHV * D;    // [D][CHV] e^{+eps t}
-            for (int x = threadIdx.x; x < CHV * D; x += blockDim.x) {
-                const int i = x / CHV, s = x - i * CHV;
+            long long* sk = reinterpret_cast<long long*>(sm);   // [D][PCH] time order keys
+            double* sp = sm + PCH * D;        // [D][PCH] coef+ e^{-eps t}
+            double* sn = sm + 2 * PCH * D;    // [D][PCH] coef- e^{-eps t}
+            double* se = sm + 3 * PCH * D;    // [D][PCH] e^{+eps t}
+            for (int x = threadIdx.x; x < PCH * D; x += blockDim.x) {
+                const int i = x / PCH, s = x - i * PCH;
                 const double t = p.t[(int64_t)i * p.t_ld + s0 + s];
                 double em, ep;
                 exp_pair(eps * t, p.exp_tab, em, ep);
@@ -624,15 +669,16 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                 const long long smask = (jw & 0x40000000) ? (long long)0x8000000000000000ULL : 0LL;
                 const long long amask = p.abs_weights ? 0x7FFFFFFFFFFFFFFFLL : -1LL;   // |G| for A(s)
 #pragma unroll
-                for (int v = 0; v < CHV / 32; ++v) {
-                    const int xi = i * CHV + v * 32 + lane, xj = j * CHV + v * 32 + lane;
+                for (int v = 0; v < PCH / 32; ++v) {
+                    const int xi = i * PCH + v * 32 + lane, xj = j * PCH + v * 32 + lane;
                     const double a = (sk[xi] >= sk[xj]) ? sp[xi] : sn[xi];   // tau = t_i - t_j >= 0 ?
                     const double g = __longlong_as_double((__double_as_longlong(a * se[xj]) ^ smask) & amask);
                     __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
                 }
             }
         }
-        __syncthreads();   // the next item reuses the shared memory
+        __syncthreads();   // the next pass or item reuses the shared memory
+        }
     }
 }
 
@@ -1160,11 +1206,138 @@ __device__ __forceinline__ bool item_level_bulk(const WalkParams& p, int l, cons
     return true;
 }
 
+// Wide layout with an async-copy ring (CHV = 32*V).  Same items, rows and per-row
+// order as the wide layout.  Instead of holding a few edges' loads in registers, every
+// lane copies its V values of the parent run and of the propagator run of edge
+// e + kAsyncRing into a ring slot in shared memory (cp.async, one commit group per edge)
+// while it consumes edge e from the ring, so kAsyncRing edges stay in flight per warp
+// without registers.  A lane reads back only the values it copied itself (no
+// synchronisation between lanes), and a slot is refilled only after the multiply-add
+// that used its values has issued.
+template <int MODE, int V>
+__device__ __forceinline__ void item_level_async(const WalkParams& p, int l, const TileCtx& tc, int item,
+                                                 unsigned char* smem) {
+    using Tr = Traits<MODE>;
+    using Val = typename Tr::Val;
+    using Prop = typename Tr::Prop;
+    constexpr int CHV = 32 * V;
+    constexpr int R = kAsyncRing;
+    constexpr int VB = V * (int)sizeof(Val);                    // bytes of a lane's parent values
+    constexpr int GB = Tr::kCount ? 0 : V * (int)sizeof(Prop);  // ... and propagator values
+    constexpr int SB = 32 * (VB + GB);                          // one slot of the warp's ring
+    const LevelDesc ld = p.levels[l];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rpw = p.rows_per_warp;
+    const int rows_per_item = kWarps * rpw;
+    const int nrb = (ld.width + rows_per_item - 1) / rows_per_item;
+    const int cl = item / nrb;   // chunk within the item range
+    const int c = tc.c0 + cl;
+    const int rb = item - cl * nrb;
+    const bool sink = (l == p.L - 1);
+    const int off = lane * V;
+    const Val* pc = static_cast<const Val*>(p.slab[(l - 1) & 1]) + (int64_t)c * p.wmax * CHV + off;
+    Val* child = static_cast<Val*>(p.slab[l & 1]);
+    const Prop* gc = Tr::kCount ? nullptr : static_cast<const Prop*>(p.gtab) + (int64_t)c * p.P * CHV + off;
+    const int r0 = rb * rows_per_item + warp * rpw;
+    if (r0 >= ld.width) return;
+    const int nr = min(rpw, ld.width - r0);
+    if constexpr (Tr::kBase == COS_MODE_FP32_MIXED) {
+        if (sink) {
+            for (int r = r0; r < r0 + nr; ++r) {
+                const int node = ld.row_begin + r;
+                sink_row_mixed<V, CHV>(p, pc, gc, __ldg(p.row_ptr + node), __ldg(p.row_ptr + node + 1), c, tc, off);
+            }
+            return;
+        }
+    }
+    // lane j <= nr holds rp_j = row_ptr of row r0 + j
+    const int rp = (lane <= nr) ? __ldg(p.row_ptr + ld.row_begin + r0 + lane) : 0;
+    const int rp_next = __shfl_down_sync(0xffffffffu, rp, 1);
+    const int beg = __shfl_sync(0xffffffffu, rp, 0);
+    const int end = __shfl_sync(0xffffffffu, rp, nr);
+    const unsigned nonempty = __ballot_sync(0xffffffffu, lane < nr && rp_next > rp);
+    const unsigned empty = __ballot_sync(0xffffffffu, lane < nr && rp_next == rp);
+    Val acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+    for (unsigned m = empty; m; m &= m - 1)   // rows without in-edges hold 0
+        store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(m) - 1, tc, off, acc);
+    if (beg == end) return;
+    unsigned char* ring = smem + (size_t)warp * R * SB;
+    unsigned char* mine_p = ring + lane * VB;            // this lane's parent values in slot 0
+    unsigned char* mine_g = ring + 32 * VB + lane * GB;  // ... and its propagator values
+    // metadata windows [wbase, wbase+32) and [wbase+32, wbase+64)
+    int wbase = beg;
+    int2 meta_a = (beg + lane < end) ? __ldg(p.edges + beg + lane) : make_int2(0, 0);
+    int2 meta_b = (beg + 32 + lane < end) ? __ldg(p.edges + beg + 32 + lane) : make_int2(0, 0);
+    auto ends_of = [&](int w0) {   // bit q set <=> edge w0+q is the last in-edge of its row
+        const int pos = rp_next - 1 - w0;
+        return __reduce_or_sync(0xffffffffu,
+                                (lane < nr && rp_next > rp && pos >= 0 && pos < 32) ? (1u << pos) : 0u);
+    };
+    unsigned ends = ends_of(wbase);
+    // copy edge e (within the two windows) into ring slot `slot`; one commit group per call
+    auto issue = [&](int e, int slot) {   // warp-uniform call
+        const int o = e - wbase;
+        const int sa = __shfl_sync(0xffffffffu, meta_a.x, o & 31), sb = __shfl_sync(0xffffffffu, meta_b.x, o & 31);
+        const int src = o < 32 ? sa : sb;
+        cp_async_lane<VB>(mine_p + slot * SB, pc + (int64_t)src * CHV);
+        if constexpr (!Tr::kCount) {
+            const int ga = __shfl_sync(0xffffffffu, meta_a.y, o & 31), gb = __shfl_sync(0xffffffffu, meta_b.y, o & 31);
+            cp_async_lane<GB>(mine_g + slot * SB, gc + (int64_t)(o < 32 ? ga : gb) * CHV);
+        }
+        cp_async_commit();
+    };
+    const int n = end - beg;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (j < n) issue(beg + j, j);
+        else cp_async_commit();   // empty group: every iteration below waits on the same count
+    }
+    unsigned rows_left = nonempty;
+    int slot = 0;
+    for (int k = 0; k < n; ++k) {
+        const int e = beg + k;
+        cp_async_wait<R - 1>();   // this lane's copies of edge k have landed
+        const VecT<Val, V> pv = *reinterpret_cast<const VecT<Val, V>*>(mine_p + slot * SB);
+        if constexpr (Tr::kCount) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += pv.v[v];
+        } else {
+            const VecT<Prop, V> gv = *reinterpret_cast<const VecT<Prop, V>*>(mine_g + slot * SB);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = madd(pv.v[v], gv.v[v], acc[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) order_after(acc[v]);   // the slot's values are used: it may be refilled
+        if ((ends >> (e - wbase)) & 1u) {
+            store_row<MODE, V, CHV>(p, sink, child, c, r0 + __ffs(rows_left) - 1, tc, off, acc);
+            rows_left &= rows_left - 1;
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = (Val)0;
+        }
+        if (e + 1 - wbase == 32) {   // the first window is consumed: slide (edge e + R < wbase + 64 then)
+            wbase += 32;
+            meta_a = meta_b;
+            meta_b = (wbase + 32 + lane < end) ? __ldg(p.edges + wbase + 32 + lane) : make_int2(0, 0);
+            ends = ends_of(wbase);
+        }
+        if (k + R < n) issue(e + R, slot);
+        else cp_async_commit();
+        slot = slot + 1 == R ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();   // nothing in flight into shared memory that the next item reuses
+}
+
 template <int MODE, int V, int LAYOUT, bool BALANCE = false>
 __device__ __forceinline__ bool item_level(const WalkParams& p, int l, const TileCtx& tc, int item,
                                            unsigned char* smem) {
     static_assert(!Traits<MODE>::kAbs || LAYOUT == LAYOUT_WIDE, "sums of |path| values: wide layout only");
     if constexpr (LAYOUT == LAYOUT_BULK) return item_level_bulk<MODE, V>(p, l, tc, item, smem);
+    if constexpr (LAYOUT == LAYOUT_ASYNC) {
+        item_level_async<MODE, V>(p, l, tc, item, smem);
+        return true;
+    }
     if constexpr (LAYOUT == LAYOUT_WIDE) item_level_wide<MODE, V, BALANCE>(p, l, tc, item);
     else item_level_grouped<MODE, V>(p, l, tc, item);
     return true;

@@ -62,13 +62,14 @@ __device__ __noinline__ bool grid_sync(const WalkParams& p, unsigned long long& 
 
 
 // Resident CTAs per SM the register budget is tuned for (no spills at these bounds).
-template <int MODE, int V>
+template <int MODE, int V, int LAYOUT>
 constexpr int min_blocks() {
+    if (LAYOUT == LAYOUT_ASYNC) return 4;   // no loads held in registers: a fourth CTA per SM
     return (Traits<MODE>::kBase == COS_MODE_FP64 && V > 2) ? 2 : 3;
 }
 
 template <int MODE, int V, int LAYOUT>
-__global__ void __launch_bounds__(kThreads, min_blocks<MODE, V>()) walk_kernel(const WalkParams p) {
+__global__ void __launch_bounds__(kThreads, min_blocks<MODE, V, LAYOUT>()) walk_kernel(const WalkParams p) {
     constexpr int CHV = chunk_samples<V, LAYOUT>();
     extern __shared__ __align__(16) double smem[];
     unsigned long long epoch = 0;
@@ -190,6 +191,7 @@ const void* select_kernel(int mode, int vec, int layout) {
             default: return nullptr;
         }
     }
+    if (layout == 4) return select_kernel_layout<LAYOUT_ASYNC>(mode, vec);
     if (layout == 3) return select_kernel_layout<LAYOUT_BULK>(mode, vec);
     if (layout == 2) return select_kernel_layout<LAYOUT_GROUPED>(mode, vec);
     if (layout == 1) return select_kernel_layout<LAYOUT_WIDE>(mode, vec);
@@ -206,6 +208,12 @@ int ring_bytes(int vec) {
 int walk_smem_bytes(int mode, int vec, int layout, int D) {
     mode = base_mode(mode);
     const int props = mode == COS_MODE_COUNT_I64 ? 0 : prop_smem_bytes(D, layout == 2 ? 32 : 32 * vec);
+    if (layout == 4) {
+        const int ring = mode == COS_MODE_FP64 ? (vec == 1 ? async_ring_bytes<COS_MODE_FP64, 1>() : vec == 2 ? async_ring_bytes<COS_MODE_FP64, 2>() : async_ring_bytes<COS_MODE_FP64, 4>())
+                         : mode == COS_MODE_FP32_MIXED ? (vec == 1 ? async_ring_bytes<COS_MODE_FP32_MIXED, 1>() : vec == 2 ? async_ring_bytes<COS_MODE_FP32_MIXED, 2>() : async_ring_bytes<COS_MODE_FP32_MIXED, 4>())
+                         : (vec == 1 ? async_ring_bytes<COS_MODE_COUNT_I64, 1>() : vec == 2 ? async_ring_bytes<COS_MODE_COUNT_I64, 2>() : async_ring_bytes<COS_MODE_COUNT_I64, 4>());
+        return props > ring ? props : ring;
+    }
     if (layout != 3) return props;
     const int ring = mode == COS_MODE_FP64 ? ring_bytes<COS_MODE_FP64>(vec)
                      : mode == COS_MODE_FP32_MIXED ? ring_bytes<COS_MODE_FP32_MIXED>(vec)
@@ -213,9 +221,11 @@ int walk_smem_bytes(int mode, int vec, int layout, int D) {
     return props > ring ? props : ring;
 }
 
-// Opt every kernel instance into its dynamic shared-memory size (once per process).
+// Opt every kernel instance into its dynamic shared-memory size.  Without the opt-in,
+// dynamic and static shared memory together are limited to 48 KB, so a kernel with a
+// few bytes of static shared memory needs it already below 48 KB of dynamic.
 int prepare_kernel_attrs(const void* k, int smem) {
-    if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (smem > 40 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return COS_ERR_CUDA;
     return COS_OK;
 }

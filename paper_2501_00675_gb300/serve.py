@@ -380,7 +380,7 @@ class ResidentScheduler:
     def __init__(self, graphs, mode: int, budget_bytes: int = 150 << 30, max_samples: int = 1_000_000,
                  handles_per_graph: int = 2, tile_samples: int = 8192, workspace_bytes: int = 512 << 20,
                  max_queue: int = 4096, beta: float = 10.0, queue_tasks: int = 1 << 20, max_requests: int = 512,
-                 idle_ms: int = 50, max_inflight: int = 64, max_inflight_work: float = 1e12):
+                 idle_ms: int = 50, max_inflight: int = 64, max_inflight_work: float = 8e12):
         import torch
         from . import binding as cg
         self.torch, self.cg = torch, cg

@@ -55,6 +55,9 @@ def mix():
     (1, {"window_chunks": 2}),
     (0, {"window_chunks": 1, "tile_samples": 2048}),
     (2, {"window_chunks": 3, "samples_per_lane": 1}),
+    (1, {"samples_per_lane": 4, "layout": 4, "rows_per_warp": 31}),
+    (0, {"samples_per_lane": 2, "layout": 4, "window_chunks": 2}),
+    (2, {"samples_per_lane": 2, "layout": 4}),
 ])
 def test_batch_matches_single_graph_bitwise(cg, mix, mode, tuning):
     graphs = _setup(cg, mix)
@@ -105,7 +108,7 @@ def test_batch_autotune_keeps_results(cg, mix):
     outs = _outs(sub, 1)
     b = cg.Batch(graphs, 1, outs)
     best = b.autotune()
-    assert best["samples_per_lane"] in (1, 2, 4) and best["layout"] in (1, 2, 3) and 1 <= best["rows_per_warp"] <= 31
+    assert best["samples_per_lane"] in (1, 2, 4) and best["layout"] in (1, 2, 3, 4) and 1 <= best["rows_per_warp"] <= 31
     b.launch()
     b.results()
     for w, gr, o in zip(sub, graphs, outs):

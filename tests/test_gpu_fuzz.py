@@ -53,8 +53,8 @@ def _case(seed):
 
 def _shape(rng):
     shape = {"schedule": int(rng.integers(1, 3)), "samples_per_lane": int(rng.choice([1, 2, 4])),
-             "rows_per_warp": int(rng.integers(1, 32)), "layout": int(rng.choice([1, 1, 2, 3])),
-             "prefetch": int(rng.integers(1, 4))}
+             "rows_per_warp": int(rng.integers(1, 32)), "layout": int(rng.choice([1, 1, 2, 3, 4])),
+             "prefetch": int(rng.integers(1, 6))}
     if rng.random() < 0.5:
         shape["window_chunks"] = int(rng.integers(1, 6))
     if rng.random() < 0.5:

@@ -316,7 +316,12 @@ def test_results_independent_of_launch_shape(cg):
                    {"schedule": 2, "window_chunks": 3, "samples_per_lane": 2, "tile_samples": 1000},
                    {"schedule": 2, "window_chunks": 5, "samples_per_lane": 4, "layout": 2, "rows_per_warp": 6},
                    {"schedule": 2, "samples_per_lane": 4, "layout": 3, "window_chunks": 2},
-                   {"prefetch": 3}, {"prefetch": 3, "schedule": 2, "samples_per_lane": 1}, {"prefetch": 1}):
+                   {"prefetch": 3}, {"prefetch": 3, "schedule": 2, "samples_per_lane": 1}, {"prefetch": 1},
+                   {"samples_per_lane": 4, "layout": 4, "rows_per_warp": 16},
+                   {"samples_per_lane": 2, "layout": 4, "rows_per_warp": 7, "tile_samples": 900},
+                   {"samples_per_lane": 1, "layout": 4, "rows_per_warp": 31},
+                   {"schedule": 2, "samples_per_lane": 4, "layout": 4, "window_chunks": 3},
+                   {"prefetch": 5}, {"prefetch": 4, "schedule": 2, "samples_per_lane": 2}):
         for mode in (0, 1):
             Rg, mg = run_gpu(cg, w.graph, w.samples.eps, w.samples.beta, w.samples.t, mode, tuning)
             if ref is None:
