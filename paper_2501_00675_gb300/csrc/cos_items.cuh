@@ -775,7 +775,7 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
     using Val = typename Tr::Val;
     using Prop = typename Tr::Prop;
     constexpr int CHV = 32 * V;
-    constexpr int U = 4;
+    constexpr int U = Tr::kAbs ? 2 : 4;   // edges in flight per warp (the walk with A holds three runs per edge)
     const LevelDesc ld = p.levels[l];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rpw = p.rows_per_warp;
