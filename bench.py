@@ -346,7 +346,7 @@ def run_ours(args, rank, world, local):
     hbm = {"bound": "hbm", "achieved": alg_bytes / walk_s / 1e9, "peak": peak, "unit": "GB/s",
            "frac": alg_bytes / walk_s / 1e9 / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
            if peak_kind == "measured" else "fallback 6.8 TB/s",
-           "traffic": profiled_traffic(f"walk_{mode_name}_{args.workload}"),
+           "traffic": profiled_traffic(f"walk_{mode_name}{'_abs' if args.abs else ''}_{args.workload}"),
            "algorithmic_bytes_per_launch": alg_bytes}
     if mode == 0:
         tflops = 2.0 * E * S / walk_s / 1e12
