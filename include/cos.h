@@ -257,7 +257,8 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *   samples_per_lane  1, 2 or 4 consecutive samples per thread (vector width)
  *   tile_samples      samples per tile (rounded up to 32 * samples_per_lane)
  *   rows_per_warp     consecutive destination rows one warp takes per work item (<= 31);
- *                     automatic: 31 with the work queue, else 4 (FP64) or 16
+ *                     automatic: 31 with the work queue, else 4 (FP64), 8 (FP32
+ *                     mixed) or 16 (count)
  *   blocks_per_sm     persistent CTAs per SM (capped by occupancy)
  *   timeout_ms        limit of every bounded wait in the kernels (grid barrier,
  *                     work-queue dependency, bulk-copy barrier); default 10 s

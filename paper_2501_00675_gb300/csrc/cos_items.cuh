@@ -284,14 +284,15 @@ struct Traits<kModeMixedAbs> : Traits<COS_MODE_FP32_MIXED> {
     static constexpr bool kAbs = true;
 };
 
-// |x| as a float, rounded toward zero, by integer operations only (no instruction of
-// GB300's slow FP64 pipe); 0 below the float normal range, the largest float above it.
+// |x| as a float, rounded toward zero, by 32-bit integer operations on the two halves
+// of x only (no instruction of GB300's slow FP64 pipe); 0 below the float normal
+// range, the largest float above it.
 __device__ __forceinline__ float abs_to_float(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-    const unsigned e = (unsigned)(b >> 52);
-    if (e < 1023u - 126u) return 0.0f;
-    if (e > 1023u + 127u) return __uint_as_float(0x7f7fffffu);
-    return __uint_as_float(((e - 1023u + 127u) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu, lo = (unsigned)__double2loint(x);
+    const unsigned e = hi >> 20;
+    const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 of the 52 fraction bits
+    const unsigned f = ((e - 1023u + 127u) << 23) | mant;
+    return __uint_as_float(e < 1023u - 126u ? 0u : e > 1023u + 127u ? 0x7f7fffffu : f);
 }
 __device__ __forceinline__ float abs_to_float(float x) { return __uint_as_float(__float_as_uint(x) & 0x7fffffffu); }
 
