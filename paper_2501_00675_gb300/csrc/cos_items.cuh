@@ -416,27 +416,26 @@ __device__ __forceinline__ void exp_pair(double x, const double* __restrict__ ta
 
 // ---------------------------------------------------------------- float-float helpers
 
-// Leading 24 significant bits of a double as a float, by truncation with integer
-// operations only (no FP64 conversion); |x| below 2^-126 gives a signed zero.  The
-// callers keep |x| below 2^127.
+// Leading 24 significant bits of a double as a float, by truncation with 32-bit
+// integer operations on the double's two halves only (no FP64 conversion; 64-bit
+// integer operations occupy GB300's FP64 pipe); |x| below 2^-126 gives a signed zero.
+// The callers keep |x| below 2^127.
 __device__ __forceinline__ float trunc_to_float(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-    if (e < 1023u - 126u) return __uint_as_float((unsigned)(b >> 32) & 0x80000000u);
-    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    const unsigned mant = (unsigned)(b >> 29) & 0x7fffffu;
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    const unsigned sign = hi & 0x80000000u;
+    if (e < 1023u - 126u) return __uint_as_float(sign);
+    const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
     return __uint_as_float(sign | ((e - 1023u + 127u) << 23) | mant);
 }
 
-// The float value f as a double, exactly, with integer operations only (normal f or 0).
+// The float value f as a double, exactly, with 32-bit integer operations only (normal f or 0).
 __device__ __forceinline__ double float_to_double_exact(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu;
     if (e == 0) return 0.0;
-    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e - 127u + 1023u) << 52) |
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)b);
+    const unsigned hi = (u & 0x80000000u) | ((e - 127u + 1023u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)((u & 0x7u) << 29));
 }
 
 // x = hi + lo with hi, lo floats (about 48 significant bits), one DADD.
@@ -512,10 +511,31 @@ __device__ __forceinline__ int prop_items(const WalkParams& p, const TileCtx& tc
 
 // Integer key of a time whose signed 64-bit order is the order of the doubles
 // (non-NaN; -0 taken as +0), so that the branch test t_i >= t_j of every slot and
-// sample runs on the integer pipes instead of GB300's slow FP64 pipe.
+// sample runs on the integer pipes instead of GB300's slow FP64 pipe.  Built and
+// compared with 32-bit operations on the two halves only: 64-bit integer operations
+// occupy the FP64 pipe too.
 __device__ __forceinline__ long long time_order_key(double t) {
-    const long long b = __double_as_longlong(t + 0.0);   // -0 + 0 = +0
-    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+    int hi = __double2hiint(t), lo = __double2loint(t);
+    if (hi == (int)0x80000000 && lo == 0) hi = 0;   // -0 as +0
+    if (hi < 0) {                                    // negative: reverse the magnitude order
+        hi ^= 0x7fffffff;
+        lo = ~lo;
+    }
+    return __double_as_longlong(__hiloint2double(hi, lo));
+}
+
+// a >= b for two time keys, as signed 64-bit integers (high words signed, then low
+// words unsigned), by 32-bit operations.
+__device__ __forceinline__ bool key_ge(long long a, long long b) {
+    const double da = __longlong_as_double(a), db = __longlong_as_double(b);
+    const int ah = __double2hiint(da), bh = __double2hiint(db);
+    return ah > bh || (ah == bh && (unsigned)__double2loint(da) >= (unsigned)__double2loint(db));
+}
+
+// x with its sign bit flipped by shi (0 or 0x80000000) and then masked by ahi (-1, or
+// 0x7fffffff for |x|), on the high word only.
+__device__ __forceinline__ double sign_ops(double x, int shi, int ahi) {
+    return __hiloint2double((__double2hiint(x) ^ shi) & ahi, __double2loint(x));
 }
 
 // Samples of a chunk that one pass of a propagator item keeps in shared memory.
@@ -574,8 +594,8 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
             for (int q = q0 + warp; q < q1; q += kWarps) {
                 const int i = __ldg(p.slot_kij + 3 * q + 1), jw = __ldg(p.slot_kij + 3 * q + 2);
                 const int j = jw & 0x3fffffff;
-                const long long smask = (jw & 0x40000000) ? (long long)0x8000000000000000ULL : 0LL;
-                const long long amask = p.abs_weights ? 0x7FFFFFFFFFFFFFFFLL : -1LL;
+                const int shi = (jw & 0x40000000) ? (int)0x80000000 : 0;   // closes a fermion loop
+                const int ahi = p.abs_weights ? 0x7fffffff : -1;            // |G| for A(s)
 #pragma unroll
                 for (int v = 0; v < PCH / 32; ++v) {
                     const double tau = st[i * PCH + v * 32 + lane] - st[j * PCH + v * 32 + lane];
@@ -593,8 +613,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                         f = 1.0;
                     }
                     const double2 as = __ldg(tk + (pos ? 0 : T) + m);
-                    const double g =
-                        __longlong_as_double((__double_as_longlong(__dadd_rn(as.x, __dmul_rn(f, as.y))) ^ smask) & amask);
+                    const double g = sign_ops(__dadd_rn(as.x, __dmul_rn(f, as.y)), shi, ahi);
                     __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
                 }
             }
@@ -640,7 +659,7 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
 #pragma unroll
                     for (int v = 0; v < PCH / 32; ++v) {
                         const int xi = i * PCH + v * 32 + lane, xj = j * PCH + v * 32 + lane;
-                        const float2 a = (sk[xi] >= sk[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
+                        const float2 a = key_ge(sk[xi], sk[xj]) ? fp_[xi] : fn_[xi];   // tau = t_i - t_j >= 0 ?
                         __stcg(reinterpret_cast<float*>(gt) + (int64_t)q * CHV + v * 32 + lane,
                                __uint_as_float((__float_as_uint(mul_ff(a, fe_[xj])) ^ smask) & amask));
                     }
@@ -667,13 +686,13 @@ __device__ __forceinline__ void item_props(const WalkParams& p, const TileCtx& t
                 const int i = __ldg(p.slot_kij + 3 * q + 1), jw = __ldg(p.slot_kij + 3 * q + 2);
                 const int j = jw & 0x3fffffff;
                 // closes a fermion loop: flip the sign bit (no extra FP64 operation)
-                const long long smask = (jw & 0x40000000) ? (long long)0x8000000000000000ULL : 0LL;
-                const long long amask = p.abs_weights ? 0x7FFFFFFFFFFFFFFFLL : -1LL;   // |G| for A(s)
+                const int shi = (jw & 0x40000000) ? (int)0x80000000 : 0;
+                const int ahi = p.abs_weights ? 0x7fffffff : -1;   // |G| for A(s)
 #pragma unroll
                 for (int v = 0; v < PCH / 32; ++v) {
                     const int xi = i * PCH + v * 32 + lane, xj = j * PCH + v * 32 + lane;
-                    const double a = (sk[xi] >= sk[xj]) ? sp[xi] : sn[xi];   // tau = t_i - t_j >= 0 ?
-                    const double g = __longlong_as_double((__double_as_longlong(a * se[xj]) ^ smask) & amask);
+                    const double a = key_ge(sk[xi], sk[xj]) ? sp[xi] : sn[xi];   // tau = t_i - t_j >= 0 ?
+                    const double g = sign_ops(a * se[xj], shi, ahi);
                     __stcg(gt + (int64_t)q * CHV + v * 32 + lane, (Prop)g);
                 }
             }
