@@ -87,7 +87,7 @@ def parse_args(argv=None):
                     help="the same walk also sums |path| values (COS_EVAL_ABS; fp64 and mixed modes)")
     ap.add_argument("--samples", type=int, default=None, help="samples per GPU (default: the workload's)")
     ap.add_argument("--tuning", type=str, default="", help="JSON dict passed to cos_set_tuning")
-    ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
@@ -248,10 +248,12 @@ def profiled_traffic(kernel_tag: str):
 # ------------------------------------------------------------------ CPU oracle timing
 
 def oracle_rate(graph, samples, seconds: float, nthreads: int = 0):
-    """Edge.sample updates/s of the CPU oracle on a bounded prefix of the samples."""
+    """Edge.sample updates/s of the CPU oracle on a bounded prefix of the samples, sized
+    from a short timed run after a warm-up (thread pool start, first touch)."""
     import oracle
     oracle.build()
-    n = 16
+    n = 32
+    oracle.evaluate(graph, samples.eps, samples.beta, samples.t[:n], with_abs=False, nthreads=nthreads)
     t0 = time.perf_counter()
     oracle.evaluate(graph, samples.eps, samples.beta, samples.t[:n], with_abs=False, nthreads=nthreads)
     dt = time.perf_counter() - t0
