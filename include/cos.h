@@ -297,6 +297,8 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *                     4 and 5: as 2 and 3, but every lane of a warp issues one bulk
  *                     L2 prefetch (cp.async.bulk.prefetch) of a whole parent run, for
  *                     the 32 edges of the next metadata window (and of the first).
+ *                     6 and 7: as 2 and 3, prefetching the batch of 4 edges after the
+ *                     next.
  */
 typedef struct cos_tuning {
     int32_t samples_per_lane;

@@ -561,7 +561,7 @@ int cos_batch_set_tuning(cos_batch_t b, const cos_tuning* t) {
     if (t->rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
     if (t->layout < 0 || t->layout > 4) return set_error(COS_ERR_INVALID, "layout must be 0, 1, 2, 3 or 4");
     if (t->window_chunks < 0) return set_error(COS_ERR_INVALID, "window_chunks must be >= 0");
-    if (t->prefetch < 0 || t->prefetch > 5) return set_error(COS_ERR_INVALID, "prefetch must be 0..5");
+    if (t->prefetch < 0 || t->prefetch > 7) return set_error(COS_ERR_INVALID, "prefetch must be 0..7");
     b->tuning = *t;
     b->planned = false;
     return COS_OK;

@@ -512,8 +512,9 @@ int cos_set_tuning(cos_graph_t g, const cos_tuning* t) {
     if (t->schedule < 0 || t->schedule > 2)
         return fail(COS_ERR_INVALID, "schedule must be 0 (auto), 1 (level-synchronous) or 2 (windowed)");
     if (t->window_chunks < 0) return fail(COS_ERR_INVALID, "window_chunks must be >= 0");
-    if (t->prefetch < 0 || t->prefetch > 5)
-        return fail(COS_ERR_INVALID, "prefetch must be 0 (auto), 1 (off), 2/4 (large parent slices) or 3/5 (always)");
+    if (t->prefetch < 0 || t->prefetch > 7)
+        return fail(COS_ERR_INVALID,
+                    "prefetch must be 0 (auto), 1 (off), 2/4/6 (large parent slices) or 3/5/7 (always)");
     g->tuning = *t;
     g->generation++;
     return COS_OK;
@@ -1051,8 +1052,10 @@ int prepare_walk(cos_graph_t g, int mode, const cos_tuning* force, void* per_sam
     p.tile = tile;
     p.rows_per_warp = tn.rows_per_warp;
     p.wmax = (int32_t)g->Wmax;
-    p.pf_slice_bytes = tn.prefetch == 1 ? INT64_MAX : (tn.prefetch == 3 || tn.prefetch == 5) ? 0 : ((int64_t)32 << 20);
-    p.pf_bulk = tn.prefetch >= 4 ? 1 : 0;
+    p.pf_slice_bytes = tn.prefetch == 1 ? INT64_MAX
+                       : (tn.prefetch == 3 || tn.prefetch == 5 || tn.prefetch == 7) ? 0 : ((int64_t)32 << 20);
+    p.pf_bulk = (tn.prefetch == 4 || tn.prefetch == 5) ? 1 : 0;
+    p.pf_ahead = tn.prefetch >= 6 ? 2 : 1;
     p.ptab = g->d_ptab;
     p.ptab_T = g->ptab_T;
     p.ptab_tau_max = g->ptab_tau_max;

@@ -96,7 +96,7 @@ struct WalkParams {
     int32_t abs_weights;         // 1: every factor replaced by its absolute value (A(s) = sum of |path|)
     int64_t pf_slice_bytes;      // wide layout: L2-prefetch parents on levels whose parent slice per chunk exceeds this
     int32_t pf_bulk;             // 1: that prefetch is one bulk copy per edge run, a window of 32 edges ahead
-    int32_t pad_;
+    int32_t pf_ahead;            // line prefetch: how many batches of edges ahead (1 or 2)
 };
 
 constexpr int kThreads = 256;           // 8 warps per CTA

@@ -871,11 +871,12 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
             const unsigned ends = __reduce_or_sync(
                 0xffffffffu, (lane < nr && rp_next > rp && pos >= 0 && pos < 32) ? (1u << pos) : 0u);
             for (int q0 = 0; q0 < n; q0 += U) {
-                if (pf) {   // L2 prefetch of the next U edges' parent runs, one lane per 128-byte line
+                if (pf) {   // L2 prefetch of a later batch's U parent runs, one lane per 128-byte line
                     constexpr int LPL = (128 / (int)(sizeof(Val) * V)) - 1;
+                    const int ahead = U * p.pf_ahead;
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const int qn = q0 + U + u;
+                        const int qn = q0 + ahead + u;
                         const int sn = __shfl_sync(0xffffffffu, meta.x, qn & 31);
                         if (qn < n && (lane & LPL) == 0) {
                             asm volatile("prefetch.global.L2 [%0];" ::"l"(pc + (int64_t)sn * CHV));

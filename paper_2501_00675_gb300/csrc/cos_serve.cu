@@ -716,8 +716,8 @@ int cos_server_create(int32_t mode, int32_t max_times, const cos_tuning* tuning,
         return set_error(COS_ERR_INVALID, "samples_per_lane must be 1, 2 or 4");
     if (t.layout > 1) return set_error(COS_ERR_INVALID, "the resident server runs the wide layout (layout 0 or 1)");
     if (t.rows_per_warp > 31) return set_error(COS_ERR_INVALID, "rows_per_warp must be <= 31");
-    if (t.window_chunks < 0 || t.prefetch < 0 || t.prefetch > 5)
-        return set_error(COS_ERR_INVALID, "window_chunks must be >= 0 and prefetch 0..5");
+    if (t.window_chunks < 0 || t.prefetch < 0 || t.prefetch > 7)
+        return set_error(COS_ERR_INVALID, "window_chunks must be >= 0 and prefetch 0..7");
     int device = -1;
     const cudaError_t de = cudaGetDevice(&device);
     if (de != cudaSuccess) return set_error(COS_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(de));

@@ -138,7 +138,7 @@ def test_server_arguments_checked_before_any_cuda_call(lib):
     assert create(0, 4, None, 0, -5, 0, ctypes.byref(h)) == binding.COS_ERR_INVALID         # queue_tasks
     assert create(0, 4, None, 0, 0, -1, ctypes.byref(h)) == binding.COS_ERR_INVALID         # idle_ms
     assert create(0, 4, None, 0, 0, 0, None) == binding.COS_ERR_INVALID
-    for field, value in (("samples_per_lane", 3), ("layout", 2), ("rows_per_warp", 32), ("prefetch", 6),
+    for field, value in (("samples_per_lane", 3), ("layout", 2), ("rows_per_warp", 32), ("prefetch", 8),
                          ("window_chunks", -1)):
         t = binding.CosTuning()
         setattr(t, field, value)

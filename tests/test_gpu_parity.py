@@ -683,3 +683,31 @@ def test_evaluate_batch_with_a_mode_per_graph(cg):
         cg.evaluate_batch(graphs[:1], [7])
     for gr in graphs:
         gr.close()
+
+
+def test_fused_sum_of_abs_paths_with_tabulated_propagators(cg):
+    """COS_EVAL_ABS with user-tabulated propagators and fermion-loop signs: R(s) bitwise
+    the walk without the flag, A(s) (float products) within 1e-5 of the oracle's A plus
+    the tables' grid-position rounding bound."""
+    rng = np.random.default_rng(43)
+    w = medium(num_samples=1500)
+    g = w.graph
+    from workloads import Graph
+    e = g.edges.copy()
+    e[rng.random(len(e)) < 0.3, 2] |= oracle.SIGN_BIT
+    g = Graph(g.widths, g.edge_counts, e, g.num_kinds, g.num_times)
+    tables = _tables(rng, g.num_kinds, 33)
+    R, A, B = oracle.evaluate_tabulated(g, tables, 9.5, w.samples.t, with_bound=True)
+    gr = cg.Graph.from_workload_graph(g)
+    gr.set_propagator_table(tables, 9.5)
+    gr.set_samples(torch.from_numpy(w.samples.t).cuda(), w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+    for mode in (0, 1):
+        both = torch.empty(3000, dtype=torch.float64, device="cuda")
+        mr, ma = gr.evaluate(mode | cg.COS_EVAL_ABS, out=both)
+        plain = torch.empty(1500, dtype=torch.float64, device="cuda")
+        gr.evaluate(mode, out=plain)
+        r, a = both[:1500].cpu().numpy(), both[1500:].cpu().numpy()
+        np.testing.assert_array_equal(r, plain.cpu().numpy())
+        check_fp(r, mr, R, A, mode, extra=B)
+        assert np.all(np.abs(a - A) <= 1e-5 * A + B)
+    gr.close()

@@ -98,6 +98,15 @@ def test_static_rejects_graphs_beyond_the_scratch_limit(cg):
     gr.close()
 
 
+def test_static_rejects_the_sum_of_abs_paths_flag(cg):
+    # the entry evaluates R only; COS_EVAL_ABS (a second output) is refused before any launch
+    wl = tiny(num_samples=64)
+    gr = cg.Graph.from_workload_graph(wl.graph)
+    rc, _, _ = _static(cg, gr, 0 | cg.COS_EVAL_ABS, wl.samples.t, wl.samples.eps, wl.samples.beta)
+    assert rc == cg.COS_ERR_INVALID
+    gr.close()
+
+
 def test_static_uses_the_handles_propagator_tables(cg):
     # tables set on the handle (cos_set_propagator_table) apply to the static entry too
     wl = tiny(num_samples=600)
