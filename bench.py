@@ -87,6 +87,8 @@ def parse_args(argv=None):
                     help="the same walk also sums |path| values (COS_EVAL_ABS; fp64 and mixed modes)")
     ap.add_argument("--samples", type=int, default=None, help="samples per GPU (default: the workload's)")
     ap.add_argument("--tuning", type=str, default="", help="JSON dict passed to cos_set_tuning")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the launch shape with cos_autotune on the workload before timing")
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -303,6 +305,9 @@ def run_ours(args, rank, world, local):
         gr.set_samples(t_dev, s.eps, s.beta, cg.COS_T_SAMPLE_MAJOR, stream=stream)
         gr.evaluate(emode, out=out, want_mean=False, stream=stream, allow_overflow=True)
 
+    if args.autotune:
+        step()
+        gr.autotune(emode, out=out, stream=stream)   # times candidate shapes on these samples, keeps the fastest
     for _ in range(args.warmup):
         step()
     gr.get_result(stream)
