@@ -53,6 +53,10 @@ struct BatchArgs {
 template <int MODE, int V, int LAYOUT>
 constexpr int batch_min_blocks() {
     if (LAYOUT == LAYOUT_ASYNC) return 4;   // no loads held in registers: a fourth CTA per SM
+    // FP32 walk from the work queue: a fourth CTA per SM (64 registers) measured faster on
+    // the large graph (3.74 -> 3.49 s) and the batched launch (3.02 -> 2.87 s); the
+    // level-synchronous kernel keeps three (medium 2.47 -> 2.72 ms with four)
+    if (MODE == COS_MODE_FP32_MIXED && LAYOUT == LAYOUT_WIDE) return 4;
     return (Traits<MODE>::kBase == COS_MODE_FP64 && V > 2) ? 2 : 3;
 }
 
@@ -180,6 +184,19 @@ const void* select_batch_kernel(int mode, int vec, int layout) {
 }  // namespace cosgpu
 
 using namespace cosgpu;
+
+// Co-resident CTAs of the work-queue kernel for (mode, vec, layout) with D time variables
+// over the whole device; 0 on failure.
+int cosgpu::batch_coresident_blocks(int mode, int vec, int layout, int D, int device) {
+    const void* k = select_batch_kernel(mode, vec, layout);
+    if (!k) return 0;
+    const int smem = walk_smem_bytes(mode, vec, layout, D);
+    if (prepare_kernel_attrs(k, smem) != COS_OK) return 0;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    return per_sm * sms;
+}
 
 struct cos_batch {
     int device = 0;

@@ -543,7 +543,9 @@ static int resolve_tuning(cos_graph_t g, int kmode, cos_tuning* out, int64_t* ti
     while (t.samples_per_lane > 1 && (t.layout == 1 || t.layout == 4) &&
            walk_smem_bytes(kmode, t.samples_per_lane, t.layout, g->D) > (160 << 10))
         t.samples_per_lane /= 2;
-    int dev_max = max_coresident_blocks(kmode, t.samples_per_lane, t.layout, g->D, g->device);
+    // occupancy of the kernel this schedule runs (the work queue's may differ)
+    int dev_max = t.schedule == 2 ? batch_coresident_blocks(kmode, t.samples_per_lane, t.layout, g->D, g->device)
+                                  : max_coresident_blocks(kmode, t.samples_per_lane, t.layout, g->D, g->device);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     if (dev_max <= 0 || sms <= 0) return fail(COS_ERR_CUDA, "cannot query occupancy of the walker kernel");

@@ -158,6 +158,8 @@ int launch_walk(int mode, int vec, int layout, const WalkParams& p, int grid, cu
                 size_t msglen);
 // Co-resident persistent grid size for (mode, vec, layout) with D time variables; 0 on failure.
 int max_coresident_blocks(int mode, int vec, int layout, int D, int device);
+// The same for the work-queue kernel (cos_batch.cu), whose register budget can differ.
+int batch_coresident_blocks(int mode, int vec, int layout, int D, int device);
 // Dynamic shared memory of a launch (the propagator phase keeps 32 samples x D times
 // in shared memory), and the once-per-kernel opt-in to sizes above 48 KB.
 int walk_smem_bytes(int mode, int vec, int layout, int D);
