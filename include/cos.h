@@ -510,7 +510,10 @@ int cos_probe_fma_rate(int32_t precision, double* fma_per_second);
  *   cos_server_submit  evaluate handle g over num_samples samples numbered
  *                      first_sample.. of generator key `seed`; per-sample values go
  *                      to per_sample_out (device, max(num_samples,1) doubles, or
- *                      int64 in count mode; required).  g must have had a sample
+ *                      int64 in count mode; required).  The running kernel may write
+ *                      them as soon as the request is submitted, unordered with the
+ *                      caller's streams: work on other streams that uses that buffer
+ *                      must be complete before submit.  g must have had a sample
  *                      set of at least num_samples attached in its own buffer
  *                      (cos_set_samples_uniform, or cos_set_samples without
  *                      COS_T_BORROW) so that eps, beta and the buffers exist; the

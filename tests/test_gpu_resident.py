@@ -77,6 +77,7 @@ def test_requests_match_oracle(cg, mode):
             S = 0 if (wi, q) == (0, 2) else int(rng.integers(1, cap))
             seed, first = int(rng.integers(1, 2 ** 40)), int(rng.integers(0, 2 ** 34))
             out = torch.full((max(S, 1),), -9, dtype=dt, device="cuda")
+            torch.cuda.synchronize()   # the fill, on torch's stream, must not land after the server's writes
             rid = srv.submit(h, S, seed, out, first)
             assert rid is not None
             reqs.append((wi, h, S, seed, first, out, rid))
