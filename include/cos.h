@@ -257,7 +257,8 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *   samples_per_lane  1, 2 or 4 consecutive samples per thread (vector width)
  *   tile_samples      samples per tile (rounded up to 32 * samples_per_lane)
  *   rows_per_warp     consecutive destination rows one warp takes per work item (<= 31);
- *                     automatic: 31 with the work queue, else 4 (FP64), 8 (FP32
+ *                     automatic: 31 with the work queue (16 in FP32 mixed mode when
+ *                     every level has fewer than 65536 nodes), else 4 (FP64), 8 (FP32
  *                     mixed) or 16 (count)
  *   blocks_per_sm     persistent CTAs per SM (capped by occupancy)
  *   timeout_ms        limit of every bounded wait in the kernels (grid barrier,
@@ -282,8 +283,9 @@ int cos_graph_info(cos_graph_t g, int64_t* info, int32_t n);
  *                     1..L-1, continuing into the same window of the next tile) and
  *                     the chains are issued in wavefront order, so about L windows
  *                     are in flight.  Results are bitwise the same either way.
- *                     Automatic: 2 in FP64 mode with at least 1e9 edge x samples
- *                     or when the widest level has at least 65536 nodes, else 1.
+ *                     Automatic: 2 in FP64 and FP32 mixed modes with at least 1e9
+ *                     edge x samples or when the widest level has at least 65536
+ *                     nodes, else 1.
  *                     Batched launches always use the
  *                     work queue, with windows when window_chunks > 0.
  *   window_chunks     chunks (of 32*samples_per_lane samples, 32 in the grouped

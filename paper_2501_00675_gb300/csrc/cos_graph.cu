@@ -528,12 +528,19 @@ static int resolve_tuning(cos_graph_t g, int kmode, cos_tuning* out, int64_t* ti
     // is ahead on large FP64 walks and on graphs with very wide levels; the cooperative
     // kernel on the FP32 and count walks of smaller graphs and on small evaluations,
     // where the work queue's per-call planning and upload are not amortised.
+    // (with the FP32 work-queue walker at four CTAs per SM the FP32 walk of medium graphs
+    // joined the FP64 one there: medium mixed 2.44 -> 2.36 ms)
+    const bool big = (double)g->E * (double)g->S >= 1e9;
     if (t.schedule <= 0)
-        t.schedule = ((mode == COS_MODE_FP64 && (double)g->E * (double)g->S >= 1e9) || g->Wmax >= 65536) ? 2 : 1;
+        t.schedule = ((big && (mode == COS_MODE_FP64 || mode == COS_MODE_FP32_MIXED)) || g->Wmax >= 65536) ? 2 : 1;
     // level-synchronous: 8 rows per warp measured best for the FP32 walk (medium: 2.46 ms
     // against 2.50 with 16 and 2.88 with 31)
-    if (t.rows_per_warp <= 0)
-        t.rows_per_warp = t.schedule == 2 ? 31 : (mode == COS_MODE_FP64 ? 4 : mode == COS_MODE_FP32_MIXED ? 8 : 16);
+    if (t.rows_per_warp <= 0) {
+        if (t.schedule == 2)   // FP32 below 65,536 nodes per level: 16 (medium 2.36 ms against 2.50 with 31)
+            t.rows_per_warp = (mode == COS_MODE_FP32_MIXED && g->Wmax < 65536) ? 16 : 31;
+        else
+            t.rows_per_warp = mode == COS_MODE_FP64 ? 4 : mode == COS_MODE_FP32_MIXED ? 8 : 16;
+    }
     if (t.layout <= 0 || mode_has_abs(kmode)) t.layout = 1;   // sums of |path| values: wide layout only
     if (t.timeout_ms <= 0) {
         const char* env = getenv("COS_TIMEOUT_MS");
