@@ -108,3 +108,17 @@ def test_reference_arm_on_other_ranks_does_no_work():
     line = bench.run_reference(args, rank=0, world=1)
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_profiled_traffic_scales_with_samples_and_checks_the_schedule():
+    """The committed ncu figure is per launch at the profiled sample count; other sample
+    counts scale it, and a launch on another schedule gets no figure."""
+    import json
+    with open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")) as f:
+        d = json.load(f)
+    for tag, v in d.items():
+        full = bench.profiled_traffic(tag, v["samples"], v["schedule"])
+        assert full == v["bytes_per_launch"]
+        assert bench.profiled_traffic(tag, v["samples"] // 4, v["schedule"]) == full / 4
+        assert bench.profiled_traffic(tag, v["samples"], 3 - v["schedule"]) is None
+    assert bench.profiled_traffic("walk_count_nothing", 1, 1) is None
