@@ -235,17 +235,17 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(kernel_tag: str, samples: int, schedule: int):
-    """DRAM bytes per launch from the committed ncu summary, if it covers this kernel build
-    and schedule.  The walk's traffic grows in proportion to the samples (per-sample slabs,
-    per-chunk items), so the profiled figure is scaled to this launch's sample count."""
+def profiled_traffic(kernel_tag: str, samples: int, schedule: int, layout: int):
+    """DRAM bytes per launch from the committed ncu summary, if it covers this kernel build,
+    schedule and layout.  The walk's traffic grows in proportion to the samples (per-sample
+    slabs, per-chunk items), so the profiled figure is scaled to this launch's sample count."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             v = json.load(f).get(kernel_tag)
     except (OSError, ValueError):
         return None
-    if not isinstance(v, dict) or v.get("schedule") != schedule:
+    if not isinstance(v, dict) or v.get("schedule") != schedule or v.get("layout") != layout:
         return None
     return v["bytes_per_launch"] * samples / v["samples"]
 
@@ -357,7 +357,7 @@ def run_ours(args, rank, world, local):
            "frac": alg_bytes / walk_s / 1e9 / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
            if peak_kind == "measured" else "fallback 6.8 TB/s",
            "traffic": profiled_traffic(f"walk_{mode_name}{'_abs' if args.abs else ''}_{args.workload}",
-                                       S, tuning["schedule"]),
+                                       S, tuning["schedule"], tuning["layout"]),
            "algorithmic_bytes_per_launch": alg_bytes}
     if mode == 0:
         tflops = 2.0 * E * S / walk_s / 1e12

@@ -117,8 +117,9 @@ def test_profiled_traffic_scales_with_samples_and_checks_the_schedule():
     with open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")) as f:
         d = json.load(f)
     for tag, v in d.items():
-        full = bench.profiled_traffic(tag, v["samples"], v["schedule"])
+        full = bench.profiled_traffic(tag, v["samples"], v["schedule"], v["layout"])
         assert full == v["bytes_per_launch"]
-        assert bench.profiled_traffic(tag, v["samples"] // 4, v["schedule"]) == full / 4
-        assert bench.profiled_traffic(tag, v["samples"], 3 - v["schedule"]) is None
-    assert bench.profiled_traffic("walk_count_nothing", 1, 1) is None
+        assert bench.profiled_traffic(tag, v["samples"] // 4, v["schedule"], v["layout"]) == full / 4
+        assert bench.profiled_traffic(tag, v["samples"], 3 - v["schedule"], v["layout"]) is None
+        assert bench.profiled_traffic(tag, v["samples"], v["schedule"], v["layout"] + 1) is None
+    assert bench.profiled_traffic("walk_count_nothing", 1, 1, 1) is None
