@@ -59,6 +59,7 @@ E2E_LONG_STEPS = 5
 ORACLE_FULL_MAX = 1 << 17
 ORACLE_SLICE = 1024
 ORACLE_TIGHT = 64
+BATCH_CHECK_SAMPLES = 32          # batched workload: samples of every graph compared with the oracle
 
 
 def parse_args(argv=None):
@@ -513,6 +514,9 @@ def run_batched(args, rank, world, local):
     barrier(world)
     step_ms = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, local) * 1e3 / max(args.steps, 1)
     b.results(stream)
+    # the timed launch's first samples of every graph, kept for the oracle check below
+    n_chk = BATCH_CHECK_SAMPLES
+    got = [o[:min(n_chk, w.samples.num_samples)].cpu().numpy() for o, w in zip(outs, wls)]
     # the same graphs one after another through cos_evaluate, same launch shape
     seq = []
     for g in graphs:
@@ -531,6 +535,29 @@ def run_batched(args, rank, world, local):
         g.close()
     if rank != 0:
         return None
+    err = None
+    if not args.no_oracle_check:
+        # every graph's first samples of the timed launch against the FP64 oracle
+        import oracle
+        t0 = time.perf_counter()
+        worst, ok, n_tot = 0.0, True, 0
+        for w, r in zip(wls, got):
+            n = r.size
+            n_tot += n
+            if mode == 2:
+                cnt, _ = oracle.count_paths(w.graph)
+                ok = ok and bool(np.all(r == cnt))
+                continue
+            R_or, A_or = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[:n])
+            tol = 1e-12 if mode == 0 else 1e-5
+            worst = max(worst, float(np.max(np.abs(r - R_or) / A_or)))
+            ok = ok and bool(np.all(np.abs(r - R_or) <= tol * A_or))
+        err = {"samples_checked": n_tot, "samples": f"the first {n_chk} of each of the {len(wls)} graphs",
+               "oracle_s": time.perf_counter() - t0}
+        if mode == 2:
+            err["bit_exact"] = ok
+        else:
+            err.update(max_err_over_abs_path_sum=worst, tolerance=1e-12 if mode == 0 else 1e-5, within_tolerance=ok)
     t_b = step_ms / 1e3
     w_bytes = 4 if mode == 1 else 8
     alg_bytes = float(sum(w.samples.num_samples * (2.0 * w.graph.num_nodes * w_bytes + 8 * w.graph.num_times + 8)
@@ -550,6 +577,7 @@ def run_batched(args, rank, world, local):
                    "edge_samples": units, "l2": "no flush: every step's working set is GBs of node values"},
         "roofline": roofline, "gpu_launches": args.steps,
         "sequential_ms": min(seq), "batched_speedup_vs_sequential": min(seq) / step_ms,
+        "error_vs_oracle": err,
     }
 
 

@@ -218,3 +218,37 @@ def test_batch_replans_when_a_member_reattaches_samples(cg):
     b.close()
     for gr in graphs:
         gr.close()
+
+
+def test_batched_workload_full_size_first_samples(cg):
+    """The batched uneven workload at its full size (64 graphs, 2.6e7 edges, 1.4e7
+    samples) in one work-queue launch, in the launch shape the benchmark times (4
+    samples per lane, 31 rows per warp, wide layout, each graph's workspace capped at
+    2 GB): every graph's first 32 samples are compared with the oracle one by one,
+    and every sample and mean against |R| <= C (C = the graph's path count)."""
+    import math
+    wls = batched(seed=3, num_graphs=64)
+    graphs, outs = [], []
+    for w in wls:
+        gr = cg.Graph.from_workload_graph(w.graph)
+        inf = gr.info()
+        psb = 2 * 8 * inf["W_max"] + 8 * inf["P"]
+        gr.set_tuning(tile_samples=int(max(128, min(65536, (2 << 30) // psb // 128 * 128))))
+        gr.set_samples(torch.from_numpy(w.samples.t).cuda(), w.samples.eps, w.samples.beta, cg.COS_T_SAMPLE_MAJOR)
+        graphs.append(gr)
+        outs.append(torch.full((w.samples.num_samples,), float("nan"), dtype=torch.float64, device="cuda"))
+    b = cg.Batch(graphs, 1, outs)
+    b.set_tuning(samples_per_lane=4, rows_per_warp=31, layout=1)
+    b.launch()
+    means = b.results()
+    for w, o, m in zip(wls, outs, means):
+        r = o.cpu().numpy()
+        R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[:32])
+        assert np.all(np.abs(r[:32] - R) <= TOL[1] * A)
+        cnt, ovf = oracle.count_paths(w.graph)
+        assert not ovf
+        assert np.all(np.isfinite(r)) and np.all(np.abs(r) <= cnt)
+        assert math.isfinite(m) and abs(m) <= cnt
+    b.close()
+    for gr in graphs:
+        gr.close()
