@@ -60,6 +60,7 @@ ORACLE_FULL_MAX = 1 << 17
 ORACLE_SLICE = 1024
 ORACLE_TIGHT = 64
 BATCH_CHECK_SAMPLES = 32          # batched workload: samples of every graph compared with the oracle
+SERVING_CHECK_REQUESTS = 8        # serving: completed requests per form whose means meet the oracle
 
 
 def parse_args(argv=None):
@@ -583,6 +584,34 @@ def run_batched(args, rank, world, local):
 
 # ------------------------------------------------------------------ serving
 
+def serving_oracle_check(torch, reqs, wpool, beta, mode, counter, n_req=SERVING_CHECK_REQUESTS):
+    """Means of completed requests against the FP64 oracle: the n_req completed requests
+    with the least work (edges x samples), their sample times drawn again from their
+    seeds (the counter-based generator the resident kernel uses, or the seeded device
+    generator of the batched server), the oracle's Neumaier mean compared with the
+    served mean relative to the mean of sum |paths|."""
+    import oracle
+    from paper_2501_00675_gb300.serve import request_times
+    from workloads import counter_times
+    done = [r for r in reqs if r.status == "done" and r.spec.num_samples > 0]
+    done.sort(key=lambda r: wpool[r.spec.graph_id][0].num_edges * r.spec.num_samples)
+    worst, ok, t0 = 0.0, True, time.perf_counter()
+    tol = 1e-12 if mode == 0 else 1e-5
+    for r in done[:n_req]:
+        g, eps = wpool[r.spec.graph_id]
+        S, D = r.spec.num_samples, g.num_times
+        if counter:
+            t = counter_times(r.spec.seed, 0, S, D, beta)
+        else:
+            t = np.ascontiguousarray(request_times(torch, r.spec, D, beta)[:, :S].cpu().numpy().T)
+        R, A = oracle.evaluate(g, eps, beta, t)
+        e = abs(r.mean - oracle.neumaier_mean(R)) / float(np.mean(A))
+        worst = max(worst, e)
+        ok = ok and e <= tol
+    return {"requests_checked": min(n_req, len(done)), "max_mean_err_over_mean_abs_path_sum": worst,
+            "tolerance": tol, "within_tolerance": ok, "oracle_s": time.perf_counter() - t0}
+
+
 def run_serving(args, rank, world, local):
     """Poisson request stream against the resident pool in the FP32/FP64-mixed mode:
     the resident server (the headline value), batched launches on two streams, and
@@ -595,8 +624,8 @@ def run_serving(args, rank, world, local):
     torch.cuda.set_device(local)
     cg.load_library(build_if_missing=True)
     t0 = time.perf_counter()
-    pool = [(cg.Graph.from_workload_graph(g), eps) for g, eps in serving_pool(seed=4, pool_size=args.pool_size,
-                                                                               max_nodes=args.max_nodes)]
+    wpool = serving_pool(seed=4, pool_size=args.pool_size, max_nodes=args.max_nodes)
+    pool = [(cg.Graph.from_workload_graph(g), eps) for g, eps in wpool]
     build_s = time.perf_counter() - t0
     rng = np.random.default_rng(1234 + rank)
     n_spec = int(args.rate * args.duration * 1.2) + 16
@@ -631,6 +660,9 @@ def run_serving(args, rank, world, local):
                          / (1 << 30)})
             if name.startswith("resident"):
                 summ["kernel_launches"] = srv.srv.stats()["launches"]
+            if rank == 0 and not args.no_oracle_check:
+                summ["error_vs_oracle"] = serving_oracle_check(torch, reqs, wpool, srv.beta, kw["mode"],
+                                                               counter=name.startswith("resident"))
             res[name] = summ
             srv.close()
         return res
