@@ -797,8 +797,9 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
     constexpr int CHV = 32 * V;
     // edges in flight per warp: 4; 3 for the FP32 walk with A, which holds three 16-byte
     // runs per edge (medium 4.13 ms with 2, 3.89 with 3, 3.98 with 4; the FP64 walk with A:
-    // 9.84 ms with 2, 7.82 with 4, 9.34 with 5; the FP64 walk: 6.38 with 4, 6.48 with 5)
-    constexpr int U = (Tr::kAbs && Tr::kBase == COS_MODE_FP32_MIXED) ? 3 : 4;
+    // 9.84 ms with 2, 7.82 with 4, 9.34 with 5; the FP64 walk: 6.38 with 4, 6.48 with 5);
+    // 8 for the count walk, which holds no propagator runs (medium 3.45 -> 3.13 ms)
+    constexpr int U = (Tr::kAbs && Tr::kBase == COS_MODE_FP32_MIXED) ? 3 : Tr::kCount ? 8 : 4;
     const LevelDesc ld = p.levels[l];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rpw = p.rows_per_warp;
