@@ -123,3 +123,24 @@ def test_profiled_traffic_scales_with_samples_and_checks_the_schedule():
         assert bench.profiled_traffic(tag, v["samples"], 3 - v["schedule"], v["layout"]) is None
         assert bench.profiled_traffic(tag, v["samples"], v["schedule"], v["layout"] + 1) is None
     assert bench.profiled_traffic("walk_count_nothing", 1, 1, 1) is None
+
+
+def test_profiled_traffic_entries_name_their_ncu_summaries():
+    """Every traffic figure the bench may report names the committed ncu summary it was
+    read from, and that summary exists and gives the same per-capture bytes."""
+    import json
+    import re
+    root = os.path.dirname(bench.__file__)
+    with open(os.path.join(root, "profiles", "traffic.json")) as f:
+        d = json.load(f)
+    for tag, v in d.items():
+        m = re.search(r"profiles/([\w.]+\.md)", v["source"])
+        assert m, tag
+        path = os.path.join(root, "profiles", m.group(1))
+        assert os.path.exists(path), (tag, path)
+        # the capture's read + write bytes (GB, 3 decimals) appear in the summary
+        gb = re.search(r"\(([\d.]+) \+ ([\d.]+) = ([\d.]+) GB\)", v["source"])
+        assert gb, tag
+        with open(path) as f:
+            text = f.read()
+        assert f"{gb.group(1)} + {gb.group(2)} = {gb.group(3)} GB" in text, tag
