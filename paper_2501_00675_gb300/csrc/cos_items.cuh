@@ -789,7 +789,7 @@ __device__ __forceinline__ void store_row_abs(const WalkParams& p, bool sink, fl
 // propagator loads in flight, and closes a row (store, reset) at its last in-edge.
 // Every row is the sum of its in-edges in CSR order, one multiply-add per edge per
 // sample.
-template <int MODE, int V, bool BALANCE = false>
+template <int MODE, int V, bool BALANCE = false, int U_FP32 = 4>
 __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, const TileCtx& tc, int item) {
     using Tr = Traits<MODE>;
     using Val = typename Tr::Val;
@@ -798,8 +798,14 @@ __device__ __forceinline__ void item_level_wide(const WalkParams& p, int l, cons
     // edges in flight per warp: 4; 3 for the FP32 walk with A, which holds three 16-byte
     // runs per edge (medium 4.13 ms with 2, 3.89 with 3, 3.98 with 4; the FP64 walk with A:
     // 9.84 ms with 2, 7.82 with 4, 9.34 with 5; the FP64 walk: 6.38 with 4, 6.48 with 5);
-    // 8 for the count walk, which holds no propagator runs (medium 3.45 -> 3.13 ms)
-    constexpr int U = (Tr::kAbs && Tr::kBase == COS_MODE_FP32_MIXED) ? 3 : Tr::kCount ? 8 : 4;
+    // 8 for the count walk, which holds no propagator runs (medium 3.45 -> 3.13 ms); for
+    // the FP32 walk, U_FP32: 4, and 6 in the level-synchronous kernel (80 registers;
+    // medium 2.44 -> 2.36 ms), where the work-queue kernel (64 registers) lost with 6
+    // (3.47 ms) and the resident server's kernel would spill 124 bytes
+    constexpr int U = (Tr::kAbs && Tr::kBase == COS_MODE_FP32_MIXED) ? 3
+                      : Tr::kCount                                 ? 8
+                      : Tr::kBase == COS_MODE_FP32_MIXED           ? U_FP32
+                                                                   : 4;
     const LevelDesc ld = p.levels[l];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rpw = p.rows_per_warp;
@@ -1354,7 +1360,7 @@ __device__ __forceinline__ void item_level_async(const WalkParams& p, int l, con
     cp_async_wait<0>();   // nothing in flight into shared memory that the next item reuses
 }
 
-template <int MODE, int V, int LAYOUT, bool BALANCE = false>
+template <int MODE, int V, int LAYOUT, bool BALANCE = false, int U_FP32 = 4>
 __device__ __forceinline__ bool item_level(const WalkParams& p, int l, const TileCtx& tc, int item,
                                            unsigned char* smem) {
     static_assert(!Traits<MODE>::kAbs || LAYOUT == LAYOUT_WIDE, "sums of |path| values: wide layout only");
@@ -1363,7 +1369,7 @@ __device__ __forceinline__ bool item_level(const WalkParams& p, int l, const Til
         item_level_async<MODE, V>(p, l, tc, item, smem);
         return true;
     }
-    if constexpr (LAYOUT == LAYOUT_WIDE) item_level_wide<MODE, V, BALANCE>(p, l, tc, item);
+    if constexpr (LAYOUT == LAYOUT_WIDE) item_level_wide<MODE, V, BALANCE, U_FP32>(p, l, tc, item);
     else item_level_grouped<MODE, V>(p, l, tc, item);
     return true;
 }

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<MODE, V, LAYOUT>()) walk_
         for (int l = 1; l < p.L; ++l) {
             const int n = level_items(p, p.levels[l], tc);
             for (int it = blockIdx.x; it < n; it += gridDim.x)
-                if (!item_level<MODE, V, LAYOUT>(p, l, tc, it, reinterpret_cast<unsigned char*>(smem))) break;
+                if (!item_level<MODE, V, LAYOUT, false, 6>(p, l, tc, it, reinterpret_cast<unsigned char*>(smem))) break;
             if (!grid_sync(p, epoch, 3 + l)) return;
         }
     }
