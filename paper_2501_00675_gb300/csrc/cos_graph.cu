@@ -529,7 +529,8 @@ static int resolve_tuning(cos_graph_t g, int kmode, cos_tuning* out, int64_t* ti
     // kernel on the FP32 and count walks of smaller graphs and on small evaluations,
     // where the work queue's per-call planning and upload are not amortised.
     // (with the FP32 work-queue walker at four CTAs per SM the FP32 walk of medium graphs
-    // joined the FP64 one there: medium mixed 2.44 -> 2.36 ms)
+    // joined the FP64 one there: medium mixed 2.44 -> 2.36 ms; the level-synchronous
+    // walker with six edges in flight per warp later matched it, 2.36 ms)
     const bool big = (double)g->E * (double)g->S >= 1e9;
     if (t.schedule <= 0)
         t.schedule = ((big && (mode == COS_MODE_FP64 || mode == COS_MODE_FP32_MIXED)) || g->Wmax >= 65536) ? 2 : 1;
