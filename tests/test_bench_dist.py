@@ -144,3 +144,29 @@ def test_profiled_traffic_entries_name_their_ncu_summaries():
         with open(path) as f:
             text = f.read()
         assert f"{gb.group(1)} + {gb.group(2)} = {gb.group(3)} GB" in text, tag
+
+
+def test_serving_oracle_check_flags_a_wrong_mean():
+    """The serving line's check: requests whose served means equal the oracle's pass;
+    one served mean moved by 1e-3 of the mean of sum |paths| is flagged.  Counter-drawn
+    times (the resident server's generator) only, so no device is needed."""
+    import oracle
+    from paper_2501_00675_gb300.serve import Request, RequestSpec
+    from workloads import counter_times
+    w = tiny(seed=5)
+    wpool = [(w.graph, w.samples.eps)]
+    reqs, scale = [], []
+    for q, S in enumerate((40, 130, 7)):
+        spec = RequestSpec(0, S, 1000 + q)
+        R, A = oracle.evaluate(w.graph, w.samples.eps, 10.0, counter_times(spec.seed, 0, S, w.graph.num_times, 10.0))
+        r = Request(spec=spec, need_bytes=0, t_submit=0.0, rid=q, status="done", mean=oracle.neumaier_mean(R))
+        reqs.append(r)
+        scale.append(float(np.mean(A)))
+    reqs.append(Request(spec=RequestSpec(0, 50, 9), need_bytes=0, t_submit=0.0, rid=9, status="shed"))
+    ok = bench.serving_oracle_check(None, reqs, wpool, 10.0, 1, counter=True)
+    assert ok["within_tolerance"] and ok["requests_checked"] == 3
+    assert ok["max_mean_err_over_mean_abs_path_sum"] == 0.0
+    reqs[1].mean += 1e-3 * scale[1]
+    bad = bench.serving_oracle_check(None, reqs, wpool, 10.0, 1, counter=True)
+    assert not bad["within_tolerance"]
+    assert abs(bad["max_mean_err_over_mean_abs_path_sum"] - 1e-3) < 1e-9
