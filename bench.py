@@ -536,29 +536,7 @@ def run_batched(args, rank, world, local):
         g.close()
     if rank != 0:
         return None
-    err = None
-    if not args.no_oracle_check:
-        # every graph's first samples of the timed launch against the FP64 oracle
-        import oracle
-        t0 = time.perf_counter()
-        worst, ok, n_tot = 0.0, True, 0
-        for w, r in zip(wls, got):
-            n = r.size
-            n_tot += n
-            if mode == 2:
-                cnt, _ = oracle.count_paths(w.graph)
-                ok = ok and bool(np.all(r == cnt))
-                continue
-            R_or, A_or = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[:n])
-            tol = 1e-12 if mode == 0 else 1e-5
-            worst = max(worst, float(np.max(np.abs(r - R_or) / A_or)))
-            ok = ok and bool(np.all(np.abs(r - R_or) <= tol * A_or))
-        err = {"samples_checked": n_tot, "samples": f"the first {n_chk} of each of the {len(wls)} graphs",
-               "oracle_s": time.perf_counter() - t0}
-        if mode == 2:
-            err["bit_exact"] = ok
-        else:
-            err.update(max_err_over_abs_path_sum=worst, tolerance=1e-12 if mode == 0 else 1e-5, within_tolerance=ok)
+    err = None if args.no_oracle_check else batched_oracle_check(wls, got, mode)
     t_b = step_ms / 1e3
     w_bytes = 4 if mode == 1 else 8
     alg_bytes = float(sum(w.samples.num_samples * (2.0 * w.graph.num_nodes * w_bytes + 8 * w.graph.num_times + 8)
@@ -583,6 +561,34 @@ def run_batched(args, rank, world, local):
 
 
 # ------------------------------------------------------------------ serving
+
+def batched_oracle_check(wls, got, mode):
+    """Every graph's first samples of the timed batched launch (got[g], host arrays)
+    against the FP64 oracle on the same samples, relative to sum |paths| (bit-exact
+    path counts in count mode)."""
+    import oracle
+    t0 = time.perf_counter()
+    worst, ok, n_tot = 0.0, True, 0
+    tol = 1e-12 if mode == 0 else 1e-5
+    for w, r in zip(wls, got):
+        n = r.size
+        n_tot += n
+        if mode == 2:
+            cnt, _ = oracle.count_paths(w.graph)
+            ok = ok and bool(np.all(r == cnt))
+            continue
+        R_or, A_or = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[:n])
+        if n:
+            worst = max(worst, float(np.max(np.abs(r - R_or) / A_or)))
+        ok = ok and bool(np.all(np.abs(r - R_or) <= tol * A_or))
+    err = {"samples_checked": n_tot, "samples": f"the first {max((r.size for r in got), default=0)} of each "
+                                                f"of the {len(wls)} graphs", "oracle_s": time.perf_counter() - t0}
+    if mode == 2:
+        err["bit_exact"] = ok
+    else:
+        err.update(max_err_over_abs_path_sum=worst, tolerance=tol, within_tolerance=ok)
+    return err
+
 
 def serving_oracle_check(torch, reqs, wpool, beta, mode, counter, n_req=SERVING_CHECK_REQUESTS):
     """Means of completed requests against the FP64 oracle: the n_req completed requests

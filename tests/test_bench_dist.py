@@ -170,3 +170,24 @@ def test_serving_oracle_check_flags_a_wrong_mean():
     bad = bench.serving_oracle_check(None, reqs, wpool, 10.0, 1, counter=True)
     assert not bad["within_tolerance"]
     assert abs(bad["max_mean_err_over_mean_abs_path_sum"] - 1e-3) < 1e-9
+
+
+def test_batched_oracle_check_flags_a_wrong_sample():
+    """The batched line's check on host arrays: the oracle's own values pass (and the
+    path counts in count mode); one sample moved by 1e-3 of its sum |paths| is flagged."""
+    import oracle
+    wls = [tiny(seed=11, num_samples=40), tiny(seed=12, num_samples=25)]
+    got, scale = [], []
+    for w in wls:
+        R, A = oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[:16])
+        got.append(R.copy())
+        scale.append(A)
+    ok = bench.batched_oracle_check(wls, got, 1)
+    assert ok["within_tolerance"] and ok["samples_checked"] == 32 and ok["max_err_over_abs_path_sum"] == 0.0
+    got[1][3] += 1e-3 * scale[1][3]
+    bad = bench.batched_oracle_check(wls, got, 1)
+    assert not bad["within_tolerance"] and abs(bad["max_err_over_abs_path_sum"] - 1e-3) < 1e-9
+    counts = [np.full(8, oracle.count_paths(w.graph)[0], dtype=np.int64) for w in wls]
+    assert bench.batched_oracle_check(wls, counts, 2)["bit_exact"]
+    counts[0][2] += 1
+    assert not bench.batched_oracle_check(wls, counts, 2)["bit_exact"]
