@@ -16,11 +16,13 @@ import os
 import pytest
 
 import oracle
+import test_oracle_mc as mc_pins
 import test_oracle_pins as pins
 
 ORACLE_DIR = os.path.dirname(os.path.abspath(oracle.__file__))
 SOURCE = os.path.join(ORACLE_DIR, "cos_oracle.c")
 MODULE = os.path.join(ORACLE_DIR, "__init__.py")
+MC_MODULE = os.path.join(ORACLE_DIR, "metropolis.py")
 
 # (name, text in cos_oracle.c, replacement, which occurrence)
 MUTATIONS = [
@@ -79,6 +81,21 @@ PY_MUTATIONS = [
     ("brute force: |path| sums signed paths", "a += abs(prod)", "a += prod", 0),
     ("brute force: paths lose their edges", "stack.append((int(e[q, 1]), path + [q]))",
      "stack.append((int(e[q, 1]), path))", 0),
+]
+
+
+# the same for the Metropolis walkers, against the pins of test_oracle_mc.py
+MC_MUTATIONS = [
+    ("Metropolis: acceptance rule inverted", "acc = lhs < rhs", "acc = lhs > rhs", 0),
+    ("Metropolis: weight |R| replaced by R", "lhs, rhs = u * np.abs(R), np.abs(Rp)", "lhs, rhs = u * R, Rp", 0),
+    ("Metropolis: every move accepted", "acc = lhs < rhs", "acc = np.ones(S, dtype=bool)", 0),
+    ("Metropolis: last coordinate never proposed", "i = ((w0 * np.uint64(num_times)) >> np.uint64(32))",
+     "i = ((w0 * np.uint64(max(num_times - 1, 1))) >> np.uint64(32))", 0),
+    ("Metropolis: tally of the proposal", "n_pos += int((R > 0).sum())", "n_pos += int((Rp > 0).sum())", 0),
+    ("Metropolis: streams share the sample generator's counters", "0x80000000 | ((step >> 32) & 0x7FFFFFFF)",
+     "((step >> 32) & 0x7FFFFFFF)", 0),
+    ("Metropolis: proposals in [0, 1) instead of [0, beta)", "return i, beta * x, u", "return i, x, u", 0),
+    ("Metropolis: accepted moves not kept", "t[acc] = tp[acc]", "pass", 0),
 ]
 
 
@@ -151,6 +168,41 @@ def test_unchanged_copy_passes_every_pin(tmp_path, monkeypatch):
     for tag, text in (("control", None), ("control_py", py)):   # the package, then a copied module
         mod = _oracle_from(src, tmp_path, tag, py_text=text)
         assert _failing_pins(mod, monkeypatch, stop_at_first=False) == []
+
+
+def _mc_module(py_text, tmp_path, tag):
+    """A copy of oracle.metropolis built from py_text (its relative import of the
+    oracle's evaluate still resolves to the unchanged package)."""
+    path = tmp_path / f"{tag}.py"
+    path.write_text(py_text)
+    spec = importlib.util.spec_from_file_location(f"oracle.metropolis_{tag}", str(path))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _failing_mc_pins(mod, monkeypatch):
+    monkeypatch.setattr(mc_pins, "mc", mod)
+    failed = []
+    for name in dir(mc_pins):
+        if name.startswith("test_"):
+            try:
+                getattr(mc_pins, name)()
+            except (AssertionError, ValueError, IndexError, FloatingPointError):
+                failed.append(name)
+    return failed
+
+
+def test_unchanged_metropolis_copy_passes_every_pin(tmp_path, monkeypatch):
+    with open(MC_MODULE) as f:
+        assert _failing_mc_pins(_mc_module(f.read(), tmp_path, "control"), monkeypatch) == []
+
+
+@pytest.mark.parametrize("name,old,new,which", MC_MUTATIONS, ids=[m[0] for m in MC_MUTATIONS])
+def test_planted_metropolis_mistake_fails_a_pin(tmp_path, monkeypatch, name, old, new, which):
+    with open(MC_MODULE) as f:
+        mod = _mc_module(_plant(f.read(), old, new, which), tmp_path, "mutant")
+    assert _failing_mc_pins(mod, monkeypatch), f"no pin catches: {name}"
 
 
 @pytest.mark.parametrize("name,old,new,which", MUTATIONS, ids=[m[0] for m in MUTATIONS])
