@@ -92,6 +92,8 @@ def parse_args(argv=None):
     ap.add_argument("--autotune", action="store_true",
                     help="pick the launch shape with cos_autotune on the workload before timing")
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
+    ap.add_argument("--reference-seconds", type=float, default=120.0,
+                    help="reference arm: about how long its warm-up and timed steps take in total")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
@@ -550,9 +552,7 @@ def run_batched(args, rank, world, local):
         "metric": "edge·sample updates/s", "value": units * world / t_b, "unit": "edge·sample updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.mode or "mixed"], "data": "synthetic",
-        "config": {"workload": f"batched uneven: {len(wls)} graphs, order n~U{{2..8}}, L=2n+2, N logU[1e3,1e6], "
-                               "fan-in U{1..4}, K=16, D=L, samples logU[4096,2^20], one persistent "
-                               "CUDA-graph-captured launch", "autotuned": best, "generation_s": gen_s,
+        "config": {"workload": batched_desc(len(wls)), "autotuned": best, "generation_s": gen_s,
                    "edge_samples": units, "l2": "no flush: every step's working set is GBs of node values"},
         "roofline": roofline, "gpu_launches": args.steps,
         "sequential_ms": min(seq), "batched_speedup_vs_sequential": min(seq) / step_ms,
@@ -696,6 +696,58 @@ def run_serving(args, rank, world, local):
 
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
 
+def batched_desc(num_graphs: int) -> str:
+    return (f"batched uneven: {num_graphs} graphs, order n~U{{2..8}}, L=2n+2, N logU[1e3,1e6], "
+            "fan-in U{1..4}, K=16, D=L, samples logU[4096,2^20], one persistent CUDA-graph-captured launch")
+
+
+def run_reference_batched(args, rank, world):
+    """The oracle on the batched workload: each step evaluates the same fraction of
+    every graph's samples (its first ones, at least one), so a step has the
+    workload's mix of graphs and sample counts; the fraction is sized so that
+    warm-up and timed steps take about --reference-seconds (two minutes by default)."""
+    if rank != 0:
+        return None
+    from workloads import batched
+    import oracle
+    oracle.build()
+    wls = batched(seed=3, num_graphs=args.num_graphs)
+    t0 = time.perf_counter()
+    for w in wls:                                          # rate probe: 4 samples of every graph
+        oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[:4], with_abs=False)
+    rate = sum(w.graph.num_edges * min(4, w.samples.num_samples) for w in wls) / (time.perf_counter() - t0)
+    total = float(sum(w.graph.num_edges * w.samples.num_samples for w in wls))
+    frac = min(1.0, rate * args.reference_seconds / max(1, args.steps + args.warmup) / total)
+    n = [max(1, int(frac * w.samples.num_samples)) for w in wls]
+    units = float(sum(w.graph.num_edges * k for w, k in zip(wls, n)))
+
+    def step():
+        for w, k in zip(wls, n):
+            oracle.evaluate(w.graph, w.samples.eps, w.samples.beta, w.samples.t[:k], with_abs=False)
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    value = units * args.steps / sum(times)
+    cores = len(os.sched_getaffinity(0))
+    mode_name = args.mode or "mixed"
+    return {
+        "impl": "reference", "metric": "edge·sample updates/s", "value": value, "unit": "edge·sample updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": batched_desc(len(wls)), "mode": mode_name, "sample_fraction": frac,
+                   "edge_samples_per_step": units,
+                   "note": "the reference arm is the CPU oracle (plain level-wise DP in double, OpenMP over samples)"},
+        "cpu_baseline": {"value": value, "unit": "edge·sample updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"the first {frac:.2e} of every graph's samples per step"},
+        "e2e": {"value": value, "unit": "edge·sample updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -706,12 +758,12 @@ def run_reference(args, rank, world):
     g, s = wl.graph, wl.samples
     import oracle
     oracle.build()
-    # size each step so that warmup + steps take about two minutes in total
+    # size each step so that warmup + steps take about --reference-seconds in total
     n = 8
     t0 = time.perf_counter()
     oracle.evaluate(g, s.eps, s.beta, s.t[:n], with_abs=False)
     per = (time.perf_counter() - t0) / n
-    n_step = int(max(8, min(s.num_samples, 120.0 / max(per, 1e-9) / max(1, args.steps + args.warmup))))
+    n_step = int(max(8, min(s.num_samples, args.reference_seconds / max(per, 1e-9) / max(1, args.steps + args.warmup))))
     for k in range(args.warmup):
         oracle.evaluate(g, s.eps, s.beta, s.t[:n_step], with_abs=False)
     times = []
@@ -752,8 +804,10 @@ def main(argv=None):
         else:
             dist.init_process_group(backend=backend)
     if args.impl == "reference":
-        if args.workload in ("serving", "batched"):
-            line = {"impl": "reference", "unavailable": f"the {args.workload} workload has no CPU reference arm"} if rank == 0 else None
+        if args.workload == "serving":
+            line = {"impl": "reference", "unavailable": "the serving workload has no CPU reference arm"} if rank == 0 else None
+        elif args.workload == "batched":
+            line = run_reference_batched(args, rank, world)
         else:
             line = run_reference(args, rank, world)
     elif args.workload == "serving":

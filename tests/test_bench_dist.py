@@ -191,3 +191,13 @@ def test_batched_oracle_check_flags_a_wrong_sample():
     assert bench.batched_oracle_check(wls, counts, 2)["bit_exact"]
     counts[0][2] += 1
     assert not bench.batched_oracle_check(wls, counts, 2)["bit_exact"]
+
+
+def test_batched_reference_arm_times_the_oracle_on_the_same_mix():
+    args = bench.parse_args(["--impl", "reference", "--workload", "batched", "--num-graphs", "3",
+                             "--steps", "1", "--warmup", "0", "--reference-seconds", "1"])
+    assert bench.run_reference_batched(args, rank=1, world=2) is None
+    line = bench.run_reference_batched(args, rank=0, world=1)
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["workload"] == bench.batched_desc(3)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
